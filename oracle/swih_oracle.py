@@ -1,0 +1,311 @@
+"""CPU FP64 oracle for spatially weighted local histograms (SWIH).
+
+TEST INFRASTRUCTURE ONLY. The only code allowed to import, call or execute
+anything under ``oracle/`` is the test suite, the package smoke check in
+``__graft_entry__.py`` and the CPU-baseline leg of ``bench.py``. The CUDA
+library never links it and this module never imports the CUDA library; the
+two share nothing but the seeded input generators.
+
+Every function states the passage of the paper it writes out. Where the
+paper is silent the reading taken is stated in the docstring:
+
+* ``quantize`` -- the quantiser Q of Sec. 2.1 (named after Eq. 2, not
+  defined): equal-width bins, b = floor(v * B / 2^bitdepth).
+* ``weighted_ih`` -- Eq. 2 with the pixel weight w(i, j) = i^p j^q, as a
+  plain double cumulative sum. Kept in the ring Z / 2^bits, which is exact
+  modular arithmetic: the CUDA path stores the same ring elements, so the
+  comparison is bit for bit.
+* ``kernel_weights`` -- the spatial kernels of Fig. 1 / Sec. 2:
+  Manhattan from the city-block distance of Eq. 1, Euclidean and Gaussian
+  (the paper names these without a formula; readings below).
+* ``hist_*`` / ``likelihood_*`` -- the brute-force approach of Sec. 2
+  (visit every pixel of every window), normalised by the window's own
+  total weight, scored by the Bhattacharyya coefficient (the paper leaves
+  the similarity unnamed).
+
+Parity unpinned: the Gaussian kernel is a polynomial approximant (the paper
+gives no decomposition of it); its distance from the true Gaussian is
+reported by the tests, not pinned to a value printed in the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from functools import lru_cache
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "brute.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD_DIR, "libswih_oracle.so")
+
+KINDS = ("plain", "manhattan", "euclidean", "gaussian")
+
+
+# --------------------------------------------------------------------------
+# build / load the brute-force C routines
+# --------------------------------------------------------------------------
+def build(force: bool = False) -> str:
+    """Compile brute.c into a shared object with gcc (-O2, OpenMP, no fast-math)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+@lru_cache(maxsize=1)
+def _lib() -> ctypes.CDLL:
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    L = ctypes.c_long
+    lib.swih_oracle_threads.restype = I
+    lib.swih_oracle_hist_at.argtypes = [P, I, I, I, P, I, I, P, P, L, P]
+    lib.swih_oracle_hist_rect.argtypes = [P, I, I, I, P, I, I, I, I, I, I, P]
+    lib.swih_oracle_likelihood_at.argtypes = [P, I, I, I, P, I, I, P, P, L, P, P]
+    lib.swih_oracle_likelihood_rect.argtypes = [P, I, I, I, P, I, I, I, I, I, I, P, P]
+    return lib
+
+
+def threads() -> int:
+    """OpenMP threads the brute-force loops use."""
+    return int(_lib().swih_oracle_threads())
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# --------------------------------------------------------------------------
+# quantiser Q (Sec. 2.1, after Eq. 2)
+# --------------------------------------------------------------------------
+def quantize(image: np.ndarray, bitdepth: int, B: int) -> np.ndarray:
+    """Equal-width quantiser: b = floor(v * B / 2^bitdepth), as uint8 (B <= 256).
+
+    The paper names Q as "the quantization function that determines which
+    bin to increase" without fixing it; equal-width bins over the full
+    pixel range are the reading taken.
+    """
+    if not (1 <= B <= 256):
+        raise ValueError("B must be in [1, 256]")
+    v = image.astype(np.int64)
+    return ((v * B) >> bitdepth).astype(np.uint8)
+
+
+# --------------------------------------------------------------------------
+# Eq. 2: weighted integral histogram with weight x^p y^q
+# --------------------------------------------------------------------------
+def weighted_ih(bins: np.ndarray, b: int, p: int, q: int, bits: int = 64) -> np.ndarray:
+    """IH_w(x, y, b) = sum_{i<=x, j<=y} [Q(f(i, j)) = b] * w(i, j), w = i^p j^q (Eq. 2).
+
+    i is the column and j the row, so the result is indexed [y, x]. The
+    sums are taken modulo 2^bits (bits = 32 or 64): unsigned numpy
+    arithmetic wraps, which is exact arithmetic in that ring.
+    """
+    if bits not in (32, 64):
+        raise ValueError("bits must be 32 or 64")
+    h, w = bins.shape
+    xs = np.arange(w, dtype=np.uint64)
+    ys = np.arange(h, dtype=np.uint64)
+    wx = np.ones(w, dtype=np.uint64)
+    for _ in range(p):
+        wx = wx * xs
+    wy = np.ones(h, dtype=np.uint64)
+    for _ in range(q):
+        wy = wy * ys
+    weight = wy[:, None] * wx[None, :]
+    term = np.where(bins == b, weight, np.uint64(0))
+    ih = np.cumsum(np.cumsum(term, axis=0, dtype=np.uint64), axis=1, dtype=np.uint64)
+    if bits == 32:
+        return (ih & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    return ih
+
+
+def plain_ih(bins: np.ndarray, B: int) -> np.ndarray:
+    """Porikli's plain integral histogram, int64 [B, H, W] (Eq. 2 with w = 1)."""
+    onehot = (bins[None, :, :] == np.arange(B, dtype=bins.dtype)[:, None, None])
+    return np.cumsum(np.cumsum(onehot.astype(np.int64), axis=1), axis=2)
+
+
+# --------------------------------------------------------------------------
+# spatial kernels (Fig. 1, Eq. 1)
+# --------------------------------------------------------------------------
+def gauss_degree(r: int, degree: int) -> int:
+    """Polynomial degree actually fitted on a half-width r: at most r, because
+    the samples t = d^2 / r^2, d = 0..r, take only r + 1 distinct values."""
+    return max(0, min(degree, r))
+
+
+def gauss_fit(r: int, sigma: float, degree: int) -> np.ndarray:
+    """Least-squares fit of P(t) = sum_i c_i t^i to exp(-d^2 / (2 sigma^2)).
+
+    Samples are the integer offsets d = -r..r of one window axis with
+    t = d^2 / r^2. Returns c (length gauss_degree(r, degree) + 1), float64.
+    Solved with numpy's SVD-based least squares.
+    """
+    D = gauss_degree(r, degree)
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    t = (d * d) / float(r * r)
+    A = np.stack([t ** i for i in range(D + 1)], axis=1)
+    y = np.exp(-(d * d) / (2.0 * sigma * sigma))
+    c, *_ = np.linalg.lstsq(A, y, rcond=None)
+    return c
+
+
+def gauss_axis(r: int, sigma: float, degree: int) -> np.ndarray:
+    """g(d) = P(d^2 / r^2) sampled at d = -r..r."""
+    c = gauss_fit(r, sigma, degree)
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    t = (d * d) / float(r * r)
+    return sum(ci * t ** i for i, ci in enumerate(c))
+
+
+def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
+                   sigma_frac: float = 0.25) -> np.ndarray:
+    """Weight table K[dy + ry, dx + rx] (float64, h x w) of one window.
+
+    * plain: K = 1 (Porikli's unweighted local histogram).
+    * manhattan: K = (rx - |dx|) + (ry - |dy|). Eq. 1's city-block distance
+      |dx| + |dy| subtracted from its value at the window corner, so the
+      weight is largest at the centre, falls linearly and is zero at the
+      four corners (Sec. 2: low weights near the contour; Sec. 2.1: weights
+      rise linearly from each quadrant's outer corner to the centre).
+    * euclidean: K = (rx^2 - dx^2) + (ry^2 - dy^2), the same construction
+      on the squared Euclidean distance dx^2 + dy^2 (the square root of
+      the true distance has no finite decomposition into integral
+      histograms).
+    * gaussian: K = Px(dx^2 / rx^2) * Py(dy^2 / ry^2), each factor the
+      least-squares polynomial (gauss_fit) of the axis Gaussian with
+      sigma = sigma_frac * (window length along that axis).
+    """
+    if w < 3 or h < 3 or w % 2 == 0 or h % 2 == 0:
+        raise ValueError("window sides must be odd and >= 3")
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    dx = np.arange(-rx, rx + 1, dtype=np.float64)[None, :]
+    dy = np.arange(-ry, ry + 1, dtype=np.float64)[:, None]
+    if kind == "plain":
+        return np.ones((h, w), dtype=np.float64)
+    if kind == "manhattan":
+        return (rx - np.abs(dx)) + (ry - np.abs(dy))
+    if kind == "euclidean":
+        return (rx * rx - dx * dx) + (ry * ry - dy * dy)
+    if kind == "gaussian":
+        gx = gauss_axis(rx, sigma_frac * w, degree)[None, :]
+        gy = gauss_axis(ry, sigma_frac * h, degree)[:, None]
+        K = gy * gx
+        if (K < 0).any():
+            raise ValueError("Gaussian approximant is negative inside the window")
+        return K
+    raise ValueError(f"unknown kernel {kind!r}")
+
+
+def true_gaussian(w: int, h: int, sigma_frac: float = 0.25) -> np.ndarray:
+    """exp(-dx^2 / 2 sx^2 - dy^2 / 2 sy^2) on the window (for reporting only)."""
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    dx = np.arange(-rx, rx + 1, dtype=np.float64)[None, :]
+    dy = np.arange(-ry, ry + 1, dtype=np.float64)[:, None]
+    sx, sy = sigma_frac * w, sigma_frac * h
+    return np.exp(-dx * dx / (2 * sx * sx) - dy * dy / (2 * sy * sy))
+
+
+# --------------------------------------------------------------------------
+# brute-force local histograms and likelihood (Sec. 2, "Brute-force Approach")
+# --------------------------------------------------------------------------
+def _check(bins: np.ndarray, B: int, K: np.ndarray):
+    if bins.dtype != np.uint8 or bins.ndim != 2:
+        raise TypeError("bins must be a 2-D uint8 array")
+    if int(bins.max(initial=0)) >= B:
+        raise ValueError("bin index out of range")
+    h, w = K.shape
+    if h % 2 == 0 or w % 2 == 0:
+        raise ValueError("odd window required")
+    return (np.ascontiguousarray(bins), np.ascontiguousarray(K, dtype=np.float64))
+
+
+def valid_centres(H: int, W: int, w: int, h: int):
+    """(x0, y0, nx, ny): centres whose whole window lies inside the image."""
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    return rx, ry, W - w + 1, H - h + 1
+
+
+def hist_rect(bins, B, K, cx0, cy0, ncx, ncy) -> np.ndarray:
+    """Unnormalised U_c(b) for a rectangle of centres, float64 [ncy, ncx, B]."""
+    bins, K = _check(bins, B, K)
+    H, W = bins.shape
+    h, w = K.shape
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    if cx0 - rx < 0 or cy0 - ry < 0 or cx0 + ncx - 1 + rx >= W or cy0 + ncy - 1 + ry >= H:
+        raise ValueError("a window leaves the image")
+    U = np.empty((ncy, ncx, B), dtype=np.float64)
+    _lib().swih_oracle_hist_rect(_ptr(bins), H, W, B, _ptr(K), w, h, cx0, cy0, ncx, ncy, _ptr(U))
+    return U
+
+
+def hist_at(bins, B, K, cx, cy) -> np.ndarray:
+    """Unnormalised U_c(b) at listed centres, float64 [n, B]."""
+    bins, K = _check(bins, B, K)
+    H, W = bins.shape
+    h, w = K.shape
+    cx = np.ascontiguousarray(cx, dtype=np.int32)
+    cy = np.ascontiguousarray(cy, dtype=np.int32)
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    if cx.size and (cx.min() < rx or cy.min() < ry or cx.max() >= W - rx or cy.max() >= H - ry):
+        raise ValueError("a window leaves the image")
+    U = np.empty((cx.size, B), dtype=np.float64)
+    _lib().swih_oracle_hist_at(_ptr(bins), H, W, B, _ptr(K), w, h, _ptr(cx), _ptr(cy),
+                               cx.size, _ptr(U))
+    return U
+
+
+def normalise(U: np.ndarray) -> np.ndarray:
+    """H_c(b) = U_c(b) / sum_b U_c(b) (Sec. 2.1: normalise the histogram)."""
+    return U / U.sum(axis=-1, keepdims=True)
+
+
+def likelihood_rect(bins, B, K, q, cx0, cy0, ncx, ncy) -> np.ndarray:
+    """Bhattacharyya coefficient of each normalised window histogram vs q, [ncy, ncx]."""
+    bins, K = _check(bins, B, K)
+    H, W = bins.shape
+    h, w = K.shape
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    if cx0 - rx < 0 or cy0 - ry < 0 or cx0 + ncx - 1 + rx >= W or cy0 + ncy - 1 + ry >= H:
+        raise ValueError("a window leaves the image")
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    L = np.empty((ncy, ncx), dtype=np.float64)
+    _lib().swih_oracle_likelihood_rect(_ptr(bins), H, W, B, _ptr(K), w, h, cx0, cy0, ncx, ncy,
+                                       _ptr(q), _ptr(L))
+    return L
+
+
+def likelihood_at(bins, B, K, q, cx, cy) -> np.ndarray:
+    """Bhattacharyya coefficient at listed centres, float64 [n]."""
+    bins, K = _check(bins, B, K)
+    H, W = bins.shape
+    h, w = K.shape
+    cx = np.ascontiguousarray(cx, dtype=np.int32)
+    cy = np.ascontiguousarray(cy, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    L = np.empty(cx.size, dtype=np.float64)
+    _lib().swih_oracle_likelihood_at(_ptr(bins), H, W, B, _ptr(K), w, h, _ptr(cx), _ptr(cy),
+                                     cx.size, _ptr(q), _ptr(L))
+    return L
+
+
+def likelihood_map(bins, B, K, q) -> np.ndarray:
+    """Likelihood at every valid centre, [H - h + 1, W - w + 1]."""
+    H, W = bins.shape
+    h, w = K.shape
+    x0, y0, nx, ny = valid_centres(H, W, w, h)
+    return likelihood_rect(bins, B, K, q, x0, y0, nx, ny)
+
+
+def target_hist(bins, B, K, xc, yc) -> np.ndarray:
+    """Normalised weighted histogram of the window centred at (xc, yc), float64 [B]."""
+    return normalise(hist_at(bins, B, K, [xc], [yc]))[0]

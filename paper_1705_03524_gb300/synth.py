@@ -1,0 +1,152 @@
+"""Seeded synthetic inputs shaped like the paper's tracking workloads.
+
+The paper evaluates on a VOT2016 frame (Sec. 3, Fig. 5) and on wide-area
+aerial imagery (Sec. 4, Fig. 7); neither is available here, so these
+generators produce stand-ins with the same sizes, bit depths and structure:
+a smooth textured background with compact textured objects planted on it.
+
+This module holds no arithmetic of the histogram method itself (no
+quantisation, no weighting, no integral histograms). Both the CUDA path and
+the CPU oracle consume its outputs, and nothing else is shared between them.
+Every generator is a pure function of its arguments and a seed
+(``numpy.random.default_rng``), so the same call gives the same array on any
+machine with the same numpy.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "uniform_image",
+    "fbm_value_noise",
+    "blob_scene",
+    "Scene",
+    "config1",
+    "config2",
+    "odd_window",
+]
+
+
+def uniform_image(h: int, w: int, bitdepth: int = 8, seed: int = 1) -> np.ndarray:
+    """i.i.d. uniform pixels in [0, 2^bitdepth) as uint8 (bitdepth 8) or uint16."""
+    rng = np.random.default_rng(seed)
+    dtype = np.uint8 if bitdepth <= 8 else np.uint16
+    return rng.integers(0, 1 << bitdepth, size=(h, w), dtype=np.int64).astype(dtype)
+
+
+def _quintic_fade(t: np.ndarray) -> np.ndarray:
+    # Perlin's improved-noise fade curve 6t^5 - 15t^4 + 10t^3 (Perlin, 2002).
+    return t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+
+
+def fbm_value_noise(h: int, w: int, octaves: int, cell: float, rng: np.random.Generator,
+                    gain: float = 0.5) -> np.ndarray:
+    """Fractal sum of lattice value noise, normalised to [-1, 1] (float64, h x w).
+
+    Octave o uses a lattice of spacing ``cell / 2^o`` with i.i.d. U[-1, 1]
+    values interpolated by the quintic fade; amplitudes fall by ``gain``.
+    """
+    out = np.zeros((h, w), dtype=np.float64)
+    norm = 0.0
+    amp = 1.0
+    for o in range(octaves):
+        c = max(cell / (2.0 ** o), 2.0)
+        gy = int(np.ceil(h / c)) + 2
+        gx = int(np.ceil(w / c)) + 2
+        lat = rng.uniform(-1.0, 1.0, size=(gy, gx))
+        ys = np.arange(h) / c
+        xs = np.arange(w) / c
+        y0 = np.floor(ys).astype(np.int64)
+        x0 = np.floor(xs).astype(np.int64)
+        fy = _quintic_fade(ys - y0)[:, None]
+        fx = _quintic_fade(xs - x0)[None, :]
+        v00 = lat[y0][:, x0]
+        v01 = lat[y0][:, x0 + 1]
+        v10 = lat[y0 + 1][:, x0]
+        v11 = lat[y0 + 1][:, x0 + 1]
+        top = v00 + (v01 - v00) * fx
+        bot = v10 + (v11 - v10) * fx
+        out += amp * (top + (bot - top) * fy)
+        norm += amp
+        amp *= gain
+    return out / norm
+
+
+@dataclass
+class Scene:
+    """A generated frame plus the ground-truth objects planted in it."""
+
+    image: np.ndarray
+    bitdepth: int
+    # (cx, cy) integer centres of the planted objects; index 0 is the target.
+    centres: list = field(default_factory=list)
+    # (semi-axis a, semi-axis b, angle, mean) per planted object
+    params: list = field(default_factory=list)
+
+
+def blob_scene(h: int, w: int, bitdepth: int, seed: int, n_blobs: int,
+               axes: tuple = (10, 60), octaves: int = 4, cell: float = 128.0,
+               bg_mean_frac: float = 0.5, bg_amp_frac: float = 48.0 / 256.0,
+               noise_frac: float = 12.0 / 256.0, margin: int = 64) -> Scene:
+    """Smooth fBm background plus textured elliptical objects.
+
+    Background: ``mean + amp * fbm`` with mean and amplitude given as
+    fractions of the full range (128 +- 48 for 8-bit images). Each object is
+    an ellipse with semi-axes drawn from U[axes], a random orientation, a
+    mean level drawn uniformly from the middle 70% of the range and i.i.d.
+    Gaussian texture of std ``noise_frac * range`` (12 for 8-bit images).
+    Values are rounded and clamped to the pixel range.
+    """
+    rng = np.random.default_rng(seed)
+    full = float(1 << bitdepth)
+    img = bg_mean_frac * full + bg_amp_frac * full * fbm_value_noise(h, w, octaves, cell, rng)
+    yy, xx = np.mgrid[0:h, 0:w]
+    centres = []
+    params = []
+    lo_mean = int(0.15625 * full)   # 40 for 8-bit
+    hi_mean = int(0.83984375 * full)  # 215 for 8-bit
+    for _ in range(n_blobs):
+        a = rng.uniform(axes[0], axes[1])
+        b = rng.uniform(axes[0], axes[1])
+        ang = rng.uniform(0.0, np.pi)
+        mean = float(rng.integers(lo_mean, hi_mean + 1))
+        m = min(margin, h // 2 - 1, w // 2 - 1)
+        cx = int(rng.integers(m, w - m))
+        cy = int(rng.integers(m, h - m))
+        ca, sa = np.cos(ang), np.sin(ang)
+        u = (xx - cx) * ca + (yy - cy) * sa
+        v = -(xx - cx) * sa + (yy - cy) * ca
+        inside = (u / a) ** 2 + (v / b) ** 2 <= 1.0
+        n_in = int(inside.sum())
+        img[inside] = mean + rng.normal(0.0, noise_frac * full, size=n_in)
+        centres.append((cx, cy))
+        params.append((a, b, ang, mean))
+    img = np.clip(np.rint(img), 0, full - 1)
+    dtype = np.uint8 if bitdepth <= 8 else np.uint16
+    return Scene(image=img.astype(dtype), bitdepth=bitdepth, centres=centres, params=params)
+
+
+def odd_window(size: float) -> int:
+    """Nearest odd integer >= 3 to a (possibly fractional) window size."""
+    n = 2 * int(round((size - 1.0) / 2.0)) + 1
+    return max(n, 3)
+
+
+def config1(seed: int = 1) -> dict:
+    """128x128 uint8 i.i.d. uniform image, B=16, one 31x31 Manhattan window,
+    target = the window at the image centre (64, 64)."""
+    img = uniform_image(128, 128, 8, seed)
+    return dict(image=img, bitdepth=8, B=16, kernels=("manhattan",), windows=(31,),
+                target_centre=(64, 64))
+
+
+def config2(seed: int = 2, size: int = 1024) -> dict:
+    """1024x1024 uint8 smooth background + 8 textured elliptical objects,
+    B=32, Manhattan / Euclidean / Gaussian kernels at windows 21, 41, 81;
+    the target is the window centred on object 0."""
+    sc = blob_scene(size, size, 8, seed, n_blobs=8)
+    return dict(image=sc.image, bitdepth=8, B=32,
+                kernels=("manhattan", "euclidean", "gaussian"), windows=(21, 41, 81),
+                target_centre=sc.centres[0], scene=sc)

@@ -1,0 +1,364 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself.
+
+Each test checks the oracle against something the paper or the mathematics
+fixes: hand-summed fixtures, closed-form kernel masses (Sec. 2.1: the total
+weight of a window does not depend on where the window is), the plain
+histogram as the K = 1 special case, exhaustive tiny inputs, mirror
+symmetry, and the paper's own decomposition (Sec. 2.1, Eq. 2) evaluated in
+exact integer arithmetic, which must agree with brute force (Sec. 3: the
+method is exact).
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import swih_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------
+# helpers written independently of the oracle
+# ----------------------------------------------------------------------------
+def read_hand_fixture(name):
+    rows, cases = [], []
+    with open(os.path.join(GOLDEN, name)) as f:
+        lines = [ln.split("#")[0].strip() for ln in f]
+    lines = [ln for ln in lines if ln]
+    _, h, w = lines[0].split()
+    h, w = int(h), int(w)
+    for ln in lines[1:1 + h]:
+        rows.append([int(v) for v in ln.split()])
+    for ln in lines[1 + h:]:
+        parts = ln.split()
+        cases.append((parts[0], *map(int, parts[1:5]), [int(v) for v in parts[5:]]))
+    return np.array(rows, dtype=np.uint8), cases
+
+
+def rect_sum(ih, x_lo, x_hi, y_lo, y_hi):
+    """Sum over x in (x_lo, x_hi], y in (y_lo, y_hi] from an inclusive prefix table."""
+    def at(x, y):
+        return 0 if (x < 0 or y < 0) else ih[y][x]
+    return at(x_hi, y_hi) - at(x_lo, y_hi) - at(x_hi, y_lo) + at(x_lo, y_lo)
+
+
+def exact_ih(bins, b, weight):
+    """Eq. 2 in Python integers: prefix sums of [bin == b] * weight(x, y)."""
+    h, w = bins.shape
+    ih = [[0] * w for _ in range(h)]
+    for y in range(h):
+        run = 0
+        for x in range(w):
+            if bins[y, x] == b:
+                run += weight(x, y)
+            ih[y][x] = run + (ih[y - 1][x] if y > 0 else 0)
+    return ih
+
+
+def faulhaber_even(r, k):
+    """sum_{d=-r..r} d^(2k) for k = 0, 1, 2 (closed forms)."""
+    if k == 0:
+        return 2 * r + 1
+    if k == 1:
+        return r * (r + 1) * (2 * r + 1) // 3
+    if k == 2:
+        return r * (r + 1) * (2 * r + 1) * (3 * r * r + 3 * r - 1) // 15
+    raise ValueError(k)
+
+
+# ----------------------------------------------------------------------------
+# quantiser and integral histograms
+# ----------------------------------------------------------------------------
+def test_quantize_bin_edges():
+    v8 = np.arange(256, dtype=np.uint8)[None, :]
+    b = O.quantize(v8, 8, 16)[0]
+    assert b[0] == 0 and b[15] == 0 and b[16] == 1 and b[255] == 15
+    assert np.all(np.bincount(b, minlength=16) == 16)
+    v16 = np.array([[0, 1023, 1024, 65535]], dtype=np.uint16)
+    assert list(O.quantize(v16, 16, 64)[0]) == [0, 0, 1, 63]
+    # non-power-of-two bin count still gives equal-width bins
+    b24 = O.quantize(v8, 8, 24)[0]
+    assert b24.max() == 23 and np.all(np.diff(b24.astype(int)) >= 0)
+    counts = np.bincount(b24, minlength=24)
+    assert counts.min() >= 10 and counts.max() <= 11
+
+
+def test_plain_ih_matches_counts():
+    rng = np.random.default_rng(5)
+    bins = rng.integers(0, 4, size=(7, 9)).astype(np.uint8)
+    ih = O.plain_ih(bins, 4)
+    assert np.array_equal(ih[:, -1, -1], np.bincount(bins.ravel(), minlength=4))
+    for b in range(4):
+        for y in range(7):
+            for x in range(9):
+                assert ih[b, y, x] == int((bins[: y + 1, : x + 1] == b).sum())
+        assert np.array_equal(O.weighted_ih(bins, b, 0, 0, 64).astype(np.int64), ih[b])
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+@pytest.mark.parametrize("p,q", [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (4, 4), (3, 2)])
+def test_weighted_ih_exact_in_ring(bits, p, q):
+    rng = np.random.default_rng(11 + p + 7 * q)
+    bins = rng.integers(0, 3, size=(6, 8)).astype(np.uint8)
+    for b in range(3):
+        ref = exact_ih(bins, b, lambda x, y: x ** p * y ** q)
+        got = O.weighted_ih(bins, b, p, q, bits)
+        mod = 1 << bits
+        for y in range(6):
+            for x in range(8):
+                assert int(got[y, x]) == ref[y][x] % mod
+
+
+def test_weighted_ih_wraps_exactly_on_large_coordinates():
+    # x^4 y^4 prefix sums overflow 64 bits by far at these coordinates; the
+    # oracle must return the exact value reduced mod 2^64.
+    rng = np.random.default_rng(3)
+    H, W = 40, 300
+    bins = rng.integers(0, 2, size=(H, W)).astype(np.uint8)
+    got = O.weighted_ih(bins, 1, 4, 4, 64)
+    ys, xs = np.nonzero(bins == 1)
+    for (x, y) in [(299, 39), (150, 20), (0, 0), (299, 0)]:
+        sel = (xs <= x) & (ys <= y)
+        exact = sum(int(a) ** 4 * int(c) ** 4 for a, c in zip(xs[sel], ys[sel]))
+        assert int(got[y, x]) == exact % (1 << 64)
+
+
+# ----------------------------------------------------------------------------
+# brute-force local histograms
+# ----------------------------------------------------------------------------
+def test_hand_fixture():
+    bins, cases = read_hand_fixture("hand_5x5.txt")
+    for kind, w, h, xc, yc, expect in cases:
+        K = O.kernel_weights(kind, w, h)
+        U = O.hist_at(bins, 3, K, [xc], [yc])[0]
+        assert np.array_equal(U, np.array(expect, dtype=np.float64)), (kind, w, h)
+
+
+def test_uniform_kernel_is_plain_histogram():
+    rng = np.random.default_rng(8)
+    bins = rng.integers(0, 6, size=(23, 31)).astype(np.uint8)
+    K = O.kernel_weights("plain", 7, 5)
+    U = O.hist_rect(bins, 6, K, 3, 2, 31 - 6, 23 - 4)
+    for yc in range(2, 23 - 2):
+        for xc in range(3, 31 - 3):
+            win = bins[yc - 2: yc + 3, xc - 3: xc + 4]
+            assert np.array_equal(U[yc - 2, xc - 3], np.bincount(win.ravel(), minlength=6))
+
+
+@pytest.mark.parametrize("w,h", [(3, 3), (5, 9), (21, 7), (31, 31)])
+def test_bin_mass_is_closed_form_everywhere(w, h):
+    rng = np.random.default_rng(w * 100 + h)
+    H, W = h + 12, w + 15
+    bins = rng.integers(0, 5, size=(H, W)).astype(np.uint8)
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    x0, y0, nx, ny = O.valid_centres(H, W, w, h)
+    closed = {
+        "plain": w * h,
+        "manhattan": h * rx * rx + w * ry * ry,
+        "euclidean": (h * rx * (2 * rx + 1) * (2 * rx - 1) // 3
+                      + w * ry * (2 * ry + 1) * (2 * ry - 1) // 3),
+    }
+    for kind, M in closed.items():
+        U = O.hist_rect(bins, 5, O.kernel_weights(kind, w, h), x0, y0, nx, ny)
+        assert np.all(U.sum(-1) == M), kind
+    # Gaussian approximant: M = (sum_i c_i S_2i(rx) / rx^2i) * (same for y)
+    def axis_mass(r, sigma):
+        c = O.gauss_fit(r, sigma, 2)
+        return sum(ci * faulhaber_even(r, i) / float(r) ** (2 * i) for i, ci in enumerate(c))
+    Mg = axis_mass(rx, 0.25 * w) * axis_mass(ry, 0.25 * h)
+    U = O.hist_rect(bins, 5, O.kernel_weights("gaussian", w, h), x0, y0, nx, ny)
+    np.testing.assert_allclose(U.sum(-1), Mg, rtol=1e-12)
+
+
+def test_manhattan_config1_mass_value():
+    # the 31 x 31 Manhattan window has total weight 31*15^2 * 2 = 13950
+    assert O.kernel_weights("manhattan", 31, 31).sum() == 13950
+
+
+@pytest.mark.parametrize("kind", O.KINDS)
+def test_constant_image(kind):
+    bins = np.full((20, 25), 3, dtype=np.uint8)
+    K = O.kernel_weights(kind, 9, 7)
+    H = O.normalise(O.hist_rect(bins, 5, K, 4, 3, 25 - 8, 20 - 6))
+    e = np.zeros(5)
+    e[3] = 1.0
+    assert np.all(H == e)
+    q = O.target_hist(bins, 5, K, 10, 10)
+    L = O.likelihood_map(bins, 5, K, q)
+    assert np.all(L == 1.0)
+
+
+@pytest.mark.parametrize("kind", O.KINDS)
+def test_likelihood_is_one_at_target_centre(kind):
+    img = np.random.default_rng(1).integers(0, 256, size=(128, 128)).astype(np.uint8)
+    bins = O.quantize(img, 8, 16)
+    K = O.kernel_weights(kind, 31, 31)
+    q = O.target_hist(bins, 16, K, 64, 64)
+    L = O.likelihood_map(bins, 16, K, q)
+    assert abs(L[64 - 15, 64 - 15] - 1.0) < 1e-12
+    assert L.max() <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("kind", O.KINDS)
+def test_mirror_invariance(kind):
+    rng = np.random.default_rng(21)
+    bins = rng.integers(0, 7, size=(30, 40)).astype(np.uint8)
+    w, h = 11, 9
+    K = O.kernel_weights(kind, w, h)
+    x0, y0, nx, ny = O.valid_centres(30, 40, w, h)
+    U = O.hist_rect(bins, 7, K, x0, y0, nx, ny)
+    Ux = O.hist_rect(np.ascontiguousarray(bins[:, ::-1]), 7, K, x0, y0, nx, ny)
+    Uy = O.hist_rect(np.ascontiguousarray(bins[::-1, :]), 7, K, x0, y0, nx, ny)
+    np.testing.assert_allclose(Ux, U[:, ::-1], rtol=1e-14, atol=1e-12)
+    np.testing.assert_allclose(Uy, U[::-1, :], rtol=1e-14, atol=1e-12)
+
+
+def test_exhaustive_binary_3x3():
+    # all 512 binary 3x3 windows: U(1) is the sum of the hand-written
+    # weight table over the set pixels.
+    table = {"plain": [[1, 1, 1], [1, 1, 1], [1, 1, 1]],
+             "manhattan": [[0, 1, 0], [1, 2, 1], [0, 1, 0]],
+             "euclidean": [[0, 1, 0], [1, 2, 1], [0, 1, 0]]}
+    masks = np.array(list(itertools.product([0, 1], repeat=9)), dtype=np.uint8)
+    # tile the 512 windows side by side with a 1-pixel gap so each is one centre
+    bins = np.zeros((3, 512 * 4), dtype=np.uint8)
+    for i, m in enumerate(masks):
+        bins[:, 4 * i: 4 * i + 3] = m.reshape(3, 3)
+    cx = np.arange(512) * 4 + 1
+    cy = np.ones(512, dtype=np.int64)
+    for kind, t in table.items():
+        U = O.hist_at(bins, 2, O.kernel_weights(kind, 3, 3), cx, cy)
+        expect = masks.reshape(512, 3, 3) * np.array(t)[None]
+        assert np.array_equal(U[:, 1], expect.reshape(512, 9).sum(1)), kind
+        assert np.all(U.sum(1) == np.array(t).sum())
+
+
+# ----------------------------------------------------------------------------
+# the paper's decomposition, evaluated exactly, reproduces brute force
+# ----------------------------------------------------------------------------
+def swih_manhattan_quadrants(bins, B, w, h, xc, yc):
+    """Sec. 2.1 with four directional weighted IHs (weights +-x +-y, Eq. 2)
+    and the plain IH: each quadrant's local histogram from its own IH,
+    translated from the centre, then summed. Python integers."""
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    X0, X1, X2 = xc - rx - 1, xc, xc + rx
+    Y0, Y1, Y2 = yc - ry - 1, yc, yc + ry
+    # quadrant: (x range, y range, weight function, constant after translation)
+    quads = [
+        ((X0, X1), (Y0, Y1), lambda x, y: x + y, rx + ry - xc - yc),     # TL, rises to SE
+        ((X1, X2), (Y0, Y1), lambda x, y: -x + y, rx + ry + xc - yc),    # TR, rises to SW
+        ((X0, X1), (Y1, Y2), lambda x, y: x - y, rx + ry - xc + yc),     # BL, rises to NE
+        ((X1, X2), (Y1, Y2), lambda x, y: -x - y, rx + ry + xc + yc),    # BR, rises to NW
+    ]
+    U = []
+    for b in range(B):
+        plain = exact_ih(bins, b, lambda x, y: 1)
+        total = 0
+        for (xa, xb), (ya, yb), wdir, const in quads:
+            ihw = exact_ih(bins, b, wdir)
+            total += const * rect_sum(plain, xa, xb, ya, yb) + rect_sum(ihw, xa, xb, ya, yb)
+        U.append(total)
+    return U
+
+
+def swih_polynomial(bins, B, w, h, xc, yc, coef):
+    """U(b) = sum_{i,j} coef[i][j] * S_ij(b), where S_ij = sum over the window of
+    dx^i dy^j [bin = b] comes from the monomial IHs x^k y^l (Eq. 2) by the
+    binomial translation to the centre. Python integers."""
+    from math import comb
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    X0, X2, Y0, Y2 = xc - rx - 1, xc + rx, yc - ry - 1, yc + ry
+    P = len(coef) - 1
+    Q = len(coef[0]) - 1
+    out = []
+    for b in range(B):
+        R = {}
+        for k in range(P + 1):
+            for l in range(Q + 1):
+                ih = exact_ih(bins, b, lambda x, y, k=k, l=l: x ** k * y ** l)
+                R[k, l] = rect_sum(ih, X0, X2, Y0, Y2)
+        total = 0
+        for i in range(P + 1):
+            for j in range(Q + 1):
+                if coef[i][j] == 0:
+                    continue
+                S = sum(comb(i, k) * comb(j, l) * (-xc) ** (i - k) * (-yc) ** (j - l) * R[k, l]
+                        for k in range(i + 1) for l in range(j + 1))
+                total += coef[i][j] * S
+        out.append(total)
+    return out
+
+
+def test_paper_quadrant_decomposition_is_exact():
+    rng = np.random.default_rng(4)
+    bins = rng.integers(0, 3, size=(12, 14)).astype(np.uint8)
+    for (w, h, xc, yc) in [(5, 5, 6, 6), (7, 3, 3, 1), (9, 11, 9, 5), (3, 3, 1, 1)]:
+        K = O.kernel_weights("manhattan", w, h)
+        ref = O.hist_at(bins, 3, K, [xc], [yc])[0]
+        assert swih_manhattan_quadrants(bins, 3, w, h, xc, yc) == [int(v) for v in ref]
+
+
+def test_polynomial_decomposition_is_exact():
+    rng = np.random.default_rng(9)
+    bins = rng.integers(0, 3, size=(13, 15)).astype(np.uint8)
+    for (w, h, xc, yc) in [(5, 7, 6, 6), (9, 3, 4, 1), (3, 13, 7, 6)]:
+        rx, ry = (w - 1) // 2, (h - 1) // 2
+        # Euclidean: (rx^2 + ry^2) - dx^2 - dy^2
+        coef = [[rx * rx + ry * ry, 0, -1], [0, 0, 0], [-1, 0, 0]]
+        ref = O.hist_at(bins, 3, O.kernel_weights("euclidean", w, h), [xc], [yc])[0]
+        assert swih_polynomial(bins, 3, w, h, xc, yc, coef) == [int(v) for v in ref]
+        # Gaussian approximant: product of the axis polynomials in dx^2/rx^2, dy^2/ry^2
+        cx = O.gauss_fit(rx, 0.25 * w, 2)
+        cy = O.gauss_fit(ry, 0.25 * h, 2)
+        coef = [[0.0] * 5 for _ in range(5)]
+        for i, ci in enumerate(cx):
+            for j, cj in enumerate(cy):
+                coef[2 * i][2 * j] = ci / rx ** (2 * i) * cj / ry ** (2 * j)
+        ref = O.hist_at(bins, 3, O.kernel_weights("gaussian", w, h), [xc], [yc])[0]
+        got = swih_polynomial(bins, 3, w, h, xc, yc, coef)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# the Gaussian approximant
+# ----------------------------------------------------------------------------
+def test_gauss_fit_interpolates_when_exactly_determined():
+    # r = 1: t in {0, 1}, degree capped at 1 -> the line through both samples;
+    # r = 2: t in {0, 1/4, 1}, degree 2 -> the parabola through all three.
+    for r, sigma in [(1, 0.75), (2, 1.25)]:
+        c = O.gauss_fit(r, sigma, 2)
+        assert len(c) == min(2, r) + 1
+        for d in range(0, r + 1):
+            t = d * d / (r * r)
+            val = sum(ci * t ** i for i, ci in enumerate(c))
+            assert abs(val - np.exp(-d * d / (2 * sigma * sigma))) < 1e-13
+
+
+@pytest.mark.parametrize("r", [3, 10, 20, 40, 63])
+def test_gauss_fit_normal_equations(r):
+    # least squares <=> the residual is orthogonal to every basis column
+    sigma = 0.25 * (2 * r + 1)
+    c = O.gauss_fit(r, sigma, 2)
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    t = d * d / (r * r)
+    A = np.stack([np.ones_like(t), t, t * t], 1)
+    resid = A @ c - np.exp(-d * d / (2 * sigma * sigma))
+    assert np.abs(A.T @ resid).max() < 1e-11 * len(d)
+    # any perturbation of c increases the squared residual
+    base = float(resid @ resid)
+    for k in range(3):
+        for eps in (1e-4, -1e-4):
+            c2 = c.copy()
+            c2[k] += eps
+            r2 = A @ c2 - np.exp(-d * d / (2 * sigma * sigma))
+            assert float(r2 @ r2) > base
+
+
+def test_gauss_approximant_distance_from_true_gaussian():
+    # reported, not a paper value: the degree-2 approximant stays within a few
+    # percent of the Gaussian it replaces at the benchmark's window sizes
+    for w in (21, 41, 81):
+        err = np.abs(O.kernel_weights("gaussian", w, w) - O.true_gaussian(w, w)).max()
+        assert err < 0.05, (w, err)
