@@ -1,0 +1,186 @@
+/*
+ * swih.h -- C ABI of the GB300 library for spatially weighted local
+ * histograms in O(1) per window (SWIH, arXiv 1705.03524).
+ *
+ * The pipeline (Sec. 1 steps (1)-(5), Fig. 2):
+ *   quantise pixels into B bins (the quantiser Q of Sec. 2.1)
+ *   -> one weighted integral histogram per bin and weight term (Eq. 2)
+ *   -> for every window centre, rectangle sums from the 3 x 3 lattice of
+ *      window corners, translated to the centre and combined into the
+ *      kernel-weighted histogram, normalised by the kernel's total weight
+ *      (which is the same at every location, Sec. 2.1)
+ *   -> Bhattacharyya coefficient against a target histogram (the sliding
+ *      window matching of Sec. 2 / Fig. 3, which the paper leaves unnamed).
+ *
+ * Conventions shared by every call:
+ *   - x is the column, y the row; images are row-major.
+ *   - A window is win_w x win_h pixels, both odd and >= 3, with half sizes
+ *     rx = (win_w-1)/2, ry = (win_h-1)/2. A centre (xc, yc) is valid when its
+ *     whole window lies inside the image: rx <= xc < W-rx, ry <= yc < H-ry.
+ *     The valid centres form a (H-win_h+1) x (W-win_w+1) map.
+ *   - "d_" pointers are device pointers owned by the caller; the library
+ *     never frees them. A plan owns its own workspace (bins, integral
+ *     histograms, scan state) from swih_plan until swih_destroy.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Calls only enqueue work; they never synchronise the stream,
+ *     except swih_plan / swih_destroy (allocation) and swih_sync_status.
+ *   - Every call returns a swih_status. Argument errors are detected on the
+ *     host before anything is enqueued. swih_last_error gives a message.
+ *   - A plan is not thread-safe: one host thread at a time per plan. Work
+ *     enqueued on different streams against the same plan must be ordered
+ *     by the caller (build before gather).
+ */
+#ifndef SWIH_H
+#define SWIH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum swih_status {
+    SWIH_OK = 0,
+    SWIH_ERR_INVALID_ARG = 1, /* a size, pointer, window or enum out of range */
+    SWIH_ERR_UNSUPPORTED = 2, /* valid request outside what this build serves */
+    SWIH_ERR_OOM = 3,         /* device allocation failed */
+    SWIH_ERR_BUDGET = 4,      /* workspace larger than hbm_budget_bytes */
+    SWIH_ERR_CUDA = 5,        /* a CUDA runtime call failed (message has the name) */
+    SWIH_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (scan look-back) */
+} swih_status;
+
+typedef enum swih_pixel_type { SWIH_PIXEL_U8 = 0, SWIH_PIXEL_U16 = 1 } swih_pixel_type;
+
+/* Spatial kernels K(dx, dy), dx = x - xc, dy = y - yc (Fig. 1):
+ *   PLAIN      K = 1 (Porikli's local histogram)
+ *   MANHATTAN  K = (rx-|dx|) + (ry-|dy|): Eq. 1's city-block distance taken
+ *              from its corner value, zero at the window corners, largest at
+ *              the centre; linear in each quadrant (Sec. 2.1, Fig. 4(b))
+ *   EUCLIDEAN  K = (rx^2-dx^2) + (ry^2-dy^2): the same on the squared
+ *              Euclidean distance (the paper gives no formula)
+ *   GAUSSIAN   K = Px(dx^2/rx^2) * Py(dy^2/ry^2), P the least-squares
+ *              polynomial of degree min(D, r) fitted to exp(-d^2/(2 s^2)) on
+ *              d = -r..r, s = gauss_sigma_frac * window side (the paper names
+ *              the Gaussian without a decomposition)                         */
+typedef enum swih_kernel {
+    SWIH_KERNEL_PLAIN = 0,
+    SWIH_KERNEL_MANHATTAN = 1,
+    SWIH_KERNEL_EUCLIDEAN = 2,
+    SWIH_KERNEL_GAUSSIAN = 3
+} swih_kernel;
+
+#define SWIH_KERNEL_BIT(k) (1u << (unsigned)(k))
+
+/* Element type of the integral histograms. The weights x^p y^q are integers,
+ * so every integral histogram is kept exactly in the ring of integers modulo
+ * 2^32 or 2^64 (wrap-around arithmetic). Rectangle sums, translation to the
+ * centre and kernel combination are ring operations, so every window's
+ * result is exact whenever its true value fits the ring.
+ *   AUTO    RING32 when every requested kernel's total window weight at the
+ *           largest window is below 2^32 and no Gaussian is requested,
+ *           else RING64
+ *   RING32  4-byte elements (rejected with UNSUPPORTED if not exact)
+ *   RING64  8-byte elements                                                 */
+typedef enum swih_precision {
+    SWIH_PREC_AUTO = 0,
+    SWIH_PREC_RING32 = 1,
+    SWIH_PREC_RING64 = 2
+} swih_precision;
+
+typedef struct swih_plan_desc {
+    int32_t height;            /* H >= 3 */
+    int32_t width;             /* W, 3 <= W <= 8192 */
+    int64_t pitch_bytes;       /* input row stride in bytes, >= W * pixel size */
+    int32_t pixel_type;        /* swih_pixel_type */
+    int32_t bitdepth;          /* significant bits: 1..8 (U8) or 1..16 (U16) */
+    int32_t bins;              /* B, 1..256 */
+    uint32_t kernel_mask;      /* OR of SWIH_KERNEL_BIT(k) the plan must serve */
+    int32_t gauss_degree;      /* D of the Gaussian approximant, 1 or 2 (0: 2) */
+    double gauss_sigma_frac;   /* Gaussian sigma / window side (0: 0.25) */
+    int32_t max_win_w;         /* largest window the plan serves (odd, <= W) */
+    int32_t max_win_h;         /* (odd, <= H) */
+    int32_t precision;         /* swih_precision */
+    int32_t band_rows;         /* rows per scan band (0: automatic) */
+    uint64_t hbm_budget_bytes; /* reject plans whose workspace exceeds it (0: no limit) */
+} swih_plan_desc;
+
+typedef struct swih_plan_s *swih_plan_t;
+
+/* Workspace a plan with this description would allocate (host only, no CUDA
+ * call). Used for admission against a memory budget. */
+swih_status swih_plan_workspace_bytes(const swih_plan_desc *desc, uint64_t *bytes);
+
+/* Validate the description, choose the term set and ring, allocate the
+ * workspace on the current device. *out receives the plan (NULL on error). */
+swih_status swih_plan(const swih_plan_desc *desc, swih_plan_t *out);
+
+/* Steps (1)-(2) of Sec. 1: quantise the image (pixel_type, pitch_bytes from the
+ * plan) and build every weighted integral histogram the plan's kernels need:
+ *   IH_pq(x, y, b) = sum_{i<=x, j<=y} [Q(f(i,j)) = b] * i^p * j^q   (Eq. 2)
+ * d_image: device pointer to H rows of pitch_bytes; read-only.
+ * Device-side waits are bounded; a wait that gives up is reported by the next
+ * swih_sync_status as SWIH_ERR_TIMEOUT. */
+swih_status swih_build_ih(swih_plan_t plan, const void *d_image, void *stream);
+
+/* Steps (3)-(5) of Sec. 1 for a rectangle of centres: the normalised kernel-
+ * weighted histogram H_c(b) = U_c(b) / M, U_c(b) the kernel-weighted count of
+ * bin b in the window and M the kernel's total window weight.
+ * Centres xc in [cx0, cx0+ncx), yc in [cy0, cy0+ncy), all valid.
+ * d_hist: float32 [ncy][ncx][B], written. Requires a prior swih_build_ih. */
+swih_status swih_local_hist(swih_plan_t plan, int kernel, int win_w, int win_h, int cx0,
+                            int cy0, int ncx, int ncy, float *d_hist, void *stream);
+
+/* Steps (3)-(5) of Sec. 1 plus the matching of Sec. 2 / Fig. 3 for every valid
+ * centre: L(c) = sum_b sqrt(H_c(b) * q(b)) (Bhattacharyya coefficient).
+ * d_target: float32 [B], q(b) >= 0, summing to 1 (not checked on the device).
+ * d_map: float32 [H-win_h+1][W-win_w+1], written, row-major. */
+swih_status swih_likelihood(swih_plan_t plan, int kernel, int win_w, int win_h,
+                            const float *d_target, float *d_map, void *stream);
+
+/* Wait for the stream, then report the first device-side error the plan
+ * recorded since the last call (SWIH_ERR_TIMEOUT) and clear it. */
+swih_status swih_sync_status(swih_plan_t plan, void *stream);
+
+/* Free the plan's workspace (synchronises the device). NULL is a no-op. */
+swih_status swih_destroy(swih_plan_t plan);
+
+/* Message for the last error on this plan (plan = NULL: the last error of
+ * swih_plan / swih_plan_workspace_bytes on this host thread). Never NULL. */
+const char *swih_last_error(swih_plan_t plan);
+
+/* Introspection, for tests and tools. All pointers stay owned by the plan. */
+typedef struct swih_plan_info {
+    int32_t height, width, bins;
+    int32_t elem_bytes;      /* 4 (RING32) or 8 (RING64) */
+    int32_t n_terms;         /* number of weight terms x^p y^q */
+    int32_t term_p[32];      /* term t has weight x^term_p[t] * y^term_q[t] */
+    int32_t term_q[32];
+    const void *d_bins;      /* uint8 [H][bins_pitch] */
+    int64_t bins_pitch;      /* bytes */
+    const void *d_ih;        /* plane (t, b) starts at element (t*B + b) * plane_elems */
+    int64_t ih_pitch;        /* elements per integral-histogram row */
+    int64_t plane_elems;     /* elements per plane (H * ih_pitch) */
+    int32_t band_rows;       /* rows per scan band */
+    int32_t n_bands;
+    uint64_t workspace_bytes;
+} swih_plan_info;
+
+swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
+
+/* Fault injection for tests (host-set, no device fault): with
+ * SWIH_INJECT_STALL_SCAN_TILE the next swih_build_ih runs its scan with the
+ * first band of the first (bin, term) chain never publishing its column sums,
+ * and with a short wait bound. The bands below it give up waiting after the
+ * bound, mark themselves failed and return; the next swih_sync_status then
+ * returns SWIH_ERR_TIMEOUT and the plan's integral histograms are invalid until
+ * the next swih_build_ih. The injection applies to one build only.
+ * what = 0 clears a pending injection. */
+#define SWIH_INJECT_STALL_SCAN_TILE 1
+swih_status swih_debug_inject(swih_plan_t plan, int what);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWIH_H */

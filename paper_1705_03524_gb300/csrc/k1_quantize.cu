@@ -1,0 +1,84 @@
+// K1: quantisation Q of Sec. 2.1 (named after Eq. 2): pixel value -> bin.
+//
+//   b = floor(min(v, 2^bitdepth - 1) * B / 2^bitdepth)   (equal-width bins)
+//
+// One thread per 16 consecutive pixels of a row. With a 16-byte aligned image
+// a u8 chunk is one 16-byte load and a u16 chunk two; the 16 bins leave as one
+// 16-byte store. HBM-bound: (pixel bytes + 1) bytes per pixel.
+#include "swih_internal.h"
+
+namespace swih {
+namespace {
+
+__device__ __forceinline__ uint32_t bin_of(uint32_t v, uint32_t vmax, uint32_t B, int bitdepth)
+{
+    v = v > vmax ? vmax : v;
+    return (v * B) >> bitdepth;
+}
+
+template <int PB>
+__global__ void __launch_bounds__(256) quantize_kernel(QuantParams p)
+{
+    const int chunks_per_row = (p.W + 15) >> 4;
+    const long long n_chunks = (long long)chunks_per_row * p.H;
+    const uint32_t vmax = (1u << p.bitdepth) - 1u;
+    const uint32_t B = (uint32_t)p.B;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_chunks;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(c / chunks_per_row);
+        const int x0 = (int)(c - (long long)y * chunks_per_row) << 4;
+        const uint8_t *row = p.image + (int64_t)y * p.pitch;
+        uint32_t v[16];
+        if (p.vec && x0 + 16 <= p.W) {
+            if (PB == 1) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(row + x0);
+                const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+            } else {
+                const uint4 u0 = *reinterpret_cast<const uint4 *>(row + 2 * x0);
+                const uint4 u1 = *reinterpret_cast<const uint4 *>(row + 2 * x0 + 16);
+                const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = (w[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int x = x0 + i;
+                if (x < p.W) {
+                    v[i] = PB == 1 ? (uint32_t)row[x]
+                                   : (uint32_t)reinterpret_cast<const uint16_t *>(row)[x];
+                } else {
+                    v[i] = 0;
+                }
+            }
+        }
+        uint32_t o[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[i >> 2] |= bin_of(v[i], vmax, B, p.bitdepth) << (8 * (i & 3));
+        *reinterpret_cast<uint4 *>(p.bins + (int64_t)y * p.bins_pitch + x0) =
+            make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_quantize(const QuantParams &p, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long n_chunks = (long long)((p.W + 15) / 16) * p.H;
+    long long blocks = (n_chunks + 255) / 256;
+    const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (p.pixel_bytes == 1)
+        quantize_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(p);
+    else
+        quantize_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace swih

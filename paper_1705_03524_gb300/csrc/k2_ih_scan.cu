@@ -1,0 +1,315 @@
+// K2: weighted integral histograms (Eq. 2), one per bin b and weight term x^p y^q:
+//
+//   IH_pq(x, y, b) = sum_{i<=x, j<=y} [bin(i, j) = b] * i^p * j^q
+//
+// kept exactly in the ring of integers mod 2^32 or 2^64 (type T wraps).
+//
+// Factorisation used: with the column sums
+//   cs_q(x, y) = sum_{j<=y} [bin(x, j) = b] * j^q,
+// every term sharing q is a row prefix sum of a column scaled by x^p:
+//   IH_pq(x, y) = sum_{i<=x} i^p * cs_q(i, y).
+// So one "chain" per (b, q) carries cs_q down the image, and each row of the
+// chain emits one block-wide row scan per p.
+//
+// Work decomposition: the image is cut into horizontal bands of band_rows
+// full-width rows. A CTA takes one (chain, band) tile in ticket order (an
+// atomic counter), so every tile it may wait for has already started.
+// The column carry into a band comes from a single-pass decoupled look-back
+// over the bands above it (Merrill & Garland's scheme, carried on W-wide state
+// vectors instead of scalars):
+//   1. sum the band's own rows into a per-column aggregate, publish it
+//      (flag AGGREGATE; band 0 publishes its INCLUSIVE value directly);
+//   2. walk back over earlier bands, adding aggregates until an INCLUSIVE
+//      vector is found; every wait is bounded and a wait that gives up marks
+//      the tile ERROR and sets the plan's status word;
+//   3. publish carry + aggregate as INCLUSIVE;
+//   4. sweep the band again, carrying cs_q in registers, and write each row of
+//      every term of the chain with a block-wide scan (thread-serial over E
+//      columns, warp shuffles, then a cross-warp pass through shared memory).
+// Output writes are full rows, coalesced, each IH element written once; the
+// bin image (1 byte per pixel) is read twice per tile and stays in L2.
+#include "swih_internal.h"
+
+namespace swih {
+namespace {
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T ring_pow(T base, int e)
+{
+    T r = 1;
+    for (int i = 0; i < e; ++i) r *= base;
+    return r;
+}
+
+// E consecutive bins starting at column x0 (x0 multiple of E, row 16-byte aligned)
+template <int E>
+__device__ __forceinline__ void load_bins(const uint8_t *row, int x0, uint8_t (&v)[E])
+{
+    if constexpr (E == 4) {
+        const uint32_t u = *reinterpret_cast<const uint32_t *>(row + x0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = (uint8_t)(u >> (8 * i));
+    } else if constexpr (E == 8) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(row + x0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = (uint8_t)(u.x >> (8 * i));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[4 + i] = (uint8_t)(u.y >> (8 * i));
+    } else {
+#pragma unroll
+        for (int c = 0; c < E / 16; ++c) {
+            const uint4 u = *reinterpret_cast<const uint4 *>(row + x0 + 16 * c);
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[16 * c + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+        }
+    }
+}
+
+// store E consecutive ring elements (16-byte aligned) with 16-byte vector stores
+template <typename T, int E>
+__device__ __forceinline__ void store_row(T *dst, const T (&v)[E])
+{
+    constexpr int per = 16 / sizeof(T);
+#pragma unroll
+    for (int c = 0; c < E / per; ++c) {
+        if constexpr (sizeof(T) == 4) {
+            reinterpret_cast<uint4 *>(dst)[c] =
+                make_uint4((uint32_t)v[4 * c], (uint32_t)v[4 * c + 1], (uint32_t)v[4 * c + 2],
+                           (uint32_t)v[4 * c + 3]);
+        } else {
+            reinterpret_cast<ulonglong2 *>(dst)[c] =
+                make_ulonglong2((unsigned long long)v[2 * c], (unsigned long long)v[2 * c + 1]);
+        }
+    }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void store_state(T *dst, const T (&v)[E])
+{
+    constexpr int per = 16 / sizeof(T);
+#pragma unroll
+    for (int c = 0; c < E / per; ++c) {
+        if constexpr (sizeof(T) == 4) {
+            __stcg(reinterpret_cast<uint4 *>(dst) + c,
+                   make_uint4((uint32_t)v[4 * c], (uint32_t)v[4 * c + 1], (uint32_t)v[4 * c + 2],
+                              (uint32_t)v[4 * c + 3]));
+        } else {
+            __stcg(reinterpret_cast<ulonglong2 *>(dst) + c,
+                   make_ulonglong2((unsigned long long)v[2 * c], (unsigned long long)v[2 * c + 1]));
+        }
+    }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void add_state(const T *src, T (&acc)[E])
+{
+    constexpr int per = 16 / sizeof(T);
+#pragma unroll
+    for (int c = 0; c < E / per; ++c) {
+        if constexpr (sizeof(T) == 4) {
+            const uint4 u = __ldcg(reinterpret_cast<const uint4 *>(src) + c);
+            acc[4 * c] += u.x;
+            acc[4 * c + 1] += u.y;
+            acc[4 * c + 2] += u.z;
+            acc[4 * c + 3] += u.w;
+        } else {
+            const ulonglong2 u = __ldcg(reinterpret_cast<const ulonglong2 *>(src) + c);
+            acc[2 * c] += u.x;
+            acc[2 * c + 1] += u.y;
+        }
+    }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
+{
+    __shared__ int s_ticket;
+    __shared__ int s_flag;
+    __shared__ T s_warp[2][32];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+
+    if (tid == 0) s_ticket = atomicAdd(p.ticket, 1);
+    __syncthreads();
+    const int ticket = s_ticket;
+    const int n_chains = p.B * p.n_q;
+    const int band = ticket / n_chains;
+    const int chain = ticket - band * n_chains;
+    const int b = chain / p.n_q;
+    const int qi = chain - b * p.n_q;
+    const int q = p.q_val[qi];
+    const int y_begin = band * p.band_rows;
+    const int y_end = min(y_begin + p.band_rows, p.H);
+    const int x0 = tid * E;
+    const bool has_cols = x0 < p.W;               // any real column in this thread
+    const bool in_pitch = x0 < p.ih_pitch;        // chunk lies inside a stored row
+    const uint8_t bb = (uint8_t)b;
+    if (ticket == p.stall_tile && band == 0) return;  // injected stall: publish nothing
+
+    // ---- 1. band aggregate of [bin == b] * y^q per column
+    T agg[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) agg[e] = 0;
+    if (has_cols) {
+        for (int y = y_begin; y < y_end; ++y) {
+            const T yq = ring_pow<T>((T)y, q);
+            uint8_t v[E];
+            load_bins<E>(p.bins + (int64_t)y * p.bins_pitch, x0, v);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (v[e] == bb && x0 + e < p.W) agg[e] += yq;
+        }
+    }
+
+    const int64_t state_row = ((int64_t)chain * p.n_bands + band) * p.ih_pitch;
+    int *my_flag = p.flags + (int64_t)chain * p.n_bands + band;
+    if (in_pitch) store_state<T, E>((band == 0 ? (T *)p.incl : (T *)p.agg) + state_row + x0, agg);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        st_release(my_flag, band == 0 ? kFlagInclusive : kFlagAggregate);
+    }
+
+    // ---- 2. look back over the bands above for the column carry
+    T carry[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) carry[e] = 0;
+    bool failed = false;
+    if (band > 0) {
+        int j = band - 1;
+        while (true) {
+            if (tid == 0) {
+                const int *fp = p.flags + (int64_t)chain * p.n_bands + j;
+                int f = ld_acquire(fp);
+                long long it = 0;
+                while (f == kFlagEmpty) {
+                    if (++it > p.spin_limit) {
+                        f = kFlagError;
+                        atomicOr(p.status, kStatusTimeout);
+                        break;
+                    }
+                    __nanosleep(64);
+                    f = ld_acquire(fp);
+                }
+                s_flag = f;
+            }
+            __syncthreads();
+            const int f = s_flag;
+            __syncthreads();
+            if (f == kFlagError) {
+                failed = true;
+                break;
+            }
+            const T *src = (f == kFlagInclusive ? (const T *)p.incl : (const T *)p.agg) +
+                           ((int64_t)chain * p.n_bands + j) * p.ih_pitch;
+            if (in_pitch) add_state<T, E>(src + x0, carry);
+            if (f == kFlagInclusive || j == 0) break;
+            --j;
+        }
+        // ---- 3. publish the inclusive column sums of this band
+        if (!failed && in_pitch) {
+            T inc[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) inc[e] = carry[e] + agg[e];
+            store_state<T, E>((T *)p.incl + state_row + x0, inc);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release(my_flag, failed ? kFlagError : kFlagInclusive);
+        }
+    }
+    if (failed) return;  // uniform over the block (decided from s_flag)
+
+    // ---- 4. sweep the band: column sums in registers, one row scan per term
+    T cs[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) cs[e] = carry[e];
+    const int n_p = p.p_count[qi];
+    int parity = 0;
+    for (int y = y_begin; y < y_end; ++y) {
+        if (has_cols) {
+            const T yq = ring_pow<T>((T)y, q);
+            uint8_t v[E];
+            load_bins<E>(p.bins + (int64_t)y * p.bins_pitch, x0, v);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (v[e] == bb && x0 + e < p.W) cs[e] += yq;
+        }
+        for (int k = 0; k < n_p; ++k) {
+            const int pe = p.p_val[qi][k];
+            T val[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) val[e] = ring_pow<T>((T)(x0 + e), pe) * cs[e];
+#pragma unroll
+            for (int e = 1; e < E; ++e) val[e] += val[e - 1];
+            const T tot = val[E - 1];
+            T inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T n = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += n;
+            }
+            if (lane == 31) s_warp[parity][warp] = inc;
+            __syncthreads();
+            T off = inc - tot;
+            for (int w = 0; w < warp; ++w) off += s_warp[parity][w];
+#pragma unroll
+            for (int e = 0; e < E; ++e) val[e] += off;
+            if (in_pitch) {
+                T *row = (T *)p.ih + ((int64_t)p.term[qi][k] * p.B + b) * p.plane +
+                         (int64_t)y * p.ih_pitch;
+                store_row<T, E>(row + x0, val);
+            }
+            parity ^= 1;
+        }
+    }
+}
+
+template <typename T, int E>
+cudaError_t launch_typed(const ScanParams &p, int threads, cudaStream_t s)
+{
+    const long long tiles = (long long)p.B * p.n_q * p.n_bands;
+    ih_scan_kernel<T, E><<<(unsigned)tiles, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_e(const ScanParams &p, int E, int threads, cudaStream_t s)
+{
+    switch (E) {
+    case 4: return launch_typed<T, 4>(p, threads, s);
+    case 8: return launch_typed<T, 8>(p, threads, s);
+    case 16: return launch_typed<T, 16>(p, threads, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads, cudaStream_t s)
+{
+    if (threads < 32 || threads > kMaxScanThreads || threads % 32) return cudaErrorInvalidValue;
+    if (elem_bytes == 4) return launch_e<uint32_t>(p, E, threads, s);
+    if (elem_bytes == 8) return launch_e<unsigned long long>(p, E, threads, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace swih

@@ -1,0 +1,580 @@
+// Host side of the C ABI declared in include/swih.h: plan construction,
+// argument validation, kernel parameters and launches. No compute happens
+// here; every step of the pipeline runs in the CUDA kernels K1-K3.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/swih.h"
+#include "swih_internal.h"
+
+using namespace swih;
+
+struct swih_plan_s {
+    swih_plan_desc desc;
+    int elem_bytes = 4;
+    int n_terms = 0;
+    int term_p[kMaxTerms];
+    int term_q[kMaxTerms];
+    int term_index[5][5];  // [p][q] -> term or -1
+    // scan chains: distinct q values and their p lists
+    int n_q = 0;
+    int q_val[kMaxQ];
+    int p_count[kMaxQ];
+    int p_val[kMaxQ][kMaxP];
+    int gauss_degree = 2;
+    double sigma_frac = 0.25;
+    int64_t bins_pitch = 0, ih_pitch = 0, plane = 0;
+    int band_rows = 0, n_bands = 0;
+    int scan_E = 4, scan_threads = 32;
+    uint64_t off_ih = 0, off_agg = 0, off_incl = 0, off_flags = 0, total = 0;
+    uint64_t flags_bytes = 0;
+    char *d_mem = nullptr;
+    uint32_t *d_status = nullptr;
+    int device = 0;
+    bool built = false;
+    int inject = 0;  // SWIH_INJECT_* for the next swih_build_ih
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+swih_status fail(swih_plan_s *plan, swih_status st, const std::string &msg)
+{
+    if (plan)
+        plan->err = msg;
+    else
+        g_err = msg;
+    return st;
+}
+
+swih_status cuda_fail(swih_plan_s *plan, const char *what, cudaError_t e)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(plan, e == cudaErrorMemoryAllocation ? SWIH_ERR_OOM : SWIH_ERR_CUDA, m);
+}
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+inline bool odd_window(int w) { return w >= 3 && (w & 1); }
+
+// total kernel weight over a w x h window, for the integer-valued kernels
+long double int_kernel_mass(int kernel, int w, int h)
+{
+    const long double rx = (w - 1) / 2, ry = (h - 1) / 2;
+    switch (kernel) {
+    case SWIH_KERNEL_PLAIN: return (long double)w * h;
+    case SWIH_KERNEL_MANHATTAN: return h * rx * rx + w * ry * ry;
+    case SWIH_KERNEL_EUCLIDEAN:
+        return h * rx * (2 * rx + 1) * (2 * rx - 1) / 3 + w * ry * (2 * ry + 1) * (2 * ry - 1) / 3;
+    default: return 0;
+    }
+}
+
+int gauss_axis_degree(int r, int D) { return std::max(0, std::min(D, r)); }
+
+// Least-squares fit of P(t) = sum_i c_i t^i (i <= D) to exp(-d^2 / (2 s^2)) on the
+// integer samples d = -r..r with t = d^2 / r^2: normal equations solved by
+// Gaussian elimination with partial pivoting, in double.
+bool gauss_fit(int r, double sigma, int D, double *c)
+{
+    const int n = D + 1;
+    double A[3][4] = {};
+    for (int d = -r; d <= r; ++d) {
+        const double t = (double)d * d / ((double)r * r);
+        const double y = std::exp(-(double)d * d / (2.0 * sigma * sigma));
+        const double pw[3] = {1.0, t, t * t};
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) A[i][j] += pw[i] * pw[j];
+            A[i][n] += pw[i] * y;
+        }
+    }
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r2 = col + 1; r2 < n; ++r2)
+            if (std::fabs(A[r2][col]) > std::fabs(A[piv][col])) piv = r2;
+        if (A[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int k = 0; k <= n; ++k) std::swap(A[piv][k], A[col][k]);
+        for (int r2 = col + 1; r2 < n; ++r2) {
+            const double f = A[r2][col] / A[col][col];
+            for (int k = col; k <= n; ++k) A[r2][k] -= f * A[col][k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = A[i][n];
+        for (int k = i + 1; k < n; ++k) s -= A[i][k] * c[k];
+        c[i] = s / A[i][i];
+    }
+    return true;
+}
+
+struct GaussAxis {
+    int D = 0;
+    double beta[3] = {0, 0, 0};  // Bernstein coefficients of the fitted polynomial
+    double mass = 0;             // sum over d = -r..r of P(d^2 / r^2)
+};
+
+bool gauss_axis(int r, double sigma, int D_req, GaussAxis &g, std::string &why)
+{
+    g.D = gauss_axis_degree(r, D_req);
+    double c[3] = {0, 0, 0};
+    if (g.D < 1) {
+        why = "Gaussian window half-size must be >= 1";
+        return false;
+    }
+    if (!gauss_fit(r, sigma, g.D, c)) {
+        why = "Gaussian least-squares system is singular";
+        return false;
+    }
+    // power basis -> Bernstein basis: beta_i = sum_{k<=i} C(i,k)/C(D,k) c_k
+    if (g.D == 1) {
+        g.beta[0] = c[0];
+        g.beta[1] = c[0] + c[1];
+    } else {
+        g.beta[0] = c[0];
+        g.beta[1] = c[0] + 0.5 * c[1];
+        g.beta[2] = c[0] + c[1] + c[2];
+    }
+    for (int i = 0; i <= g.D; ++i)
+        if (!(g.beta[i] >= 0.0)) {
+            why = "Gaussian approximant has a negative Bernstein coefficient for this window";
+            return false;
+        }
+    g.mass = 0.0;
+    for (int d = -r; d <= r; ++d) {
+        const double t = (double)d * d / ((double)r * r);
+        g.mass += c[0] + t * (c[1] + t * c[2]);
+    }
+    return true;
+}
+
+// Largest Bernstein moment of the Gaussian path, w h rx^2Dx ry^2Dy: it must fit
+// the 64-bit ring for the per-window integers to be exact.
+long double gauss_bound(int w, int h, int D)
+{
+    const int rx = (w - 1) / 2, ry = (h - 1) / 2;
+    const int dx = gauss_axis_degree(rx, D), dy = gauss_axis_degree(ry, D);
+    return (long double)w * h * std::pow((long double)rx, 2 * dx) * std::pow((long double)ry, 2 * dy);
+}
+
+swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
+{
+    if (!d) return fail(nullptr, SWIH_ERR_INVALID_ARG, "desc is NULL");
+    if (d->height < 3 || d->width < 3)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "image must be at least 3 x 3");
+    if (d->width > 8192)
+        return fail(nullptr, SWIH_ERR_UNSUPPORTED, "image width above 8192 is not supported");
+    if (d->height > (1 << 24))
+        return fail(nullptr, SWIH_ERR_UNSUPPORTED, "image height above 2^24 is not supported");
+    if (d->pixel_type != SWIH_PIXEL_U8 && d->pixel_type != SWIH_PIXEL_U16)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "pixel_type must be U8 or U16");
+    const int pb = d->pixel_type == SWIH_PIXEL_U8 ? 1 : 2;
+    if (d->bitdepth < 1 || d->bitdepth > 8 * pb)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "bitdepth out of range for the pixel type");
+    if (d->pitch_bytes < (int64_t)d->width * pb)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "pitch_bytes smaller than a row");
+    if (d->pixel_type == SWIH_PIXEL_U16 && (d->pitch_bytes & 1))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "pitch_bytes of a U16 image must be even");
+    if (d->bins < 1 || d->bins > 256)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "bins must be in [1, 256]");
+    if (d->kernel_mask == 0 || (d->kernel_mask & ~0xFu))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "kernel_mask must name kernels 0..3");
+    if (!odd_window(d->max_win_w) || !odd_window(d->max_win_h))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "max window sides must be odd and >= 3");
+    if (d->max_win_w > d->width || d->max_win_h > d->height)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "max window larger than the image");
+    if (d->precision < SWIH_PREC_AUTO || d->precision > SWIH_PREC_RING64)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "precision out of range");
+    if (d->band_rows < 0) return fail(nullptr, SWIH_ERR_INVALID_ARG, "band_rows must be >= 0");
+    const int D = d->gauss_degree == 0 ? 2 : d->gauss_degree;
+    if (D < 1 || D > 2) return fail(nullptr, SWIH_ERR_UNSUPPORTED, "gauss_degree must be 1 or 2");
+    const double sf = d->gauss_sigma_frac == 0.0 ? 0.25 : d->gauss_sigma_frac;
+    if (!(sf > 0.0) || !std::isfinite(sf))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "gauss_sigma_frac must be positive");
+
+    pl->desc = *d;
+    pl->gauss_degree = D;
+    pl->sigma_frac = sf;
+    bool mark[5][5] = {};
+    const bool want_man = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_MANHATTAN);
+    const bool want_euc = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_EUCLIDEAN);
+    const bool want_gau = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_GAUSSIAN);
+    mark[0][0] = true;
+    if (want_man || want_euc) mark[1][0] = mark[0][1] = true;
+    if (want_euc) mark[2][0] = mark[0][2] = true;
+    if (want_gau) {
+        const int kx = 2 * gauss_axis_degree((d->max_win_w - 1) / 2, D);
+        const int ky = 2 * gauss_axis_degree((d->max_win_h - 1) / 2, D);
+        for (int p = 0; p <= kx; ++p)
+            for (int q = 0; q <= ky; ++q) mark[p][q] = true;
+    }
+    // canonical order: grouped by q (one scan chain per q), p ascending
+    for (auto &row : pl->term_index)
+        for (int &v : row) v = -1;
+    pl->n_terms = 0;
+    pl->n_q = 0;
+    for (int q = 0; q < 5; ++q) {
+        int cnt = 0;
+        for (int p = 0; p < 5; ++p) {
+            if (!mark[p][q]) continue;
+            pl->term_p[pl->n_terms] = p;
+            pl->term_q[pl->n_terms] = q;
+            pl->p_val[pl->n_q][cnt++] = p;
+            pl->term_index[p][q] = pl->n_terms++;
+        }
+        if (cnt) {
+            pl->q_val[pl->n_q] = q;
+            pl->p_count[pl->n_q] = cnt;
+            ++pl->n_q;
+        }
+    }
+
+    // ring: every window result must be exact in it
+    long double need = 0;
+    for (int k = SWIH_KERNEL_PLAIN; k <= SWIH_KERNEL_EUCLIDEAN; ++k)
+        if (d->kernel_mask & SWIH_KERNEL_BIT(k))
+            need = std::max(need, int_kernel_mass(k, d->max_win_w, d->max_win_h));
+    const bool fits32 = !want_gau && need < 4294967296.0L;
+    if (want_gau && gauss_bound(d->max_win_w, d->max_win_h, D) >= 18446744073709551616.0L)
+        return fail(nullptr, SWIH_ERR_UNSUPPORTED,
+                    "Gaussian window too large for exact 64-bit moments (w*h*rx^2D*ry^2D >= 2^64)");
+    if (d->precision == SWIH_PREC_RING32 && !fits32)
+        return fail(nullptr, SWIH_ERR_UNSUPPORTED,
+                    "RING32 is not exact for these kernels and windows; use AUTO or RING64");
+    pl->elem_bytes = (d->precision == SWIH_PREC_RING64 || !fits32) ? 8 : 4;
+
+    // layout
+    const int W = d->width, H = d->height;
+    pl->bins_pitch = round_up(W, 128);
+    pl->ih_pitch = round_up(W, 32);
+    pl->plane = (int64_t)H * pl->ih_pitch;
+    pl->band_rows = d->band_rows > 0 ? std::min(d->band_rows, H) : std::min(32, H);
+    pl->n_bands = (H + pl->band_rows - 1) / pl->band_rows;
+    // columns per scan thread: the fewest that keep the block at <= 512 threads
+    int E = 4;
+    while ((W + E - 1) / E > 512) E *= 2;
+    pl->scan_E = E;
+    pl->scan_threads = (int)round_up((W + E - 1) / E, 32);
+    const uint64_t n_chains = (uint64_t)d->bins * pl->n_q;
+    const uint64_t es = (uint64_t)pl->elem_bytes;
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t at = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return at;
+    };
+    take((uint64_t)H * pl->bins_pitch);  // bins at offset 0
+    pl->off_ih = take((uint64_t)pl->n_terms * d->bins * pl->plane * es);
+    pl->off_agg = take(n_chains * pl->n_bands * pl->ih_pitch * es);
+    pl->off_incl = take(n_chains * pl->n_bands * pl->ih_pitch * es);
+    pl->flags_bytes = (n_chains * pl->n_bands + 1) * sizeof(int);  // flags + ticket
+    pl->off_flags = take(pl->flags_bytes);
+    take(sizeof(uint32_t) * 64);  // status word
+    pl->total = off;
+    if (d->hbm_budget_bytes && pl->total > d->hbm_budget_bytes) {
+        char m[160];
+        std::snprintf(m, sizeof m, "workspace %llu bytes exceeds the budget of %llu bytes",
+                      (unsigned long long)pl->total, (unsigned long long)d->hbm_budget_bytes);
+        return fail(nullptr, SWIH_ERR_BUDGET, m);
+    }
+    return SWIH_OK;
+}
+
+swih_status check_window(swih_plan_s *pl, int kernel, int w, int h)
+{
+    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_GAUSSIAN)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "unknown kernel");
+    if (!(pl->desc.kernel_mask & SWIH_KERNEL_BIT(kernel)))
+        return fail(pl, SWIH_ERR_INVALID_ARG, "kernel not in the plan's kernel_mask");
+    if (!odd_window(w) || !odd_window(h))
+        return fail(pl, SWIH_ERR_INVALID_ARG, "window sides must be odd and >= 3");
+    if (w > pl->desc.max_win_w || h > pl->desc.max_win_h)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "window larger than the plan's max window");
+    if (!pl->built) return fail(pl, SWIH_ERR_INVALID_ARG, "swih_build_ih has not been called");
+    return SWIH_OK;
+}
+
+swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams &g, int &kind)
+{
+    std::memset(&g, 0, sizeof g);
+    g.ih = pl->d_mem + pl->off_ih;
+    g.plane = pl->plane;
+    g.pitch = pl->ih_pitch;
+    g.B = pl->desc.bins;
+    g.H = pl->desc.height;
+    g.W = pl->desc.width;
+    g.rx = (w - 1) / 2;
+    g.ry = (h - 1) / 2;
+    g.t1 = pl->term_index[0][0];
+    g.tx = pl->term_index[1][0];
+    g.ty = pl->term_index[0][1];
+    g.txx = pl->term_index[2][0];
+    g.tyy = pl->term_index[0][2];
+    for (int k = 0; k < 5; ++k)
+        for (int l = 0; l < 5; ++l) g.tg[k][l] = pl->term_index[k][l];
+    if (kernel == SWIH_KERNEL_GAUSSIAN) {
+        GaussAxis ax, ay;
+        std::string why;
+        if (!gauss_axis(g.rx, pl->sigma_frac * w, pl->gauss_degree, ax, why) ||
+            !gauss_axis(g.ry, pl->sigma_frac * h, pl->gauss_degree, ay, why))
+            return fail(pl, SWIH_ERR_UNSUPPORTED, why);
+        g.gdx = ax.D;
+        g.gdy = ay.D;
+        const unsigned long long rx2 = (unsigned long long)g.rx * g.rx, ry2 = (unsigned long long)g.ry * g.ry;
+        g.rx2 = rx2;
+        g.rx4 = rx2 * rx2;
+        g.ry2 = ry2;
+        g.ry4 = ry2 * ry2;
+        const double mass = ax.mass * ay.mass;
+        const double sx = std::pow((double)g.rx, 2 * ax.D), sy = std::pow((double)g.ry, 2 * ay.D);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                g.gamma[i][j] = (float)(ax.beta[i] * ay.beta[j] / (sx * sy * mass));
+        kind = kGatherGaussian;
+    } else {
+        g.inv_mass = (float)(1.0L / int_kernel_mass(kernel, w, h));
+        kind = kernel == SWIH_KERNEL_PLAIN ? kGatherPlain
+               : kernel == SWIH_KERNEL_MANHATTAN ? kGatherManhattan
+                                                 : kGatherEuclidean;
+    }
+    return SWIH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+swih_status swih_plan_workspace_bytes(const swih_plan_desc *desc, uint64_t *bytes)
+{
+    if (!bytes) return fail(nullptr, SWIH_ERR_INVALID_ARG, "bytes is NULL");
+    swih_plan_s tmp;
+    swih_plan_desc d2;
+    if (desc) {
+        d2 = *desc;
+        d2.hbm_budget_bytes = 0;  // report the size even when over budget
+    }
+    const swih_status st = build_layout(desc ? &d2 : nullptr, &tmp);
+    if (st != SWIH_OK) return st;
+    *bytes = tmp.total;
+    return SWIH_OK;
+}
+
+swih_status swih_plan(const swih_plan_desc *desc, swih_plan_t *out)
+{
+    if (!out) return fail(nullptr, SWIH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    swih_plan_s *pl = new swih_plan_s();
+    swih_status st = build_layout(desc, pl);
+    if (st != SWIH_OK) {
+        delete pl;
+        return st;
+    }
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(nullptr, "cudaGetDevice", e);
+    }
+    e = cudaMalloc(reinterpret_cast<void **>(&pl->d_mem), pl->total);
+    if (e != cudaSuccess) {
+        delete pl;
+        cudaGetLastError();
+        return cuda_fail(nullptr, "cudaMalloc(workspace)", e);
+    }
+    pl->d_status = reinterpret_cast<uint32_t *>(pl->d_mem + pl->total - sizeof(uint32_t) * 64);
+    e = cudaMemset(pl->d_status, 0, sizeof(uint32_t) * 64);
+    if (e == cudaSuccess) e = cudaMemset(pl->d_mem + pl->off_flags, 0, pl->flags_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(pl->d_mem);
+        delete pl;
+        return cuda_fail(nullptr, "cudaMemset(status)", e);
+    }
+    *out = pl;
+    return SWIH_OK;
+}
+
+swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    if (!d_image) return fail(pl, SWIH_ERR_INVALID_ARG, "d_image is NULL");
+    const swih_plan_desc &d = pl->desc;
+    if (d.pixel_type == SWIH_PIXEL_U16 && (reinterpret_cast<uintptr_t>(d_image) & 1))
+        return fail(pl, SWIH_ERR_INVALID_ARG, "a U16 image must be 2-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    QuantParams qp;
+    qp.image = static_cast<const uint8_t *>(d_image);
+    qp.pitch = d.pitch_bytes;
+    qp.H = d.height;
+    qp.W = d.width;
+    qp.B = d.bins;
+    qp.bitdepth = d.bitdepth;
+    qp.bins = reinterpret_cast<uint8_t *>(pl->d_mem);
+    qp.bins_pitch = pl->bins_pitch;
+    qp.pixel_bytes = d.pixel_type == SWIH_PIXEL_U8 ? 1 : 2;
+    qp.vec = (d.pitch_bytes % 16 == 0) && (reinterpret_cast<uintptr_t>(d_image) % 16 == 0);
+    cudaError_t e = launch_quantize(qp, s);
+    if (e != cudaSuccess) return cuda_fail(pl, "quantize launch", e);
+
+    e = cudaMemsetAsync(pl->d_mem + pl->off_flags, 0, pl->flags_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(pl, "cudaMemsetAsync(scan flags)", e);
+
+    ScanParams sp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.bins = qp.bins;
+    sp.bins_pitch = pl->bins_pitch;
+    sp.ih = pl->d_mem + pl->off_ih;
+    sp.ih_pitch = pl->ih_pitch;
+    sp.plane = pl->plane;
+    sp.agg = pl->d_mem + pl->off_agg;
+    sp.incl = pl->d_mem + pl->off_incl;
+    sp.flags = reinterpret_cast<int *>(pl->d_mem + pl->off_flags);
+    sp.ticket = sp.flags + (int64_t)d.bins * pl->n_q * pl->n_bands;
+    sp.status = pl->d_status;
+    sp.H = d.height;
+    sp.W = d.width;
+    sp.B = d.bins;
+    sp.band_rows = pl->band_rows;
+    sp.n_bands = pl->n_bands;
+    sp.n_q = pl->n_q;
+    for (int i = 0; i < pl->n_q; ++i) {
+        sp.q_val[i] = pl->q_val[i];
+        sp.p_count[i] = pl->p_count[i];
+        for (int k = 0; k < pl->p_count[i]; ++k) {
+            sp.p_val[i][k] = pl->p_val[i][k];
+            sp.term[i][k] = pl->term_index[pl->p_val[i][k]][pl->q_val[i]];
+        }
+    }
+    sp.spin_limit = 1LL << 22;  // with 64 ns sleeps: well under a few seconds
+    sp.stall_tile = -1;
+    if (pl->inject == SWIH_INJECT_STALL_SCAN_TILE) {
+        sp.stall_tile = 0;        // chain 0, band 0 never publishes
+        sp.spin_limit = 1LL << 12;
+        pl->inject = 0;
+    }
+    e = launch_ih_scan(sp, pl->elem_bytes, pl->scan_E, pl->scan_threads, s);
+    if (e != cudaSuccess) return cuda_fail(pl, "ih_scan launch", e);
+    pl->built = true;
+    return SWIH_OK;
+}
+
+swih_status swih_local_hist(swih_plan_t pl, int kernel, int win_w, int win_h, int cx0, int cy0,
+                            int ncx, int ncy, float *d_hist, void *stream)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    swih_status st = check_window(pl, kernel, win_w, win_h);
+    if (st != SWIH_OK) return st;
+    if (!d_hist) return fail(pl, SWIH_ERR_INVALID_ARG, "d_hist is NULL");
+    const int rx = (win_w - 1) / 2, ry = (win_h - 1) / 2;
+    const int W = pl->desc.width, H = pl->desc.height;
+    if (ncx < 0 || ncy < 0) return fail(pl, SWIH_ERR_INVALID_ARG, "negative centre count");
+    if (ncx == 0 || ncy == 0) return SWIH_OK;
+    if (cx0 < rx || cy0 < ry || (int64_t)cx0 + ncx > W - rx || (int64_t)cy0 + ncy > H - ry)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "centre rectangle has windows outside the image");
+    GatherParams g;
+    int kind = 0;
+    st = make_gather(pl, kernel, win_w, win_h, g, kind);
+    if (st != SWIH_OK) return st;
+    g.cx0 = cx0;
+    g.cy0 = cy0;
+    g.ncx = ncx;
+    g.ncy = ncy;
+    g.hist = d_hist;
+    const cudaError_t e = launch_gather(g, kind, pl->elem_bytes, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(pl, "gather launch", e);
+    return SWIH_OK;
+}
+
+swih_status swih_likelihood(swih_plan_t pl, int kernel, int win_w, int win_h, const float *d_target,
+                            float *d_map, void *stream)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    swih_status st = check_window(pl, kernel, win_w, win_h);
+    if (st != SWIH_OK) return st;
+    if (!d_target || !d_map) return fail(pl, SWIH_ERR_INVALID_ARG, "d_target or d_map is NULL");
+    GatherParams g;
+    int kind = 0;
+    st = make_gather(pl, kernel, win_w, win_h, g, kind);
+    if (st != SWIH_OK) return st;
+    g.cx0 = (win_w - 1) / 2;
+    g.cy0 = (win_h - 1) / 2;
+    g.ncx = pl->desc.width - win_w + 1;
+    g.ncy = pl->desc.height - win_h + 1;
+    g.target = d_target;
+    g.map = d_map;
+    const cudaError_t e = launch_gather(g, kind, pl->elem_bytes, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(pl, "gather launch", e);
+    return SWIH_OK;
+}
+
+swih_status swih_sync_status(swih_plan_t pl, void *stream)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(pl, "cudaStreamSynchronize", e);
+    uint32_t word = 0;
+    e = cudaMemcpy(&word, pl->d_status, sizeof word, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(pl, "cudaMemcpy(status)", e);
+    if (word) {
+        e = cudaMemset(pl->d_status, 0, sizeof word);
+        if (e != cudaSuccess) return cuda_fail(pl, "cudaMemset(status)", e);
+        if (word & kStatusTimeout)
+            return fail(pl, SWIH_ERR_TIMEOUT, "integral-histogram scan: a look-back wait gave up");
+    }
+    return SWIH_OK;
+}
+
+swih_status swih_destroy(swih_plan_t pl)
+{
+    if (!pl) return SWIH_OK;
+    cudaError_t e = cudaSuccess;
+    if (pl->d_mem) e = cudaFree(pl->d_mem);
+    delete pl;
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaFree", e);
+    return SWIH_OK;
+}
+
+const char *swih_last_error(swih_plan_t pl)
+{
+    if (pl) return pl->err.c_str();
+    return g_err.c_str();
+}
+
+swih_status swih_debug_inject(swih_plan_t pl, int what)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    if (what != 0 && what != SWIH_INJECT_STALL_SCAN_TILE)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "unknown injection");
+    pl->inject = what;
+    return SWIH_OK;
+}
+
+swih_status swih_plan_get_info(swih_plan_t pl, swih_plan_info *info)
+{
+    if (!pl || !info) return fail(pl, SWIH_ERR_INVALID_ARG, "plan or info is NULL");
+    std::memset(info, 0, sizeof *info);
+    info->height = pl->desc.height;
+    info->width = pl->desc.width;
+    info->bins = pl->desc.bins;
+    info->elem_bytes = pl->elem_bytes;
+    info->n_terms = pl->n_terms;
+    for (int t = 0; t < pl->n_terms; ++t) {
+        info->term_p[t] = pl->term_p[t];
+        info->term_q[t] = pl->term_q[t];
+    }
+    info->d_bins = pl->d_mem;
+    info->bins_pitch = pl->bins_pitch;
+    info->d_ih = pl->d_mem ? pl->d_mem + pl->off_ih : nullptr;
+    info->ih_pitch = pl->ih_pitch;
+    info->plane_elems = pl->plane;
+    info->band_rows = pl->band_rows;
+    info->n_bands = pl->n_bands;
+    info->workspace_bytes = pl->total;
+    return SWIH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the CUDA translation units of libswih.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swih {
+
+constexpr int kMaxQ = 5;          // distinct y-exponents q (Gaussian D=2: 0..4)
+constexpr int kMaxP = 5;          // x-exponents p per q
+constexpr int kMaxTerms = 25;
+constexpr int kMaxScanThreads = 512;
+
+// decoupled look-back tile states
+constexpr int kFlagEmpty = 0;
+constexpr int kFlagAggregate = 1;
+constexpr int kFlagInclusive = 2;
+constexpr int kFlagError = 3;
+
+// bits of the plan's device status word
+constexpr uint32_t kStatusTimeout = 1u;
+
+// ---------------------------------------------------------------- K1 quantise
+struct QuantParams {
+    const uint8_t *image;
+    int64_t pitch;       // bytes
+    int H, W;
+    int B, bitdepth;
+    uint8_t *bins;
+    int64_t bins_pitch;  // bytes, multiple of 16
+    int pixel_bytes;     // 1 or 2
+    int vec;             // 1 when every 16-pixel chunk can use aligned vector loads
+};
+cudaError_t launch_quantize(const QuantParams &p, cudaStream_t s);
+
+// ---------------------------------------------------------------- K2 scan
+// One chain per (bin b, y-exponent q); a chain's bands are scanned top to
+// bottom with decoupled look-back on per-column state vectors.
+struct ScanParams {
+    const uint8_t *bins;
+    int64_t bins_pitch;  // bytes
+    void *ih;            // planes [t][b][H][ih_pitch]
+    int64_t ih_pitch;    // elements
+    int64_t plane;       // elements per plane
+    void *agg;           // [chain][band][ih_pitch] band aggregates
+    void *incl;          // [chain][band][ih_pitch] inclusive column sums
+    int *flags;          // [chain][band]
+    int *ticket;         // tile counter (zeroed before each launch)
+    uint32_t *status;
+    int H, W, B;
+    int band_rows, n_bands;
+    int n_q;
+    int q_val[kMaxQ];
+    int p_count[kMaxQ];
+    int p_val[kMaxQ][kMaxP];
+    int term[kMaxQ][kMaxP];
+    long long spin_limit;
+    int stall_tile;      // ticket of a tile that never publishes (fault injection), else -1
+};
+// E = columns per thread, threads = ceil(W/E) rounded to a warp multiple
+cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------- K3 gather
+enum GatherKind { kGatherPlain = 0, kGatherManhattan = 1, kGatherEuclidean = 2, kGatherGaussian = 3 };
+
+struct GatherParams {
+    const void *ih;
+    int64_t plane, pitch;   // elements
+    int B, H, W;
+    int rx, ry;
+    int cx0, cy0, ncx, ncy; // centre rectangle
+    // term (plane-group) indices
+    int t1, tx, ty, txx, tyy;
+    int tg[5][5];           // Gaussian: term index of x^k y^l
+    int gdx, gdy;           // Gaussian: fitted degree per axis (1 or 2)
+    unsigned long long rx2, rx4, ry2, ry4;  // r^2, r^4 per axis (ring constants)
+    float gamma[3][3];      // Gaussian: beta_x[i] beta_y[j] / (rx^2Dx ry^2Dy M)
+    float inv_mass;         // 1 / M (plain, Manhattan, Euclidean)
+    const float *target;    // [B] or null
+    float *map;             // [ncy][ncx] or null
+    float *hist;            // [ncy][ncx][B] or null
+};
+cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
+
+}  // namespace swih

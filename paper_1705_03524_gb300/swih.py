@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libswih (C ABI in include/swih.h).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name, which enqueues CUDA kernels; nothing is computed in Python.
+Pointers may be given as integers or as objects with ``data_ptr()`` (torch
+tensors); streams as integers, ``None`` (the legacy default stream) or objects
+with a ``cuda_stream`` attribute (``torch.cuda.Stream``).
+
+Importing this module loads the shared library and fails loudly if it has not
+been built (``paper_1705_03524_gb300.build.build()``): there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+SWIH_OK = 0
+SWIH_ERR_INVALID_ARG = 1
+SWIH_ERR_UNSUPPORTED = 2
+SWIH_ERR_OOM = 3
+SWIH_ERR_BUDGET = 4
+SWIH_ERR_CUDA = 5
+SWIH_ERR_TIMEOUT = 6
+
+SWIH_PIXEL_U8 = 0
+SWIH_PIXEL_U16 = 1
+
+SWIH_KERNEL_PLAIN = 0
+SWIH_KERNEL_MANHATTAN = 1
+SWIH_KERNEL_EUCLIDEAN = 2
+SWIH_KERNEL_GAUSSIAN = 3
+
+SWIH_PREC_AUTO = 0
+SWIH_PREC_RING32 = 1
+SWIH_PREC_RING64 = 2
+
+KERNELS = {"plain": SWIH_KERNEL_PLAIN, "manhattan": SWIH_KERNEL_MANHATTAN,
+           "euclidean": SWIH_KERNEL_EUCLIDEAN, "gaussian": SWIH_KERNEL_GAUSSIAN}
+
+
+def kernel_bit(k: int) -> int:
+    return 1 << k
+
+
+class SwihError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"swih status {status}: {message}")
+        self.status = status
+
+
+class swih_plan_desc(ctypes.Structure):
+    _fields_ = [
+        ("height", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("pitch_bytes", ctypes.c_int64),
+        ("pixel_type", ctypes.c_int32),
+        ("bitdepth", ctypes.c_int32),
+        ("bins", ctypes.c_int32),
+        ("kernel_mask", ctypes.c_uint32),
+        ("gauss_degree", ctypes.c_int32),
+        ("gauss_sigma_frac", ctypes.c_double),
+        ("max_win_w", ctypes.c_int32),
+        ("max_win_h", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("band_rows", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+    ]
+
+
+class swih_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("height", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("bins", ctypes.c_int32),
+        ("elem_bytes", ctypes.c_int32),
+        ("n_terms", ctypes.c_int32),
+        ("term_p", ctypes.c_int32 * 32),
+        ("term_q", ctypes.c_int32 * 32),
+        ("d_bins", ctypes.c_void_p),
+        ("bins_pitch", ctypes.c_int64),
+        ("d_ih", ctypes.c_void_p),
+        ("ih_pitch", ctypes.c_int64),
+        ("plane_elems", ctypes.c_int64),
+        ("band_rows", ctypes.c_int32),
+        ("n_bands", ctypes.c_int32),
+        ("workspace_bytes", ctypes.c_uint64),
+    ]
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path}); run paper_1705_03524_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    lib.swih_plan_workspace_bytes.argtypes = [ctypes.POINTER(swih_plan_desc), ctypes.POINTER(ctypes.c_uint64)]
+    lib.swih_plan_workspace_bytes.restype = S
+    lib.swih_plan.argtypes = [ctypes.POINTER(swih_plan_desc), ctypes.POINTER(P)]
+    lib.swih_plan.restype = S
+    lib.swih_build_ih.argtypes = [P, P, P]
+    lib.swih_build_ih.restype = S
+    lib.swih_local_hist.argtypes = [P, I, I, I, I, I, I, I, P, P]
+    lib.swih_local_hist.restype = S
+    lib.swih_likelihood.argtypes = [P, I, I, I, P, P, P]
+    lib.swih_likelihood.restype = S
+    lib.swih_sync_status.argtypes = [P, P]
+    lib.swih_sync_status.restype = S
+    lib.swih_destroy.argtypes = [P]
+    lib.swih_destroy.restype = S
+    lib.swih_last_error.argtypes = [P]
+    lib.swih_last_error.restype = ctypes.c_char_p
+    lib.swih_debug_inject.argtypes = [P, I]
+    lib.swih_debug_inject.restype = S
+    lib.swih_plan_get_info.argtypes = [P, ctypes.POINTER(swih_plan_info)]
+    lib.swih_plan_get_info.restype = S
+    return lib
+
+
+LIB = _load()
+LIB_PATH = _build.LIB
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/swih.h."""
+    hdr = os.path.join(_build.ROOT, "include", "swih.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:swih_status|const char \*)\s*(swih_\w+)\s*\(", text, re.M)))
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _check(status: int, plan=None):
+    if status != SWIH_OK:
+        msg = LIB.swih_last_error(plan).decode(errors="replace")
+        raise SwihError(status, msg)
+
+
+def make_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8, bitdepth=None,
+              bins=16, kernels=("manhattan",), gauss_degree=2, gauss_sigma_frac=0.25,
+              max_win=(3, 3), precision=SWIH_PREC_AUTO, band_rows=0, hbm_budget_bytes=0):
+    pb = 1 if pixel_type == SWIH_PIXEL_U8 else 2
+    mask = 0
+    for k in kernels:
+        mask |= kernel_bit(KERNELS[k] if isinstance(k, str) else int(k))
+    d = swih_plan_desc()
+    d.height, d.width = int(height), int(width)
+    d.pitch_bytes = int(pitch_bytes if pitch_bytes is not None else width * pb)
+    d.pixel_type = int(pixel_type)
+    d.bitdepth = int(bitdepth if bitdepth is not None else 8 * pb)
+    d.bins = int(bins)
+    d.kernel_mask = mask
+    d.gauss_degree = int(gauss_degree)
+    d.gauss_sigma_frac = float(gauss_sigma_frac)
+    d.max_win_w, d.max_win_h = int(max_win[0]), int(max_win[1])
+    d.precision = int(precision)
+    d.band_rows = int(band_rows)
+    d.hbm_budget_bytes = int(hbm_budget_bytes)
+    return d
+
+
+def swih_plan_workspace_bytes(desc: swih_plan_desc) -> int:
+    out = ctypes.c_uint64(0)
+    _check(LIB.swih_plan_workspace_bytes(ctypes.byref(desc), ctypes.byref(out)))
+    return int(out.value)
+
+
+def swih_plan(desc: swih_plan_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(LIB.swih_plan(ctypes.byref(desc), ctypes.byref(h)))
+    return int(h.value)
+
+
+def swih_build_ih(plan: int, image, stream=None) -> None:
+    _check(LIB.swih_build_ih(plan, _ptr(image), _stream(stream)), plan)
+
+
+def swih_local_hist(plan: int, kernel: int, win_w: int, win_h: int, cx0: int, cy0: int,
+                    ncx: int, ncy: int, hist, stream=None) -> None:
+    _check(LIB.swih_local_hist(plan, int(kernel), win_w, win_h, cx0, cy0, ncx, ncy, _ptr(hist),
+                               _stream(stream)), plan)
+
+
+def swih_likelihood(plan: int, kernel: int, win_w: int, win_h: int, target, out_map,
+                    stream=None) -> None:
+    _check(LIB.swih_likelihood(plan, int(kernel), win_w, win_h, _ptr(target), _ptr(out_map),
+                               _stream(stream)), plan)
+
+
+def swih_sync_status(plan: int, stream=None) -> None:
+    _check(LIB.swih_sync_status(plan, _stream(stream)), plan)
+
+
+def swih_destroy(plan: int) -> None:
+    _check(LIB.swih_destroy(plan))
+
+
+def swih_last_error(plan=None) -> str:
+    return LIB.swih_last_error(plan).decode(errors="replace")
+
+
+SWIH_INJECT_STALL_SCAN_TILE = 1
+
+
+def swih_debug_inject(plan: int, what: int) -> None:
+    _check(LIB.swih_debug_inject(plan, int(what)), plan)
+
+
+def swih_plan_get_info(plan: int) -> swih_plan_info:
+    info = swih_plan_info()
+    _check(LIB.swih_plan_get_info(plan, ctypes.byref(info)), plan)
+    return info
+
+
+class Plan:
+    """Owning wrapper: ``with Plan(desc) as p: p.build_ih(img); p.likelihood(...)``."""
+
+    def __init__(self, desc: swih_plan_desc):
+        self.desc = desc
+        self.handle = swih_plan(desc)
+
+    def build_ih(self, image, stream=None):
+        swih_build_ih(self.handle, image, stream)
+
+    def local_hist(self, kernel, win_w, win_h, cx0, cy0, ncx, ncy, hist, stream=None):
+        k = KERNELS[kernel] if isinstance(kernel, str) else kernel
+        swih_local_hist(self.handle, k, win_w, win_h, cx0, cy0, ncx, ncy, hist, stream)
+
+    def likelihood(self, kernel, win_w, win_h, target, out_map, stream=None):
+        k = KERNELS[kernel] if isinstance(kernel, str) else kernel
+        swih_likelihood(self.handle, k, win_w, win_h, target, out_map, stream)
+
+    def sync_status(self, stream=None):
+        swih_sync_status(self.handle, stream)
+
+    def info(self) -> swih_plan_info:
+        return swih_plan_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            swih_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,292 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+* K1 bins and every K2 integral-histogram plane: bit-exact against the
+  oracle's quantiser and Eq. 2 sums in the same ring (mod 2^32 or 2^64).
+* K3 normalised histograms and likelihoods: max abs error <= 1e-5 against
+  the brute-force oracle (normalised bins and Bhattacharyya coefficients).
+
+Sizes are small enough for the oracle to finish in seconds while spanning
+several scan bands, several warps of centres and ragged tails; the
+benchmark's full-size workload is checked on sampled centres.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import swih_oracle as O  # noqa: E402
+from paper_1705_03524_gb300 import swih as S  # noqa: E402
+from paper_1705_03524_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+DEV = "cuda:0"
+
+
+class _DevView:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 3, "strides": None}
+
+
+def device_rows(ptr, rows, pitch_elems, typestr):
+    """Copy a pitched device array to the host as numpy (rows x pitch)."""
+    t = torch.as_tensor(_DevView(ptr, (rows, pitch_elems), typestr), device=DEV)
+    return t.cpu().numpy()
+
+
+def upload(img: np.ndarray, pitch_bytes=None, offset=0):
+    """Image to the device as raw bytes with an optional row pitch and base offset."""
+    h, w = img.shape
+    pb = img.dtype.itemsize
+    pitch = pitch_bytes or w * pb
+    raw = np.zeros((h, pitch), dtype=np.uint8)
+    raw[:, : w * pb] = img.view(np.uint8).reshape(h, w * pb)
+    buf = torch.zeros(h * pitch + offset + 64, dtype=torch.uint8, device=DEV)
+    buf[offset: offset + h * pitch] = torch.from_numpy(raw.reshape(-1)).to(DEV)
+    return buf, buf.data_ptr() + offset, pitch
+
+
+def make_plan(img, bitdepth, B, kernels, max_win, **kw):
+    h, w = img.shape
+    pt = S.SWIH_PIXEL_U8 if img.dtype == np.uint8 else S.SWIH_PIXEL_U16
+    pitch = kw.pop("pitch_bytes", None)
+    offset = kw.pop("offset", 0)
+    buf, ptr, pitch = upload(img, pitch, offset)
+    desc = S.make_desc(h, w, pitch_bytes=pitch, pixel_type=pt, bitdepth=bitdepth, bins=B,
+                       kernels=kernels, max_win=max_win, **kw)
+    plan = S.Plan(desc)
+    plan.build_ih(ptr)
+    plan.sync_status()
+    return plan, buf
+
+
+def oracle_bins(img, bitdepth, B):
+    vmax = (1 << bitdepth) - 1
+    return O.quantize(np.minimum(img.astype(np.int64), vmax), bitdepth, B)
+
+
+def check_ih(plan, img, bitdepth, B):
+    info = plan.info()
+    H, W = img.shape
+    bins = oracle_bins(img, bitdepth, B)
+    got_bins = device_rows(info.d_bins, H, info.bins_pitch, "|u1")[:, :W]
+    assert np.array_equal(got_bins, bins)
+    bits = 8 * info.elem_bytes
+    ts = "<i4" if info.elem_bytes == 4 else "<i8"
+    udt = np.uint32 if info.elem_bytes == 4 else np.uint64
+    for t in range(info.n_terms):
+        p, q = info.term_p[t], info.term_q[t]
+        for b in range(B):
+            ptr = info.d_ih + (t * B + b) * info.plane_elems * info.elem_bytes
+            got = device_rows(ptr, H, info.ih_pitch, ts)[:, :W].view(udt)
+            ref = O.weighted_ih(bins, b, p, q, bits)
+            if not np.array_equal(got, ref):
+                bad = np.argwhere(got != ref)[0]
+                raise AssertionError(f"IH term x^{p} y^{q} bin {b} differs at {tuple(bad)}")
+    return bins
+
+
+def check_windows(plan, bins, B, kind, w, h, rect=None):
+    H, W = bins.shape
+    K = O.kernel_weights(kind, w, h)
+    x0, y0, nx, ny = O.valid_centres(H, W, w, h)
+    # local histograms over a (sub)rectangle of centres
+    cx0, cy0, ncx, ncy = rect or (x0, y0, nx, ny)
+    hist = torch.empty((ncy, ncx, B), dtype=torch.float32, device=DEV)
+    plan.local_hist(kind, w, h, cx0, cy0, ncx, ncy, hist)
+    ref_h = O.normalise(O.hist_rect(bins, B, K, cx0, cy0, ncx, ncy))
+    err_h = np.abs(hist.cpu().numpy().astype(np.float64) - ref_h).max()
+    assert err_h <= TOL, (kind, w, h, err_h)
+    # likelihood over every valid centre, target = a window histogram
+    tx, ty = x0 + nx // 3, y0 + ny // 2
+    q = O.target_hist(bins, B, K, tx, ty)
+    qd = torch.tensor(q, dtype=torch.float32, device=DEV)
+    m = torch.empty((ny, nx), dtype=torch.float32, device=DEV)
+    plan.likelihood(kind, w, h, qd, m)
+    ref_l = O.likelihood_map(bins, B, K, q)
+    got_l = m.cpu().numpy().astype(np.float64)
+    err_l = np.abs(got_l - ref_l).max()
+    assert err_l <= TOL, (kind, w, h, err_l)
+    plan.sync_status()
+    return err_h, err_l
+
+
+# --------------------------------------------------------------------------- K1 + K2
+IH_CASES = [
+    # name, (H, W), pixel bits, B, kernels, max window, extra plan args
+    ("config1", (128, 128), 8, 16, ("manhattan",), (31, 31), {}),
+    ("ragged_all", (37, 53), 8, 5, ("plain", "manhattan", "euclidean"), (9, 7), dict(band_rows=4)),
+    ("wide_E8", (61, 1100), 8, 3, ("manhattan",), (21, 15), dict(band_rows=8)),
+    ("wide_E16", (16, 4200), 8, 2, ("manhattan",), (15, 5), dict(band_rows=4)),
+    ("plain_2500", (40, 2500), 8, 4, ("plain",), (5, 5), {}),
+    ("gauss_u16", (20, 33), 12, 7, ("gaussian",), (15, 9), dict(band_rows=3)),
+    ("ring64_forced", (45, 70), 8, 6, ("manhattan", "euclidean"), (11, 11),
+     dict(precision=S.SWIH_PREC_RING64, band_rows=5)),
+    ("one_bin", (9, 40), 8, 1, ("manhattan",), (5, 5), dict(band_rows=2)),
+    ("bins256", (33, 64), 8, 256, ("plain",), (3, 3), {}),
+    ("single_band", (24, 96), 8, 4, ("euclidean",), (7, 7), dict(band_rows=100)),
+]
+
+
+def _image(shape, bits, seed):
+    h, w = shape
+    if bits <= 8:
+        return synth.uniform_image(h, w, 8, seed)
+    img = synth.uniform_image(h, w, 16, seed)  # values beyond 'bits' exercise clamping
+    return img
+
+
+@pytest.mark.parametrize("case", IH_CASES, ids=[c[0] for c in IH_CASES])
+def test_bins_and_integral_histograms_bit_exact(case):
+    name, shape, bits, B, kernels, max_win, kw = case
+    img = _image(shape, bits, seed=len(name))
+    plan, _buf = make_plan(img, bits, B, kernels, max_win, **dict(kw))
+    with plan:
+        check_ih(plan, img, bits, B)
+
+
+@pytest.mark.parametrize("pitch_extra,offset", [(0, 0), (7, 0), (64, 0), (3, 1), (0, 5)])
+def test_pitched_and_unaligned_u8_input(pitch_extra, offset):
+    img = synth.uniform_image(29, 77, 8, seed=3)
+    plan, _buf = make_plan(img, 8, 8, ("manhattan",), (9, 9), pitch_bytes=77 + pitch_extra,
+                           offset=offset)
+    with plan:
+        check_ih(plan, img, 8, 8)
+
+
+def test_u16_offset_input():
+    img = synth.uniform_image(21, 45, 16, seed=4)
+    plan, _buf = make_plan(img, 10, 16, ("plain",), (5, 5), pitch_bytes=45 * 2 + 6, offset=2)
+    with plan:
+        check_ih(plan, img, 10, 16)
+
+
+# --------------------------------------------------------------------------- K3
+WIN_CASES = [
+    ("config1", (128, 128), 16, ("manhattan",), [(31, 31)]),
+    ("ragged", (37, 53), 5, ("plain", "manhattan", "euclidean", "gaussian"),
+     [(3, 3), (9, 7), (7, 9), (53, 37), (5, 37), (53, 3)]),
+    ("wide", (30, 1100), 4, ("manhattan", "euclidean", "gaussian"), [(21, 15), (1099, 3)]),
+    ("bins64", (70, 90), 64, ("manhattan", "gaussian"), [(21, 21), (41, 11)]),
+]
+
+
+@pytest.mark.parametrize("case", WIN_CASES, ids=[c[0] for c in WIN_CASES])
+def test_local_hist_and_likelihood_parity(case):
+    name, shape, B, kernels, windows = case
+    H, W = shape
+    img = synth.uniform_image(H, W, 8, seed=10 + len(name))
+    maxw = max(w for w, _ in windows)
+    maxh = max(h for _, h in windows)
+    plan, _buf = make_plan(img, 8, B, kernels, (maxw, maxh), band_rows=8)
+    with plan:
+        bins = oracle_bins(img, 8, B)
+        for kind in kernels:
+            for (w, h) in windows:
+                if kind == "gaussian" and (w * h > 60000):
+                    continue
+                check_windows(plan, bins, B, kind, w, h)
+
+
+def test_sub_rectangle_of_centres():
+    img = synth.uniform_image(50, 60, 8, seed=2)
+    plan, _buf = make_plan(img, 8, 8, ("manhattan", "euclidean"), (11, 11))
+    with plan:
+        bins = oracle_bins(img, 8, 8)
+        check_windows(plan, bins, 8, "manhattan", 11, 9, rect=(7, 6, 13, 1))
+        check_windows(plan, bins, 8, "euclidean", 5, 11, rect=(30, 20, 1, 9))
+
+
+def test_constant_image_gives_delta_histogram():
+    img = np.full((40, 44), 200, dtype=np.uint8)
+    plan, _buf = make_plan(img, 8, 16, ("manhattan", "euclidean", "gaussian"), (15, 15))
+    with plan:
+        for kind in ("manhattan", "euclidean", "gaussian"):
+            hist = torch.empty((40 - 14, 44 - 14, 16), device=DEV)
+            plan.local_hist(kind, 15, 15, 7, 7, 44 - 14, 40 - 14, hist)
+            e = torch.zeros(16, device=DEV)
+            e[200 * 16 // 256] = 1
+            assert (hist - e).abs().max().item() <= TOL
+
+
+def test_window_argument_errors():
+    img = synth.uniform_image(20, 20, 8, seed=1)
+    plan, _buf = make_plan(img, 8, 4, ("manhattan",), (9, 9))
+    with plan:
+        m = torch.empty(400, device=DEV)
+        q = torch.full((4,), 0.25, device=DEV)
+        for args in [("manhattan", 8, 9), ("manhattan", 11, 9), ("euclidean", 5, 5), ("manhattan", 1, 3)]:
+            with pytest.raises(S.SwihError) as ei:
+                plan.likelihood(args[0], args[1], args[2], q, m)
+            assert ei.value.status == S.SWIH_ERR_INVALID_ARG
+        with pytest.raises(S.SwihError):
+            plan.local_hist("manhattan", 9, 9, 3, 4, 5, 5, m)  # window leaves the image
+
+
+def test_injected_stall_reports_timeout_and_recovers():
+    img = synth.uniform_image(64, 96, 8, seed=6)
+    plan, buf = make_plan(img, 8, 4, ("manhattan",), (9, 9), band_rows=8)
+    with plan:
+        S.swih_debug_inject(plan.handle, S.SWIH_INJECT_STALL_SCAN_TILE)
+        plan.build_ih(buf.data_ptr())
+        with pytest.raises(S.SwihError) as ei:
+            plan.sync_status()
+        assert ei.value.status == S.SWIH_ERR_TIMEOUT
+        # the context stays usable: the next build is complete and exact
+        plan.build_ih(buf.data_ptr())
+        plan.sync_status()
+        check_ih(plan, img, 8, 4)
+
+
+# --------------------------------------------------------------------------- full size
+def test_benchmark_workload_sampled_centres():
+    """1024 x 1024 synthetic scene, B = 32, the three weighted kernels at windows
+    21/41/81, in the plan layout the benchmark uses; sampled centres vs oracle,
+    properties (unit mass, L <= 1) at every centre."""
+    cfg = synth.config2()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    bins = oracle_bins(img, 8, B)
+    rng = np.random.default_rng(12)
+    plans = []
+    buf, ptr, pitch = upload(img)
+    for kernels in (("manhattan", "euclidean"), ("gaussian",)):
+        d = S.make_desc(H, W, pitch_bytes=pitch, bins=B, kernels=kernels, max_win=(81, 81))
+        p = S.Plan(d)
+        p.build_ih(ptr)
+        plans.append((kernels, p))
+    tx, ty = cfg["target_centre"]
+    try:
+        for kernels, p in plans:
+            p.sync_status()
+            for kind in kernels:
+                for w in cfg["windows"]:
+                    K = O.kernel_weights(kind, w, w)
+                    q = O.target_hist(bins, B, K, tx, ty)
+                    x0, y0, nx, ny = O.valid_centres(H, W, w, w)
+                    m = torch.empty((ny, nx), device=DEV)
+                    p.likelihood(kind, w, w, torch.tensor(q, dtype=torch.float32, device=DEV), m)
+                    got = m.cpu().numpy()
+                    assert got.max() <= 1 + 1e-5 and got.min() >= 0
+                    cx = rng.integers(x0, x0 + nx, 3000)
+                    cy = rng.integers(y0, y0 + ny, 3000)
+                    cx = np.concatenate([cx, [x0, x0 + nx - 1, x0, x0 + nx - 1, tx]])
+                    cy = np.concatenate([cy, [y0, y0, y0 + ny - 1, y0 + ny - 1, ty]])
+                    ref = O.likelihood_at(bins, B, K, q, cx, cy)
+                    err = np.abs(got[cy - y0, cx - x0] - ref).max()
+                    assert err <= TOL, (kind, w, err)
+                    assert abs(got[ty - y0, tx - x0] - 1.0) <= TOL
+                    # histograms of one full centre row and one column
+                    hist = torch.empty((1, nx, B), device=DEV)
+                    p.local_hist(kind, w, w, x0, ty, nx, 1, hist)
+                    hh = hist.cpu().numpy()[0]
+                    assert np.abs(hh.sum(-1) - 1).max() <= 1e-5
+                    sel = np.arange(0, nx, 97)
+                    refh = O.normalise(O.hist_at(bins, B, K, x0 + sel, np.full(sel.size, ty)))
+                    assert np.abs(hh[sel] - refh).max() <= TOL
+            p.sync_status()
+    finally:
+        for _, p in plans:
+            p.close()
