@@ -26,7 +26,7 @@ DEV = "cuda:0"
 class _DevView:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3, "strides": None}
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 def device_rows(ptr, rows, pitch_elems, typestr):
