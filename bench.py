@@ -1,0 +1,448 @@
+"""Benchmark: SWIH likelihood maps on a 1024 x 1024 synthetic tracking scene.
+
+One step is one pass of the whole hot path over one frame:
+  quantise (K1) + weighted integral histograms (K2) for two plans
+    - Manhattan + Euclidean (terms 1, x, y, x^2, y^2; 32-bit ring)
+    - Gaussian approximant (terms x^k y^l, k, l <= 4; 64-bit ring)
+  + window gather / translate / normalise / Bhattacharyya (K3) for every
+    valid centre of 3 kernels x 3 windows (21, 41, 81): 8,602,224 windows.
+The metric is windows per second (whole job). Inputs are resident in HBM
+when the timed region starts; the integral histograms (7.1 GB per step) are
+far larger than L2, so no explicit L2 flush is done between steps.
+
+Also reported: an end-to-end figure through the C ABI from pinned host memory
+(frame and targets up, all nine maps back, every step), the roofline of the
+dominant kernel (CUDA events on the launching stream), SM clocks sampled
+during the timed region, and the CPU oracle timed on the host cores on a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swih|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNELS = ("manhattan", "euclidean", "gaussian")
+WINDOWS = (21, 41, 81)
+METRIC = "SWIH windows/s"
+WORKLOAD = ("1024x1024 u8 synthetic tracking scene (fBm background + 8 textured ellipses), "
+            "B=32, Manhattan/Euclidean/Gaussian(sigma=w/4) kernels x windows 21/41/81, "
+            "full valid likelihood map per kernel and window")
+
+
+def windows_per_step(H=1024, W=1024):
+    return len(KERNELS) * sum((H - w + 1) * (W - w + 1) for w in WINDOWS)
+
+
+# ----------------------------------------------------------------------------- helpers
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.first = threading.Event()
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+            self.first.set()
+
+    def wait_first(self, timeout=5.0):
+        if self.proc:
+            self.first.wait(timeout)
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken between wall times t0 and t1."""
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ts, ln in self.lines:
+            if t0 is not None and not (t0 <= ts <= t1):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) == 7:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = max(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def profile_traffic(kernel_name: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current source of the kernel (sha256 recorded in the summary), else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m and t):
+        return None
+    src = os.path.join(ROOT, "paper_1705_03524_gb300", "csrc", source)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return float(t.group(1)) if sha == m.group(1) else None
+
+
+# ----------------------------------------------------------------------------- swih arm
+def run_swih(args, rank, world, local_rank):
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg = synth.config2(seed=2 + rank, size=args.size)  # independent frame per rank
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    tx, ty = cfg["target_centre"]
+    stream = torch.cuda.Stream(device=dev)
+    d_img = torch.from_numpy(img).to(dev)
+    plan_me = S.Plan(S.make_desc(H, W, bins=B, kernels=("manhattan", "euclidean"), max_win=(81, 81)))
+    plan_g = S.Plan(S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(81, 81)))
+    plan_of = {"manhattan": plan_me, "euclidean": plan_me, "gaussian": plan_g}
+    info_me, info_g = plan_me.info(), plan_g.info()
+
+    jobs = [(k, w) for k in KERNELS for w in WINDOWS]
+    # targets: the window of each kernel and size centred on object 0 (untimed set-up)
+    plan_me.build_ih(d_img, stream)
+    plan_g.build_ih(d_img, stream)
+    targets = torch.empty((len(jobs), B), dtype=torch.float32, device=dev)
+    for j, (k, w) in enumerate(jobs):
+        plan_of[k].local_hist(k, w, w, tx, ty, 1, 1, targets[j], stream)
+    maps = [torch.empty((H - w + 1, W - w + 1), dtype=torch.float32, device=dev) for _, w in jobs]
+    plan_me.sync_status(stream)
+    plan_g.sync_status(stream)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        plan_me.build_ih(d_img, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        plan_g.build_ih(d_img, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        for j, (k, w) in enumerate(jobs):
+            plan_of[k].likelihood(k, w, w, targets[j], maps[j], stream)
+            if ev is not None:
+                ev[3 + j].record(stream)
+
+    n_ev = 3 + len(jobs)
+    for _ in range(args.warmup):
+        step()
+    plan_me.sync_status(stream)
+    plan_g.sync_status(stream)
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local_rank)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    clocks.wait_first()
+    wall0 = time.time()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(events[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    clk = clocks.stop(wall0, wall1)
+    if dist:
+        tdist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    plan_me.sync_status(stream)
+    plan_g.sync_status(stream)
+
+    # per-launch durations inside the timed region
+    seg = {"build_me": [], "build_g": []}
+    for j in range(len(jobs)):
+        seg[f"gather_{jobs[j][0]}_{jobs[j][1]}"] = []
+    for s in range(args.steps):
+        ev = events[s]
+        seg["build_me"].append(ev[0].elapsed_time(ev[1]))
+        seg["build_g"].append(ev[1].elapsed_time(ev[2]))
+        for j in range(len(jobs)):
+            seg[f"gather_{jobs[j][0]}_{jobs[j][1]}"].append(ev[2 + j].elapsed_time(ev[3 + j]))
+    seg_ms = {k: float(np.mean(v)) for k, v in seg.items()}
+
+    # algorithmic bytes per launch
+    def ih_bytes(info, n_terms_used):
+        return n_terms_used * B * H * W * info.elem_bytes
+
+    algo = {
+        "build_me": 2 * H * W + ih_bytes(info_me, info_me.n_terms),   # image + bins r/w, IH written once
+        "build_g": 2 * H * W + ih_bytes(info_g, info_g.n_terms),
+    }
+    used_terms = {"manhattan": 3, "euclidean": 5, "gaussian": info_g.n_terms}
+    for (k, w) in jobs:
+        algo[f"gather_{k}_{w}"] = (ih_bytes(info_g if k == "gaussian" else info_me, used_terms[k])
+                                   + 4 * (H - w + 1) * (W - w + 1))
+    # dominant kernel class by total time per step
+    classes = {"ih_scan (Gaussian plan, 64-bit ring)": ["build_g"],
+               "ih_scan (Manhattan+Euclidean plan, 32-bit ring)": ["build_me"],
+               "gather Gaussian": [f"gather_gaussian_{w}" for w in WINDOWS],
+               "gather Euclidean": [f"gather_euclidean_{w}" for w in WINDOWS],
+               "gather Manhattan": [f"gather_manhattan_{w}" for w in WINDOWS]}
+    totals = {c: sum(seg_ms[k] for k in ks) for c, ks in classes.items()}
+    dom = max(totals, key=totals.get)
+    dom_keys = classes[dom]
+    dom_bytes = float(np.mean([algo[k] for k in dom_keys]))
+    dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
+    peak, peak_kind = read_peaks()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    src = "k2_ih_scan.cu" if dom.startswith("ih_scan") else "k3_gather.cu"
+    prof = "ih_scan_gaussian_1024" if dom.startswith("ih_scan (G") else (
+        "gather_gaussian_1024" if dom == "gather Gaussian" else None)
+    traffic = profile_traffic(prof, src) if prof else None
+
+    # ---- end to end through the C ABI from pinned host buffers
+    h_img = torch.from_numpy(img).pin_memory()
+    h_maps = [torch.empty(m.shape, dtype=torch.float32).pin_memory() for m in maps]
+    h_targets = targets.cpu().pin_memory()
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            d_img.copy_(h_img, non_blocking=True)
+            targets.copy_(h_targets, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            for hm, m in zip(h_maps, maps):
+                hm.copy_(m, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    plan_me.sync_status(stream)
+    plan_g.sync_status(stream)
+    bi = h_img.numel() * h_img.element_size() + h_targets.numel() * 4
+    bo = sum(m.numel() * 4 for m in h_maps)
+
+    if dist:
+        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+
+    plan_me.close()
+    plan_g.close()
+    wps = windows_per_step(H, W)
+    if H != 1024:
+        line_note = f"profiling size {H}x{W}: not the benchmark workload"
+    else:
+        line_note = None
+    total_windows = wps * args.steps * world
+    line = {
+        "metric": METRIC,
+        "value": total_windows / (ms * 1e-3),
+        "unit": "windows/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32/u64-ring+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "windows_per_step_per_gpu": wps, "bins": B,
+                   "image": f"{H}x{W} u8", "kernels": list(KERNELS), "window_sizes": list(WINDOWS),
+                   "parallelism": f"replicas x{world} (independent frames, no collective)",
+                   "l2": "working set (integral histograms 7.1 GB/step) >> L2; no flush"},
+        "e2e": {"value": total_windows / (e2e_ms * 1e-3), "unit": "windows/s",
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": args.steps * (2 * 2 + len(jobs)),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
+                     "avg_launch_ms": dom_ms},
+        "per_launch_ms": seg_ms,
+        "clocks": clk,
+    }
+    if line_note:
+        line["note"] = line_note
+    return line
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_sample(budget_s: float, seed: int = 7):
+    """Time the CPU oracle on random valid centres of the same workload (all nine
+    kernel/window maps, round robin) for about budget_s seconds."""
+    from oracle import swih_oracle as O
+    from paper_1705_03524_gb300 import synth
+
+    cfg = synth.config2()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    tx, ty = cfg["target_centre"]
+    bins = O.quantize(img, 8, B)
+    jobs = []
+    for k in KERNELS:
+        for w in WINDOWS:
+            K = O.kernel_weights(k, w, w)
+            jobs.append((k, w, K, O.target_hist(bins, B, K, tx, ty)))
+    rng = np.random.default_rng(seed)
+    n_chunk = 2048
+    done = 0
+    by_job = {}
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        for (k, w, K, q) in jobs:
+            r = (w - 1) // 2
+            cx = rng.integers(r, W - r, n_chunk)
+            cy = rng.integers(r, H - r, n_chunk)
+            O.likelihood_at(bins, B, K, q, cx, cy)
+            done += n_chunk
+            by_job[(k, w)] = by_job.get((k, w), 0) + n_chunk
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "windows/s", "cores": O.threads(), "kind": "oracle",
+            "sample": (f"{done} random valid centres over the 9 kernel/window maps of the same "
+                       f"1024x1024 frame, round robin in chunks of {n_chunk}, {el:.1f} s "
+                       "(FP64 brute force, OpenMP over centres)"),
+            "seconds": el, "by_job": {f"{k}_{w}": n for (k, w), n in by_job.items()}}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    budget = max(2.0, 20.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(budget * 0.25)
+    vals = []
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = oracle_sample(budget)
+        vals.append(res["value"])
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    cpu = {"value": value, "unit": "windows/s", "cores": res["cores"], "kind": "oracle",
+           "sample": res["sample"]}
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "windows/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "note": "CPU FP64 brute-force oracle on the host cores, "
+                   "bounded sample of the workload per step"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--size", type=int, default=1024,
+                    help="frame side; 1024 is the benchmark workload, smaller sizes are for profiling")
+    ap.add_argument("--impl", choices=("swih", "reference"), default="swih")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "swih":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    # the oracle's OpenMP pool is started before any CUDA work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import swih_oracle as O
+        O.build()
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    line = run_swih(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = oracle_sample(args.cpu_seconds)
+        cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
