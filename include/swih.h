@@ -168,6 +168,51 @@ typedef struct swih_plan_info {
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
 
+/* Integral-histogram build for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface for hosts whose memory
+ * rules forbid cudaMalloc at call time -- code running while a stream is
+ * being captured into a CUDA graph, pipelines that give all device memory to a
+ * fixed pool at start-up, or allocators that refuse driver allocations later.
+ * Such callers cannot create a plan (swih_plan allocates a workspace).
+ *
+ * Computes exactly what swih_build_ih computes for a plan made from *desc,
+ * into caller-owned memory: d_ih receives every weighted integral histogram
+ * in the same layout as a plan's (plane (t, b) at element (t*B + b) *
+ * plane_elems, rows of ih_pitch elements of elem_bytes each). The bins, the
+ * scan's look-back state, its tile flags and its status word live in one
+ * static device array of 8 MiB (8388608 bytes) inside the library, which
+ * every GPU that loads the library holds until the process exits. Inputs
+ * whose scratch (bins + look-back state, reported nowhere else) exceeds it
+ * are rejected with SWIH_ERR_UNSUPPORTED and a message giving the size; when
+ * desc->band_rows is 0 the band height is raised until the state fits.
+ *
+ * Arguments:
+ *   desc      plan description (hbm_budget_bytes is ignored)
+ *   d_image   device image as for swih_build_ih
+ *   d_ih      device output, 16-byte aligned, ih_bytes long; NULL = size
+ *             query: fill *layout and return without touching the device
+ *   ih_bytes  capacity of d_ih; must be >= layout->workspace_bytes
+ *   d_status  optional device uint32 the scan ORs its error bits into
+ *             (1 = a bounded look-back wait gave up); the caller clears it.
+ *             NULL: a word inside the static array is used (cleared per call)
+ *             and such an error is not reported.
+ *   layout    optional host struct, filled with the layout: elem_bytes,
+ *             terms, pitches, plane_elems, and in workspace_bytes the bytes
+ *             d_ih must hold; d_bins points into the static array (valid until
+ *             the next call) and d_ih echoes the argument.
+ *   stream    as for swih_build_ih
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine. The first
+ * call on each device looks up the static array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture begins. Every call shares the one
+ * array and leaves its contents behind; the tile flags are cleared at each
+ * call. Calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on the array and must be serialised by the caller. */
+swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const void *d_image, void *d_ih,
+                                  uint64_t ih_bytes, uint32_t *d_status, swih_plan_info *layout,
+                                  void *stream);
+
 /* Fault injection for tests (host-set, no device fault): with
  * SWIH_INJECT_STALL_SCAN_TILE the next swih_build_ih runs its scan with the
  * first band of the first (bin, term) chain never publishing its column sums,

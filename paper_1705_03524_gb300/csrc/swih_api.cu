@@ -347,6 +347,44 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
 
 }  // namespace
 
+namespace swih {
+
+swih_status plan_layout(const swih_plan_desc *d, PlanLayout *out)
+{
+    swih_plan_s tmp;
+    swih_plan_desc d2 = *d;
+    d2.hbm_budget_bytes = 0;
+    const swih_status st = build_layout(&d2, &tmp);
+    if (st != SWIH_OK) return st;
+    out->elem_bytes = tmp.elem_bytes;
+    out->n_terms = tmp.n_terms;
+    for (int t = 0; t < tmp.n_terms; ++t) {
+        out->term_p[t] = tmp.term_p[t];
+        out->term_q[t] = tmp.term_q[t];
+    }
+    out->n_q = tmp.n_q;
+    for (int i = 0; i < tmp.n_q; ++i) {
+        out->q_val[i] = tmp.q_val[i];
+        out->p_count[i] = tmp.p_count[i];
+        for (int k = 0; k < tmp.p_count[i]; ++k) {
+            out->p_val[i][k] = tmp.p_val[i][k];
+            out->term[i][k] = tmp.term_index[tmp.p_val[i][k]][tmp.q_val[i]];
+        }
+    }
+    out->bins_pitch = tmp.bins_pitch;
+    out->ih_pitch = tmp.ih_pitch;
+    out->plane = tmp.plane;
+    out->band_rows = tmp.band_rows;
+    out->n_bands = tmp.n_bands;
+    out->scan_E = tmp.scan_E;
+    out->scan_threads = tmp.scan_threads;
+    return SWIH_OK;
+}
+
+void set_thread_error(const char *msg) { g_err = msg; }
+
+}  // namespace swih
+
 extern "C" {
 
 swih_status swih_plan_workspace_bytes(const swih_plan_desc *desc, uint64_t *bytes)

@@ -83,4 +83,16 @@ struct GatherParams {
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
+// ---------------------------------------------------------------- layout of a description
+// What a plan built from a description would use, computed on the host without
+// allocating anything.
+struct PlanLayout {
+    int elem_bytes, n_terms;
+    int term_p[kMaxTerms], term_q[kMaxTerms];
+    int n_q;
+    int q_val[kMaxQ], p_count[kMaxQ], p_val[kMaxQ][kMaxP], term[kMaxQ][kMaxP];
+    int64_t bins_pitch, ih_pitch, plane;
+    int band_rows, n_bands, scan_E, scan_threads;
+};
+
 }  // namespace swih

@@ -112,6 +112,9 @@ def _load() -> ctypes.CDLL:
     lib.swih_destroy.restype = S
     lib.swih_last_error.argtypes = [P]
     lib.swih_last_error.restype = ctypes.c_char_p
+    lib.swih_build_ih_noalloc.argtypes = [ctypes.POINTER(swih_plan_desc), P, P, ctypes.c_uint64, P,
+                                          ctypes.POINTER(swih_plan_info), P]
+    lib.swih_build_ih_noalloc.restype = S
     lib.swih_debug_inject.argtypes = [P, I]
     lib.swih_debug_inject.restype = S
     lib.swih_plan_get_info.argtypes = [P, ctypes.POINTER(swih_plan_info)]
@@ -213,6 +216,16 @@ def swih_destroy(plan: int) -> None:
 
 def swih_last_error(plan=None) -> str:
     return LIB.swih_last_error(plan).decode(errors="replace")
+
+
+def swih_build_ih_noalloc(desc: swih_plan_desc, image, d_ih, ih_bytes: int, d_status=None,
+                          stream=None) -> swih_plan_info:
+    """Allocation-free build into caller memory; d_ih=None only queries the layout
+    (layout.workspace_bytes = bytes d_ih must hold)."""
+    info = swih_plan_info()
+    _check(LIB.swih_build_ih_noalloc(ctypes.byref(desc), _ptr(image), _ptr(d_ih), int(ih_bytes),
+                                     _ptr(d_status), ctypes.byref(info), _stream(stream)))
+    return info
 
 
 SWIH_INJECT_STALL_SCAN_TILE = 1
