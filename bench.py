@@ -146,33 +146,40 @@ def run_swih(args, rank, world, local_rank):
     cfg = synth.config2(seed=2 + rank, size=args.size)  # independent frame per rank
     img = cfg["image"]
     H, W = img.shape
-    B = cfg["B"]
+    B = args.bins
+    kernels = tuple(k for k in KERNELS if k in args.kernels.split(","))
     tx, ty = cfg["target_centre"]
     stream = torch.cuda.Stream(device=dev)
     d_img = torch.from_numpy(img).to(dev)
-    plan_me = S.Plan(S.make_desc(H, W, bins=B, kernels=("manhattan", "euclidean"), max_win=(81, 81)))
-    plan_g = S.Plan(S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(81, 81)))
+    me = tuple(k for k in kernels if k != "gaussian")
+    plan_me = S.Plan(S.make_desc(H, W, bins=B, kernels=me, max_win=(81, 81))) if me else None
+    plan_g = (S.Plan(S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(81, 81)))
+              if "gaussian" in kernels else None)
+    plans = [pl for pl in (plan_me, plan_g) if pl is not None]
     plan_of = {"manhattan": plan_me, "euclidean": plan_me, "gaussian": plan_g}
-    info_me, info_g = plan_me.info(), plan_g.info()
+    info_me = plan_me.info() if plan_me else None
+    info_g = plan_g.info() if plan_g else None
 
-    jobs = [(k, w) for k in KERNELS for w in WINDOWS]
+    jobs = [(k, w) for k in kernels for w in WINDOWS]
     # targets: the window of each kernel and size centred on object 0 (untimed set-up)
-    plan_me.build_ih(d_img, stream)
-    plan_g.build_ih(d_img, stream)
+    for pl in plans:
+        pl.build_ih(d_img, stream)
     targets = torch.empty((len(jobs), B), dtype=torch.float32, device=dev)
     for j, (k, w) in enumerate(jobs):
         plan_of[k].local_hist(k, w, w, tx, ty, 1, 1, targets[j], stream)
     maps = [torch.empty((H - w + 1, W - w + 1), dtype=torch.float32, device=dev) for _, w in jobs]
-    plan_me.sync_status(stream)
-    plan_g.sync_status(stream)
+    for pl in plans:
+        pl.sync_status(stream)
 
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        plan_me.build_ih(d_img, stream)
+        if plan_me:
+            plan_me.build_ih(d_img, stream)
         if ev is not None:
             ev[1].record(stream)
-        plan_g.build_ih(d_img, stream)
+        if plan_g:
+            plan_g.build_ih(d_img, stream)
         if ev is not None:
             ev[2].record(stream)
         for j, (k, w) in enumerate(jobs):
@@ -183,8 +190,8 @@ def run_swih(args, rank, world, local_rank):
     n_ev = 3 + len(jobs)
     for _ in range(args.warmup):
         step()
-    plan_me.sync_status(stream)
-    plan_g.sync_status(stream)
+    for pl in plans:
+        pl.sync_status(stream)
 
     dist = world > 1
     if dist:
@@ -209,8 +216,8 @@ def run_swih(args, rank, world, local_rank):
     if dist:
         tdist.barrier()
     ms = t_start.elapsed_time(t_end)
-    plan_me.sync_status(stream)
-    plan_g.sync_status(stream)
+    for pl in plans:
+        pl.sync_status(stream)
 
     # per-launch durations inside the timed region
     seg = {"build_me": [], "build_g": []}
@@ -229,10 +236,11 @@ def run_swih(args, rank, world, local_rank):
         return n_terms_used * B * H * W * info.elem_bytes
 
     algo = {
-        "build_me": 2 * H * W + ih_bytes(info_me, info_me.n_terms),   # image + bins r/w, IH written once
-        "build_g": 2 * H * W + ih_bytes(info_g, info_g.n_terms),
+        # image read + bins written, every integral-histogram element written once
+        "build_me": 2 * H * W + ih_bytes(info_me, info_me.n_terms) if info_me else 0,
+        "build_g": 2 * H * W + ih_bytes(info_g, info_g.n_terms) if info_g else 0,
     }
-    used_terms = {"manhattan": 3, "euclidean": 5, "gaussian": info_g.n_terms}
+    used_terms = {"manhattan": 3, "euclidean": 5, "gaussian": info_g.n_terms if info_g else 0}
     for (k, w) in jobs:
         algo[f"gather_{k}_{w}"] = (ih_bytes(info_g if k == "gaussian" else info_me, used_terms[k])
                                    + 4 * (H - w + 1) * (W - w + 1))
@@ -242,9 +250,10 @@ def run_swih(args, rank, world, local_rank):
                "gather Gaussian": [f"gather_gaussian_{w}" for w in WINDOWS],
                "gather Euclidean": [f"gather_euclidean_{w}" for w in WINDOWS],
                "gather Manhattan": [f"gather_manhattan_{w}" for w in WINDOWS]}
-    totals = {c: sum(seg_ms[k] for k in ks) for c, ks in classes.items()}
+    totals = {c: sum(seg_ms.get(k, 0.0) for k in ks) for c, ks in classes.items()}
     dom = max(totals, key=totals.get)
     dom_keys = classes[dom]
+    dom_keys = [k for k in dom_keys if k in seg_ms]
     dom_bytes = float(np.mean([algo[k] for k in dom_keys]))
     dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
     peak, peak_kind = read_peaks()
@@ -281,8 +290,8 @@ def run_swih(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    plan_me.sync_status(stream)
-    plan_g.sync_status(stream)
+    for pl in plans:
+        pl.sync_status(stream)
     bi = h_img.numel() * h_img.element_size() + h_targets.numel() * 4
     bo = sum(m.numel() * 4 for m in h_maps)
 
@@ -291,11 +300,11 @@ def run_swih(args, rank, world, local_rank):
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         ms, e2e_ms = float(t[0]), float(t[1])
 
-    plan_me.close()
-    plan_g.close()
-    wps = windows_per_step(H, W)
-    if H != 1024:
-        line_note = f"profiling size {H}x{W}: not the benchmark workload"
+    for pl in plans:
+        pl.close()
+    wps = len(kernels) * sum((H - w + 1) * (W - w + 1) for w in WINDOWS)
+    if H != 1024 or B != 32 or len(kernels) != 3:
+        line_note = f"profiling case {H}x{W}, B={B}, kernels {kernels}: not the benchmark workload"
     else:
         line_note = None
     total_windows = wps * args.steps * world
@@ -318,7 +327,7 @@ def run_swih(args, rank, world, local_rank):
                    "l2": "working set (integral histograms 7.1 GB/step) >> L2; no flush"},
         "e2e": {"value": total_windows / (e2e_ms * 1e-3), "unit": "windows/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "gpu_launches": args.steps * (2 * 2 + len(jobs)),
+        "gpu_launches": args.steps * (2 * len(plans) + len(jobs)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
@@ -406,6 +415,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--size", type=int, default=1024,
                     help="frame side; 1024 is the benchmark workload, smaller sizes are for profiling")
+    ap.add_argument("--kernels", default="manhattan,euclidean,gaussian",
+                    help="subset of kernels (profiling); the benchmark runs all three")
+    ap.add_argument("--bins", type=int, default=32,
+                    help="bin count; 32 is the benchmark workload, fewer bins shrink profiling captures")
     ap.add_argument("--impl", choices=("swih", "reference"), default="swih")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

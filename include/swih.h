@@ -168,6 +168,14 @@ typedef struct swih_plan_info {
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
 
+/* Launch shape of the tiled window gather for one kernel of this plan:
+ * tile_cols = centre columns per CTA (128 or 256; 0 = automatic), stages =
+ * depth of the shared-memory copy ring (2..8; 0 = automatic, the deepest that
+ * keeps the register-limited number of CTAs resident). A shape whose row
+ * segments do not fit falls back to the automatic choice, then to the direct
+ * gather. Results do not depend on the shape; only speed does. */
+swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, int stages);
+
 /* Integral-histogram build for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface for hosts whose memory
  * rules forbid cudaMalloc at call time -- code running while a stream is
@@ -220,8 +228,12 @@ swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const void *d_imag
  * bound, mark themselves failed and return; the next swih_sync_status then
  * returns SWIH_ERR_TIMEOUT and the plan's integral histograms are invalid until
  * the next swih_build_ih. The injection applies to one build only.
- * what = 0 clears a pending injection. */
+ * SWIH_INJECT_DIRECT_GATHER routes the plan's gathers through the direct
+ * kernel (one thread per centre, corner reads from global memory) instead of
+ * the tiled one, until cleared; results are the same, only speed differs.
+ * what = 0 clears both. */
 #define SWIH_INJECT_STALL_SCAN_TILE 1
+#define SWIH_INJECT_DIRECT_GATHER 2
 swih_status swih_debug_inject(swih_plan_t plan, int what);
 
 #ifdef __cplusplus

@@ -36,6 +36,9 @@ struct swih_plan_s {
     int device = 0;
     bool built = false;
     int inject = 0;  // SWIH_INJECT_* for the next swih_build_ih
+    int gather_path = 0;  // 0: tiled when it fits, 1: direct gather only
+    int cfg_tx[4] = {0, 0, 0, 0};      // tiled gather tile width per kernel (0: automatic)
+    int cfg_stages[4] = {0, 0, 0, 0};  // tiled gather ring depth per kernel (0: automatic)
     std::string err;
 };
 
@@ -317,6 +320,9 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
     g.tyy = pl->term_index[0][2];
     for (int k = 0; k < 5; ++k)
         for (int l = 0; l < 5; ++l) g.tg[k][l] = pl->term_index[k][l];
+    g.status = pl->d_status;
+    g.want_tx = pl->cfg_tx[kernel];
+    g.want_stages = pl->cfg_stages[kernel];
     if (kernel == SWIH_KERNEL_GAUSSIAN) {
         GaussAxis ax, ay;
         std::string why;
@@ -336,13 +342,52 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
             for (int j = 0; j < 3; ++j)
                 g.gamma[i][j] = (float)(ax.beta[i] * ay.beta[j] / (sx * sy * mass));
         kind = kGatherGaussian;
+        const int kx = 2 * ax.D, ky = 2 * ay.D;
+        g.n_load_even = 0;
+        for (int l = 0; l <= ky; ++l)
+            for (int k = 0; k <= kx; ++k) g.load_even[g.n_load_even++] = g.tg[k][l];
+        g.n_load_odd = 0;
+        g.nl = g.n_load_even;
     } else {
         g.inv_mass = (float)(1.0L / int_kernel_mass(kernel, w, h));
         kind = kernel == SWIH_KERNEL_PLAIN ? kGatherPlain
                : kernel == SWIH_KERNEL_MANHATTAN ? kGatherManhattan
                                                  : kGatherEuclidean;
+        if (kind == kGatherPlain) {
+            g.load_even[0] = g.t1;
+            g.n_load_even = 1;
+            g.n_load_odd = 0;
+        } else if (kind == kGatherManhattan) {
+            g.load_even[0] = g.t1;
+            g.load_even[1] = g.tx;
+            g.load_even[2] = g.ty;
+            g.n_load_even = 3;
+            g.load_odd[0] = g.t1;
+            g.load_odd[1] = g.ty;
+            g.n_load_odd = 2;
+        } else {
+            g.load_even[0] = g.t1;
+            g.load_even[1] = g.tx;
+            g.load_even[2] = g.ty;
+            g.load_even[3] = g.txx;
+            g.load_even[4] = g.tyy;
+            g.n_load_even = 5;
+            g.n_load_odd = 0;
+        }
+        g.nl = std::max(g.n_load_even, g.n_load_odd);
     }
     return SWIH_OK;
+}
+
+// tiled gather when its row segments fit in shared memory, else the direct one
+cudaError_t run_gather(swih_plan_s *pl, const GatherParams &g, int kind, cudaStream_t s)
+{
+    if (pl->gather_path != 1) {
+        const cudaError_t e = launch_gather_tiled(g, kind, pl->elem_bytes, s);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
+    return launch_gather(g, kind, pl->elem_bytes, s);
 }
 
 }  // namespace
@@ -522,7 +567,7 @@ swih_status swih_local_hist(swih_plan_t pl, int kernel, int win_w, int win_h, in
     g.ncx = ncx;
     g.ncy = ncy;
     g.hist = d_hist;
-    const cudaError_t e = launch_gather(g, kind, pl->elem_bytes, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = run_gather(pl, g, kind, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(pl, "gather launch", e);
     return SWIH_OK;
 }
@@ -544,7 +589,7 @@ swih_status swih_likelihood(swih_plan_t pl, int kernel, int win_w, int win_h, co
     g.ncy = pl->desc.height - win_h + 1;
     g.target = d_target;
     g.map = d_map;
-    const cudaError_t e = launch_gather(g, kind, pl->elem_bytes, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = run_gather(pl, g, kind, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(pl, "gather launch", e);
     return SWIH_OK;
 }
@@ -585,9 +630,28 @@ const char *swih_last_error(swih_plan_t pl)
 swih_status swih_debug_inject(swih_plan_t pl, int what)
 {
     if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
-    if (what != 0 && what != SWIH_INJECT_STALL_SCAN_TILE)
+    if (what != 0 && what != SWIH_INJECT_STALL_SCAN_TILE && what != SWIH_INJECT_DIRECT_GATHER)
         return fail(pl, SWIH_ERR_INVALID_ARG, "unknown injection");
+    if (what == SWIH_INJECT_DIRECT_GATHER) {
+        pl->gather_path = 1;
+        return SWIH_OK;
+    }
+    if (what == 0) pl->gather_path = 0;
     pl->inject = what;
+    return SWIH_OK;
+}
+
+swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, int stages)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_GAUSSIAN)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "unknown kernel");
+    if (tile_cols != 0 && tile_cols != 128 && tile_cols != 256)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "tile_cols must be 0, 128 or 256");
+    if (stages != 0 && (stages < 2 || stages > 8))
+        return fail(pl, SWIH_ERR_INVALID_ARG, "stages must be 0 or 2..8");
+    pl->cfg_tx[kernel] = tile_cols;
+    pl->cfg_stages[kernel] = stages;
     return SWIH_OK;
 }
 

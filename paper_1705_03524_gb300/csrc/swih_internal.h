@@ -80,8 +80,24 @@ struct GatherParams {
     const float *target;    // [B] or null
     float *map;             // [ncy][ncx] or null
     float *hist;            // [ncy][ncx][B] or null
+    // tiled gather only
+    uint32_t *status;       // error bits (bounded waits)
+    int load_even[kMaxTerms], n_load_even;  // planes copied per corner row
+    int load_odd[kMaxTerms], n_load_odd;    // planes copied per centre row (Manhattan)
+    int nl;                 // shared-memory slots per stage (max of the two)
+    int seg, stage_off;     // set by the launcher
+    int dtop_off;           // Gaussian carried differences (set by the launcher)
+    int nstage;             // shared-memory stages in the copy ring (set by the launcher)
+    int want_stages;        // requested ring depth (0: default)
+    int want_tx;            // requested tile width, 128 or 256 (0: default)
+    int kchain, nblk;       // windows per chain, chains per phase (set by the launcher)
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
+
+// Tiled gather; returns cudaErrorNotSupported when a window's row segments do
+// not fit in shared memory (the caller then uses launch_gather).
+constexpr int kTiledChainMax = 8;
+cudaError_t launch_gather_tiled(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
 // ---------------------------------------------------------------- layout of a description
 // What a plan built from a description would use, computed on the host without

@@ -115,6 +115,8 @@ def _load() -> ctypes.CDLL:
     lib.swih_build_ih_noalloc.argtypes = [ctypes.POINTER(swih_plan_desc), P, P, ctypes.c_uint64, P,
                                           ctypes.POINTER(swih_plan_info), P]
     lib.swih_build_ih_noalloc.restype = S
+    lib.swih_set_gather_config.argtypes = [P, I, I, I]
+    lib.swih_set_gather_config.restype = S
     lib.swih_debug_inject.argtypes = [P, I]
     lib.swih_debug_inject.restype = S
     lib.swih_plan_get_info.argtypes = [P, ctypes.POINTER(swih_plan_info)]
@@ -228,7 +230,12 @@ def swih_build_ih_noalloc(desc: swih_plan_desc, image, d_ih, ih_bytes: int, d_st
     return info
 
 
+def swih_set_gather_config(plan: int, kernel: int, tile_cols: int = 0, stages: int = 0) -> None:
+    _check(LIB.swih_set_gather_config(plan, int(kernel), int(tile_cols), int(stages)), plan)
+
+
 SWIH_INJECT_STALL_SCAN_TILE = 1
+SWIH_INJECT_DIRECT_GATHER = 2
 
 
 def swih_debug_inject(plan: int, what: int) -> None:

@@ -165,6 +165,8 @@ def test_u16_offset_input():
 # --------------------------------------------------------------------------- K3
 WIN_CASES = [
     ("config1", (128, 128), 16, ("manhattan",), [(31, 31)]),
+    ("tall_chains", (300, 40), 3, ("plain", "manhattan", "euclidean", "gaussian"),
+     [(3, 3), (5, 3), (3, 29), (39, 45), (17, 299)]),
     ("ragged", (37, 53), 5, ("plain", "manhattan", "euclidean", "gaussian"),
      [(3, 3), (9, 7), (7, 9), (53, 37), (5, 37), (53, 3)]),
     ("wide", (30, 1100), 4, ("manhattan", "euclidean", "gaussian"), [(21, 15), (1099, 3)]),
@@ -172,14 +174,17 @@ WIN_CASES = [
 ]
 
 
+@pytest.mark.parametrize("path", ["tiled", "direct"])
 @pytest.mark.parametrize("case", WIN_CASES, ids=[c[0] for c in WIN_CASES])
-def test_local_hist_and_likelihood_parity(case):
+def test_local_hist_and_likelihood_parity(case, path):
     name, shape, B, kernels, windows = case
     H, W = shape
     img = synth.uniform_image(H, W, 8, seed=10 + len(name))
     maxw = max(w for w, _ in windows)
     maxh = max(h for _, h in windows)
     plan, _buf = make_plan(img, 8, B, kernels, (maxw, maxh), band_rows=8)
+    if path == "direct":
+        S.swih_debug_inject(plan.handle, S.SWIH_INJECT_DIRECT_GATHER)
     with plan:
         bins = oracle_bins(img, 8, B)
         for kind in kernels:
@@ -187,6 +192,18 @@ def test_local_hist_and_likelihood_parity(case):
                 if kind == "gaussian" and (w * h > 60000):
                     continue
                 check_windows(plan, bins, B, kind, w, h)
+
+
+def test_window_too_wide_for_shared_memory_uses_direct_gather():
+    # a 4001-wide window with 64-bit Euclidean terms needs more shared memory
+    # than a CTA has; the library falls back to the direct gather on its own
+    img = synth.uniform_image(7, 4200, 8, seed=9)
+    plan, _buf = make_plan(img, 8, 6, ("euclidean", "manhattan"), (4001, 5),
+                           precision=S.SWIH_PREC_RING64)
+    with plan:
+        bins = oracle_bins(img, 8, 6)
+        check_windows(plan, bins, 6, "euclidean", 4001, 5)
+        check_windows(plan, bins, 6, "manhattan", 4001, 3)
 
 
 def test_sub_rectangle_of_centres():
