@@ -171,10 +171,13 @@ swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
 /* Launch shape of the tiled window gather for one kernel of this plan:
  * tile_cols = centre columns per CTA (128 or 256; 0 = automatic), stages =
  * depth of the shared-memory copy ring (2..8; 0 = automatic, the deepest that
- * keeps the register-limited number of CTAs resident). A shape whose row
+ * keeps the register-limited number of CTAs resident), bins_per_step = bins
+ * carried per pipeline step by the plain, Manhattan and Euclidean kernels
+ * (4 or 8; 0 = automatic; the Gaussian always carries one). A shape whose row
  * segments do not fit falls back to the automatic choice, then to the direct
  * gather. Results do not depend on the shape; only speed does. */
-swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, int stages);
+swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, int stages,
+                                   int bins_per_step);
 
 /* Integral-histogram build for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface for hosts whose memory

@@ -25,7 +25,8 @@
 //   3. publish carry + aggregate as INCLUSIVE;
 //   4. sweep the band again, carrying cs_q in registers, and write each row of
 //      every term of the chain with a block-wide scan (thread-serial over E
-//      columns, warp shuffles, then a cross-warp pass through shared memory).
+//      columns, warp shuffles, then a cross-warp pass through shared memory);
+//      the next row's bins are loaded while the current row is scanned.
 // Output writes are full rows, coalesced, each IH element written once; the
 // bin image (1 byte per pixel) is read twice per tile and stays in L2.
 #include "swih_internal.h"
@@ -51,6 +52,19 @@ __device__ __forceinline__ T ring_pow(T base, int e)
     T r = 1;
     for (int i = 0; i < e; ++i) r *= base;
     return r;
+}
+
+// v * f for a ring element v and a factor f < 2^32 (64-bit ring: two IMADs)
+template <typename T>
+__device__ __forceinline__ T mul_small(T v, uint32_t f)
+{
+    if constexpr (sizeof(T) == 4) {
+        return v * f;
+    } else {
+        const unsigned long long lo = (unsigned long long)(uint32_t)v * f;
+        const uint32_t hi = (uint32_t)(v >> 32) * f;
+        return lo + ((unsigned long long)hi << 32);
+    }
 }
 
 // E consecutive bins starting at column x0 (x0 multiple of E, row 16-byte aligned)
@@ -133,12 +147,13 @@ __device__ __forceinline__ void add_state(const T *src, T (&acc)[E])
     }
 }
 
-template <typename T, int E>
+template <typename T, int E, int NP>
 __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
 {
     __shared__ int s_ticket;
     __shared__ int s_flag;
-    __shared__ T s_warp[2][32];
+    __shared__ T s_warp[2][1][32];
+    (void)NP;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -238,28 +253,38 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
     }
     if (failed) return;  // uniform over the block (decided from s_flag)
 
-    // ---- 4. sweep the band: column sums in registers, one row scan per term
+    // ---- 4. sweep the band: column sums in registers; per row and term x^k y^q
+    // (k < n_p), one block-wide scan: thread-serial over the E columns, warp
+    // shuffles, then the warp totals through shared memory (double-buffered, one
+    // barrier per scan). The values x^k cs(x) are built by repeated
+    // multiplication by x (x < 2^13); the next row's bins are loaded while the
+    // current row is scanned.
+    const int n_p = p.p_count[qi];  // the chain's x-exponents are 0..n_p-1
     T cs[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) cs[e] = carry[e];
-    const int n_p = p.p_count[qi];
     int parity = 0;
+    uint8_t vnext[E];
+    if (has_cols && y_begin < y_end) load_bins<E>(p.bins + (int64_t)y_begin * p.bins_pitch, x0, vnext);
     for (int y = y_begin; y < y_end; ++y) {
         if (has_cols) {
-            const T yq = ring_pow<T>((T)y, q);
             uint8_t v[E];
-            load_bins<E>(p.bins + (int64_t)y * p.bins_pitch, x0, v);
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = vnext[e];
+            if (y + 1 < y_end) load_bins<E>(p.bins + (int64_t)(y + 1) * p.bins_pitch, x0, vnext);
+            const T yq = ring_pow<T>((T)y, q);
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (v[e] == bb && x0 + e < p.W) cs[e] += yq;
         }
+        T cur[E];
         for (int k = 0; k < n_p; ++k) {
-            const int pe = p.p_val[qi][k];
             T val[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) val[e] = ring_pow<T>((T)(x0 + e), pe) * cs[e];
-#pragma unroll
-            for (int e = 1; e < E; ++e) val[e] += val[e - 1];
+            for (int e = 0; e < E; ++e) {
+                cur[e] = k == 0 ? cs[e] : mul_small<T>(cur[e], (uint32_t)(x0 + e));
+                val[e] = e == 0 ? cur[0] : val[e - 1] + cur[e];
+            }
             const T tot = val[E - 1];
             T inc = tot;
 #pragma unroll
@@ -267,10 +292,10 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
                 const T n = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += n;
             }
-            if (lane == 31) s_warp[parity][warp] = inc;
+            if (lane == 31) s_warp[parity][0][warp] = inc;
             __syncthreads();
             T off = inc - tot;
-            for (int w = 0; w < warp; ++w) off += s_warp[parity][w];
+            for (int w = 0; w < warp; ++w) off += s_warp[parity][0][w];
 #pragma unroll
             for (int e = 0; e < E; ++e) val[e] += off;
             if (in_pitch) {
@@ -287,7 +312,14 @@ template <typename T, int E>
 cudaError_t launch_typed(const ScanParams &p, int threads, cudaStream_t s)
 {
     const long long tiles = (long long)p.B * p.n_q * p.n_bands;
-    ih_scan_kernel<T, E><<<(unsigned)tiles, threads, 0, s>>>(p);
+    int np = 1;
+    for (int i = 0; i < p.n_q; ++i) np = p.p_count[i] > np ? p.p_count[i] : np;
+    if (np == 1)
+        ih_scan_kernel<T, E, 1><<<(unsigned)tiles, threads, 0, s>>>(p);
+    else if (np <= 3)
+        ih_scan_kernel<T, E, 3><<<(unsigned)tiles, threads, 0, s>>>(p);
+    else
+        ih_scan_kernel<T, E, 5><<<(unsigned)tiles, threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

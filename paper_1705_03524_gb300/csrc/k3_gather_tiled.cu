@@ -356,18 +356,23 @@ __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
                         for (int i = 0; i <= DX; ++i) E[i][g] = ex[i];
                     }
                 } else {
+                    // the window completed by this lattice row (if any); its
+                    // likelihood terms for the step's bins are summed in a register
+                    const int done_k = kMan ? ((s & 1) || s == 0 ? -1 : (s >> 1) - 1) : s - 1;
+                    float step_acc = 0.f;
 #pragma unroll
                     for (int j = 0; j < BB; ++j) {
                         if (j >= nb) break;
                         const int b = b0 + j;
-                        int done_k = -1;
+                        // h stays 0 for a bin with no pixel in the window: the
+                        // combination, conversion and square root are skipped
                         float hval = 0.f;
                         if constexpr (KIND == kGatherPlain) {
                             const T *q = st + (size_t)j * p.seg;
                             const T d = zero_row ? T(0) : (T)(q[i2] - q[i0]);
-                            if (s > 0) {
-                                done_k = s - 1;
-                                hval = ring_to_float<T>(d - top[j][0]) * p.inv_mass;
+                            if (done_k >= 0) {
+                                const T U = d - top[j][0];
+                                if (U != 0) hval = ring_to_float<T>(U) * p.inv_mass;
                             }
                             top[j][0] = d;
                         } else if constexpr (kMan) {
@@ -388,20 +393,20 @@ __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
                                     dxr = sx[i2] - sx[i1];
                                     dyf = sy[i2] - sy[i0];
                                 }
-                                if (s > 0) {
-                                    const int k = (s >> 1) - 1;
-                                    const T tyc = (T)(yc0 + k * h);
+                                if (done_k >= 0) {
                                     const T R1l = d1l - top[j][0], R1r = d1r - top[j][1];
-                                    const T R1 = R1l + R1r;
-                                    const T R1t = mid1[j] - (top[j][0] + top[j][1]);
-                                    const T R1b = (d1l + d1r) - mid1[j];
-                                    const T Rxl = dxl - top[j][2], Rxr = dxr - top[j][3];
-                                    const T Ryt = midy[j] - top[j][4], Ryb = dyf - midy[j];
-                                    const T sdx = (Rxr - txc * R1r) - (Rxl - txc * R1l);
-                                    const T sdy = (Ryb - tyc * R1b) - (Ryt - tyc * R1t);
-                                    const T U = (T)(p.rx + p.ry) * R1 - sdx - sdy;
-                                    done_k = k;
-                                    hval = ring_to_float<T>(U) * p.inv_mass;
+                                    const T R1 = R1l + R1r;  // pixel count of the bin in the window
+                                    if (R1 != 0) {
+                                        const T tyc = (T)(yc0 + done_k * h);
+                                        const T R1t = mid1[j] - (top[j][0] + top[j][1]);
+                                        const T R1b = (d1l + d1r) - mid1[j];
+                                        const T Rxl = dxl - top[j][2], Rxr = dxr - top[j][3];
+                                        const T Ryt = midy[j] - top[j][4], Ryb = dyf - midy[j];
+                                        const T sdx = (Rxr - txc * R1r) - (Rxl - txc * R1l);
+                                        const T sdy = (Ryb - tyc * R1b) - (Ryt - tyc * R1t);
+                                        const T U = (T)(p.rx + p.ry) * R1 - sdx - sdy;
+                                        hval = ring_to_float<T>(U) * p.inv_mass;
+                                    }
                                 }
                                 top[j][0] = d1l;
                                 top[j][1] = d1r;
@@ -416,15 +421,17 @@ __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
 #pragma unroll
                                 for (int t = 0; t < 5; ++t) d[t] = q[t * p.seg + i2] - q[t * p.seg + i0];
                             }
-                            if (s > 0) {
-                                const T tyc = (T)(yc0 + (s - 1) * h);
-                                const T R1 = d[0] - top[j][0], Rx = d[1] - top[j][1], Ry = d[2] - top[j][2];
-                                const T Rxx = d[3] - top[j][3], Ryy = d[4] - top[j][4];
-                                const T sdx2 = Rxx - (T)2 * txc * Rx + txc * txc * R1;
-                                const T sdy2 = Ryy - (T)2 * tyc * Ry + tyc * tyc * R1;
-                                const T U = ((T)p.rx * (T)p.rx + (T)p.ry * (T)p.ry) * R1 - sdx2 - sdy2;
-                                done_k = s - 1;
-                                hval = ring_to_float<T>(U) * p.inv_mass;
+                            if (done_k >= 0) {
+                                const T R1 = d[0] - top[j][0];
+                                if (R1 != 0) {
+                                    const T tyc = (T)(yc0 + done_k * h);
+                                    const T Rx = d[1] - top[j][1], Ry = d[2] - top[j][2];
+                                    const T Rxx = d[3] - top[j][3], Ryy = d[4] - top[j][4];
+                                    const T sdx2 = Rxx - (T)2 * txc * Rx + txc * txc * R1;
+                                    const T sdy2 = Ryy - (T)2 * tyc * Ry + tyc * tyc * R1;
+                                    const T U = ((T)p.rx * (T)p.rx + (T)p.ry * (T)p.ry) * R1 - sdx2 - sdy2;
+                                    hval = ring_to_float<T>(U) * p.inv_mass;
+                                }
                             }
 #pragma unroll
                             for (int t = 0; t < 5; ++t) top[j][t] = d[t];
@@ -434,9 +441,10 @@ __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
                                 const int yc = yc0 + done_k * h;
                                 p.hist[((int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)) * p.B + b] = hval;
                             }
-                            if (p.target) s_acc[done_k * TX + tid] += sqrtf(hval) * s_sq[b];
+                            if (hval != 0.f) step_acc += sqrtf(hval) * s_sq[b];
                         }
                     }
+                    if (done_k >= 0 && p.target) s_acc[done_k * TX + tid] += step_acc;
                 }
                 // release the stage: every lane of the warp is done reading it
                 __syncwarp();
@@ -528,10 +536,9 @@ cudaError_t launch_tx(const GatherParams &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int KIND, typename T, int DX, int DY>
-cudaError_t launch_kind(const GatherParams &p, cudaStream_t s)
+template <int KIND, typename T, int DX, int DY, int BB>
+cudaError_t launch_bb(const GatherParams &p, cudaStream_t s)
 {
-    constexpr int BB = KIND == kGatherGaussian ? 1 : 4;
     // wide tiles amortise the window halo; narrow ones when wide segments do not
     // fit, and for the register-heavy Gaussian (more resident CTAs per SM)
     const int want_tx = p.want_tx ? p.want_tx : (KIND == kGatherGaussian ? 128 : 0);
@@ -539,6 +546,18 @@ cudaError_t launch_kind(const GatherParams &p, cudaStream_t s)
     cudaError_t e = launch_tx<KIND, T, 256, DX, DY, BB>(p, s);
     if (e != cudaErrorNotSupported || want_tx == 256) return e;
     return launch_tx<KIND, T, 128, DX, DY, BB>(p, s);
+}
+
+template <int KIND, typename T, int DX, int DY>
+cudaError_t launch_kind(const GatherParams &p, cudaStream_t s)
+{
+    if constexpr (KIND == kGatherGaussian) {
+        return launch_bb<KIND, T, DX, DY, 1>(p, s);
+    } else {
+        // bins per pipeline step
+        if (p.want_bb == 8) return launch_bb<KIND, T, DX, DY, 8>(p, s);
+        return launch_bb<KIND, T, DX, DY, 4>(p, s);
+    }
 }
 
 }  // namespace
@@ -549,7 +568,10 @@ cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_byt
     GatherParams p = p_in;
     const int h = 2 * p.ry + 1;
     const int slots = (p.ncy + h - 1) / h;
-    const int nb = (slots + KMAX - 1) / KMAX;
+    // windows per chain: long chains for the Gaussian (its extra lattice rows
+    // cost copies), short ones for the cheap kernels (more CTAs, smaller tail)
+    const int kmax = kind == kGatherGaussian ? KMAX : KMAX / 2;
+    const int nb = (slots + kmax - 1) / kmax;
     p.kchain = (slots + nb - 1) / nb;
     p.nblk = nb;
     if ((long long)h * nb > 65535) return cudaErrorNotSupported;

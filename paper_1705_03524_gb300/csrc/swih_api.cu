@@ -7,7 +7,7 @@
 #include <cstring>
 #include <string>
 
-#include "../../include/swih.h"
+#include "swih.h"
 #include "swih_internal.h"
 
 using namespace swih;
@@ -39,6 +39,7 @@ struct swih_plan_s {
     int gather_path = 0;  // 0: tiled when it fits, 1: direct gather only
     int cfg_tx[4] = {0, 0, 0, 0};      // tiled gather tile width per kernel (0: automatic)
     int cfg_stages[4] = {0, 0, 0, 0};  // tiled gather ring depth per kernel (0: automatic)
+    int cfg_bb[4] = {0, 0, 0, 0};      // tiled gather bins per step per kernel (0: automatic)
     std::string err;
 };
 
@@ -230,6 +231,10 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
             pl->p_val[pl->n_q][cnt++] = p;
             pl->term_index[p][q] = pl->n_terms++;
         }
+        // the scan kernel relies on each chain's x-exponents being 0..cnt-1
+        for (int k = 0; k < cnt; ++k)
+            if (pl->p_val[pl->n_q][k] != k)
+                return fail(nullptr, SWIH_ERR_UNSUPPORTED, "internal: non-contiguous term set");
         if (cnt) {
             pl->q_val[pl->n_q] = q;
             pl->p_count[pl->n_q] = cnt;
@@ -323,6 +328,7 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
     g.status = pl->d_status;
     g.want_tx = pl->cfg_tx[kernel];
     g.want_stages = pl->cfg_stages[kernel];
+    g.want_bb = pl->cfg_bb[kernel];
     if (kernel == SWIH_KERNEL_GAUSSIAN) {
         GaussAxis ax, ay;
         std::string why;
@@ -641,7 +647,8 @@ swih_status swih_debug_inject(swih_plan_t pl, int what)
     return SWIH_OK;
 }
 
-swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, int stages)
+swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, int stages,
+                                   int bins_per_step)
 {
     if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
     if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_GAUSSIAN)
@@ -650,8 +657,11 @@ swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, in
         return fail(pl, SWIH_ERR_INVALID_ARG, "tile_cols must be 0, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8))
         return fail(pl, SWIH_ERR_INVALID_ARG, "stages must be 0 or 2..8");
+    if (bins_per_step != 0 && bins_per_step != 4 && bins_per_step != 8)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "bins_per_step must be 0, 4 or 8");
     pl->cfg_tx[kernel] = tile_cols;
     pl->cfg_stages[kernel] = stages;
+    pl->cfg_bb[kernel] = bins_per_step;
     return SWIH_OK;
 }
 

@@ -90,6 +90,7 @@ struct GatherParams {
     int nstage;             // shared-memory stages in the copy ring (set by the launcher)
     int want_stages;        // requested ring depth (0: default)
     int want_tx;            // requested tile width, 128 or 256 (0: default)
+    int want_bb;            // requested bins per pipeline step, 4 or 8 (0: default)
     int kchain, nblk;       // windows per chain, chains per phase (set by the launcher)
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);

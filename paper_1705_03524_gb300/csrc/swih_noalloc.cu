@@ -19,7 +19,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/swih.h"
+#include "swih.h"
 #include "swih_internal.h"
 
 namespace swih {

@@ -115,7 +115,7 @@ def _load() -> ctypes.CDLL:
     lib.swih_build_ih_noalloc.argtypes = [ctypes.POINTER(swih_plan_desc), P, P, ctypes.c_uint64, P,
                                           ctypes.POINTER(swih_plan_info), P]
     lib.swih_build_ih_noalloc.restype = S
-    lib.swih_set_gather_config.argtypes = [P, I, I, I]
+    lib.swih_set_gather_config.argtypes = [P, I, I, I, I]
     lib.swih_set_gather_config.restype = S
     lib.swih_debug_inject.argtypes = [P, I]
     lib.swih_debug_inject.restype = S
@@ -230,8 +230,10 @@ def swih_build_ih_noalloc(desc: swih_plan_desc, image, d_ih, ih_bytes: int, d_st
     return info
 
 
-def swih_set_gather_config(plan: int, kernel: int, tile_cols: int = 0, stages: int = 0) -> None:
-    _check(LIB.swih_set_gather_config(plan, int(kernel), int(tile_cols), int(stages)), plan)
+def swih_set_gather_config(plan: int, kernel: int, tile_cols: int = 0, stages: int = 0,
+                           bins_per_step: int = 0) -> None:
+    _check(LIB.swih_set_gather_config(plan, int(kernel), int(tile_cols), int(stages),
+                                      int(bins_per_step)), plan)
 
 
 SWIH_INJECT_STALL_SCAN_TILE = 1
