@@ -91,11 +91,12 @@ def quantize(image: np.ndarray, bitdepth: int, B: int) -> np.ndarray:
 
     The paper names Q as "the quantization function that determines which
     bin to increase" without fixing it; equal-width bins over the full
-    pixel range are the reading taken.
+    pixel range are the reading taken. Values above 2^bitdepth - 1 (stray
+    high bits of a wider pixel type) count in the last bin.
     """
     if not (1 <= B <= 256):
         raise ValueError("B must be in [1, 256]")
-    v = image.astype(np.int64)
+    v = np.minimum(image.astype(np.int64), (1 << bitdepth) - 1)
     return ((v * B) >> bitdepth).astype(np.uint8)
 
 

@@ -78,6 +78,9 @@ def test_quantize_bin_edges():
     assert np.all(np.bincount(b, minlength=16) == 16)
     v16 = np.array([[0, 1023, 1024, 65535]], dtype=np.uint16)
     assert list(O.quantize(v16, 16, 64)[0]) == [0, 0, 1, 63]
+    # 12 significant bits in a 16-bit pixel: values past 4095 land in the last bin
+    v12 = np.array([[0, 63, 64, 4095, 4096, 65535]], dtype=np.uint16)
+    assert list(O.quantize(v12, 12, 64)[0]) == [0, 0, 1, 63, 63, 63]
     # non-power-of-two bin count still gives equal-width bins
     b24 = O.quantize(v8, 8, 24)[0]
     assert b24.max() == 23 and np.all(np.diff(b24.astype(int)) >= 0)
