@@ -43,6 +43,15 @@ namespace {
 constexpr int KMAX = kTiledChainMax;
 constexpr int kMaxStages = 8;
 constexpr int kDefaultStages = 4;
+
+template <typename T>
+struct template_tag {
+    using type = T;
+};
+template <int V>
+struct int_tag {
+    static constexpr int value = V;
+};
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 constexpr uint32_t kSuspendHintNs = 200000;                   // sleep up to 0.2 ms per try
 
@@ -171,8 +180,9 @@ __device__ __forceinline__ void axis_bernstein(const unsigned long long (&R)[5],
     }
 }
 
+// One work item: column tile `tile` and chain `cy` (phase-major) of job p.
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
-__global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
+__device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const int tile, const int cy)
 {
     using u64 = unsigned long long;
     extern __shared__ __align__(128) unsigned char sm[];
@@ -193,14 +203,14 @@ __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
     const int lane = tid & 31;
     const bool producer = tid >= TX;
     const int h = 2 * p.ry + 1;
-    const int blk = blockIdx.y % p.nblk;
-    const int phase = blockIdx.y / p.nblk;
+    const int blk = cy % p.nblk;
+    const int phase = cy / p.nblk;
     const int n_slots = (p.ncy - phase + h - 1) / h;
     const int slot0 = blk * p.kchain;
     const int K = min(p.kchain, n_slots - slot0);
     if (K <= 0) return;  // whole CTA, before any barrier
 
-    const int xs = p.cx0 + blockIdx.x * TX;
+    const int xs = p.cx0 + tile * TX;
     int xc = xs + (producer ? 0 : tid);
     const bool valid_x = xc < p.cx0 + p.ncx;
     xc = min(xc, p.cx0 + p.ncx - 1);
@@ -491,114 +501,248 @@ __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(GatherParams p)
     }
 }
 
+// A single job: the grid is (column tiles, chains).
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
-cudaError_t launch_tx(const GatherParams &p, cudaStream_t s)
+__global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(const __grid_constant__ GatherParams p)
 {
-    auto fn = gather_tiled_kernel<KIND, T, TX, DX, DY, BB>;
-    constexpr int A = 16 / (int)sizeof(T);
-    const int w = 2 * p.rx + 1;
-    GatherParams q = p;
-    q.seg = (TX + w + 2 * A + A - 1) / A * A;
-    // shared memory: barriers | sqrt(target) | window sums | [Gaussian carry] | stages
-    q.dtop_off = (16 * kMaxStages + 4 * p.B + 4 * KMAX * TX + 15) / 16 * 16;
-    const int carry = KIND == kGatherGaussian ? (2 * DX + 1) * (2 * DY + 1) * TX * 8 : 0;
-    q.stage_off = (q.dtop_off + carry + 127) / 128 * 128;
-    const int per_bin = KIND == kGatherGaussian ? 2 * DX + 1 : p.nl;
-    q.nl = BB * per_bin;
-    const size_t stage = (size_t)q.nl * q.seg * sizeof(T);
-    // stages: enough to cover the copy latency, few enough that the CTAs the
-    // register file allows stay resident
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
-    if (e != cudaSuccess) return e;
-    const int regs = std::max(fa.numRegs, 16);
-    int ctas = std::min(2048 / (TX + 32), 65536 / ((TX + 32) * ((regs + 7) / 8 * 8)));
-    ctas = std::max(ctas, 1);
-    const size_t sm_total = 227 * 1024;
-    const int want = p.want_stages > 0 ? std::min(p.want_stages, kMaxStages) : kDefaultStages;
-    int ns = 0;
-    for (; ctas >= 1; --ctas) {
-        const size_t budget = sm_total / ctas - 1024;
-        if (budget < q.stage_off + 2 * stage) continue;
-        ns = (int)std::min<size_t>(want, (budget - q.stage_off) / stage);
-        if (ns >= 2) break;
-    }
-    if (ns < 2) return cudaErrorNotSupported;
-    q.nstage = ns;
-    const size_t bytes = q.stage_off + ns * stage;
-    if (bytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-    }
-    const int h = 2 * p.ry + 1;
-    const dim3 grid((unsigned)((p.ncx + TX - 1) / TX), (unsigned)(h * p.nblk));
-    fn<<<grid, TX + 32, bytes, s>>>(q);
-    return cudaGetLastError();
+    gather_tiled_body<KIND, T, TX, DX, DY, BB>(p, blockIdx.x, blockIdx.y);
 }
 
-template <int KIND, typename T, int DX, int DY, int BB>
-cudaError_t launch_bb(const GatherParams &p, cudaStream_t s)
+// A table of jobs sharing one shape: one CTA per work item, items of job j
+// numbered from item_start[j] with the column tiles fastest.
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
+__global__ void __launch_bounds__(TX + 32)
+    gather_table_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs)
 {
-    // wide tiles amortise the window halo; narrow ones when wide segments do not
-    // fit, and for the register-heavy Gaussian (more resident CTAs per SM)
-    const int want_tx = p.want_tx ? p.want_tx : (KIND == kGatherGaussian ? 128 : 0);
-    if (want_tx == 128) return launch_tx<KIND, T, 128, DX, DY, BB>(p, s);
-    cudaError_t e = launch_tx<KIND, T, 256, DX, DY, BB>(p, s);
-    if (e != cudaErrorNotSupported || want_tx == 256) return e;
-    return launch_tx<KIND, T, 128, DX, DY, BB>(p, s);
+    const int item = blockIdx.x;
+    int lo = 0, hi = n_jobs - 1;  // the last job whose first item is <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const GatherParams &p = jobs[lo];
+    const int li = item - item_start[lo];
+    const int tiles = (p.ncx + TX - 1) / TX;
+    gather_tiled_body<KIND, T, TX, DX, DY, BB>(p, li % tiles, li / tiles);
+}
+
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
+int kernel_regs()
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, gather_tiled_kernel<KIND, T, TX, DX, DY, BB>) != cudaSuccess) return 255;
+    return fa.numRegs;
 }
 
 template <int KIND, typename T, int DX, int DY>
-cudaError_t launch_kind(const GatherParams &p, cudaStream_t s)
+int regs_of(int tx, int bb)
 {
     if constexpr (KIND == kGatherGaussian) {
-        return launch_bb<KIND, T, DX, DY, 1>(p, s);
+        return tx == 128 ? kernel_regs<KIND, T, 128, DX, DY, 1>() : kernel_regs<KIND, T, 256, DX, DY, 1>();
     } else {
-        // bins per pipeline step
-        if (p.want_bb == 8) return launch_bb<KIND, T, DX, DY, 8>(p, s);
-        return launch_bb<KIND, T, DX, DY, 4>(p, s);
+        if (tx == 128) return bb == 8 ? kernel_regs<KIND, T, 128, DX, DY, 8>() : kernel_regs<KIND, T, 128, DX, DY, 4>();
+        return bb == 8 ? kernel_regs<KIND, T, 256, DX, DY, 8>() : kernel_regs<KIND, T, 256, DX, DY, 4>();
     }
 }
 
-}  // namespace
-
-cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_bytes, cudaStream_t s)
+// instantiation selector: calls F::template run<KIND, T, TX, DX, DY, BB>()
+template <typename F>
+cudaError_t dispatch(int kind, int elem_bytes, int gdx, int gdy, int tx, int bb, F &&f)
 {
-    if (p_in.ncx <= 0 || p_in.ncy <= 0) return cudaSuccess;
-    GatherParams p = p_in;
-    const int h = 2 * p.ry + 1;
-    const int slots = (p.ncy + h - 1) / h;
-    // windows per chain: long chains for the Gaussian (its extra lattice rows
-    // cost copies), short ones for the cheap kernels (more CTAs, smaller tail)
-    const int kmax = kind == kGatherGaussian ? KMAX : KMAX / 2;
-    const int nb = (slots + kmax - 1) / kmax;
-    p.kchain = (slots + nb - 1) / nb;
-    p.nblk = nb;
-    if ((long long)h * nb > 65535) return cudaErrorNotSupported;
     using u64 = unsigned long long;
+    auto by_shape = [&](auto kind_tag, auto t_tag, auto dx_tag, auto dy_tag) -> cudaError_t {
+        constexpr int K = decltype(kind_tag)::value;
+        using T = typename decltype(t_tag)::type;
+        constexpr int DX = decltype(dx_tag)::value, DY = decltype(dy_tag)::value;
+        if constexpr (K == kGatherGaussian) {
+            if (tx == 128) return f.template run<K, T, 128, DX, DY, 1>();
+            return f.template run<K, T, 256, DX, DY, 1>();
+        } else {
+            if (tx == 128) return bb == 8 ? f.template run<K, T, 128, DX, DY, 8>() : f.template run<K, T, 128, DX, DY, 4>();
+            return bb == 8 ? f.template run<K, T, 256, DX, DY, 8>() : f.template run<K, T, 256, DX, DY, 4>();
+        }
+    };
+    template_tag<uint32_t> t32;
+    template_tag<u64> t64;
+    int_tag<0> z;
     if (elem_bytes == 4) {
         switch (kind) {
-        case kGatherPlain: return launch_kind<kGatherPlain, uint32_t, 0, 0>(p, s);
-        case kGatherManhattan: return launch_kind<kGatherManhattan, uint32_t, 0, 0>(p, s);
-        case kGatherEuclidean: return launch_kind<kGatherEuclidean, uint32_t, 0, 0>(p, s);
+        case kGatherPlain: return by_shape(int_tag<kGatherPlain>{}, t32, z, z);
+        case kGatherManhattan: return by_shape(int_tag<kGatherManhattan>{}, t32, z, z);
+        case kGatherEuclidean: return by_shape(int_tag<kGatherEuclidean>{}, t32, z, z);
         default: return cudaErrorInvalidValue;
         }
     }
     if (elem_bytes == 8) {
         switch (kind) {
-        case kGatherPlain: return launch_kind<kGatherPlain, u64, 0, 0>(p, s);
-        case kGatherManhattan: return launch_kind<kGatherManhattan, u64, 0, 0>(p, s);
-        case kGatherEuclidean: return launch_kind<kGatherEuclidean, u64, 0, 0>(p, s);
+        case kGatherPlain: return by_shape(int_tag<kGatherPlain>{}, t64, z, z);
+        case kGatherManhattan: return by_shape(int_tag<kGatherManhattan>{}, t64, z, z);
+        case kGatherEuclidean: return by_shape(int_tag<kGatherEuclidean>{}, t64, z, z);
         case kGatherGaussian:
-            if (p.gdx == 2 && p.gdy == 2) return launch_kind<kGatherGaussian, u64, 2, 2>(p, s);
-            if (p.gdx == 2 && p.gdy == 1) return launch_kind<kGatherGaussian, u64, 2, 1>(p, s);
-            if (p.gdx == 1 && p.gdy == 2) return launch_kind<kGatherGaussian, u64, 1, 2>(p, s);
-            if (p.gdx == 1 && p.gdy == 1) return launch_kind<kGatherGaussian, u64, 1, 1>(p, s);
+            if (gdx == 2 && gdy == 2) return by_shape(int_tag<kGatherGaussian>{}, t64, int_tag<2>{}, int_tag<2>{});
+            if (gdx == 2 && gdy == 1) return by_shape(int_tag<kGatherGaussian>{}, t64, int_tag<2>{}, int_tag<1>{});
+            if (gdx == 1 && gdy == 2) return by_shape(int_tag<kGatherGaussian>{}, t64, int_tag<1>{}, int_tag<2>{});
+            if (gdx == 1 && gdy == 1) return by_shape(int_tag<kGatherGaussian>{}, t64, int_tag<1>{}, int_tag<1>{});
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
         }
     }
     return cudaErrorInvalidValue;
+}
+
+struct RegsQuery {
+    int regs = 255;
+    template <int K, typename T, int TX, int DX, int DY, int BB>
+    cudaError_t run()
+    {
+        regs = kernel_regs<K, T, TX, DX, DY, BB>();
+        return cudaSuccess;
+    }
+};
+
+template <typename KernelFn>
+cudaError_t set_smem(KernelFn fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+struct SingleLaunch {
+    const GatherParams *p;
+    const GatherShape *sh;
+    cudaStream_t s;
+    template <int K, typename T, int TX, int DX, int DY, int BB>
+    cudaError_t run()
+    {
+        auto fn = gather_tiled_kernel<K, T, TX, DX, DY, BB>;
+        cudaError_t e = set_smem(fn, sh->smem);
+        if (e != cudaSuccess) return e;
+        const int h = 2 * p->ry + 1;
+        const dim3 grid((unsigned)((p->ncx + TX - 1) / TX), (unsigned)(h * p->nblk));
+        fn<<<grid, TX + 32, sh->smem, s>>>(*p);
+        return cudaGetLastError();
+    }
+};
+
+struct TableLaunch {
+    const GatherParams *jobs;
+    const int *item_start;
+    int n_jobs, n_items;
+    const GatherShape *sh;
+    cudaStream_t s;
+    template <int K, typename T, int TX, int DX, int DY, int BB>
+    cudaError_t run()
+    {
+        auto fn = gather_table_kernel<K, T, TX, DX, DY, BB>;
+        cudaError_t e = set_smem(fn, sh->smem);
+        if (e != cudaSuccess) return e;
+        fn<<<(unsigned)n_items, TX + 32, sh->smem, s>>>(jobs, item_start, n_jobs);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, int B, int nl_per_bin,
+                        int want_tx, int want_stages, int want_bb, GatherShape *shape)
+{
+    const bool gau = kind == kGatherGaussian;
+    const int A = 16 / elem_bytes;
+    const int bb = gau ? 1 : (want_bb == 8 ? 8 : 4);
+    const int per_bin = gau ? 2 * gdx + 1 : nl_per_bin;
+    const int want = want_stages > 0 ? std::min(want_stages, kMaxStages) : kDefaultStages;
+    // wide tiles amortise the window halo; narrow ones when wide segments do
+    // not fit, and by default for the register-heavy Gaussian (more resident
+    // CTAs per SM)
+    int txs[2] = {256, 128};
+    int ntx = 2;
+    if (want_tx == 128 || (want_tx == 0 && gau)) {
+        txs[0] = 128;
+        ntx = 1;
+    } else if (want_tx == 256) {
+        ntx = 1;
+    }
+    for (int i = 0; i < ntx; ++i) {
+        const int tx = txs[i];
+        GatherShape sh;
+        sh.tx = tx;
+        sh.bb = bb;
+        sh.seg = (tx + max_w + 2 * A + A - 1) / A * A;
+        sh.nl = bb * per_bin;
+        sh.kchain_max = gau ? KMAX : KMAX / 2;
+        // shared memory: barriers | sqrt(target) | window sums | [Gaussian carry] | stages
+        sh.dtop_off = (16 * kMaxStages + 4 * B + 4 * KMAX * tx + 15) / 16 * 16;
+        const int carry = gau ? (2 * gdx + 1) * (2 * gdy + 1) * tx * 8 : 0;
+        sh.stage_off = (sh.dtop_off + carry + 127) / 128 * 128;
+        const size_t stage = (size_t)sh.nl * sh.seg * elem_bytes;
+        // stages: enough to cover the copy latency, few enough that the CTAs
+        // the register file allows stay resident
+        RegsQuery rq;
+        dispatch(kind, elem_bytes, gdx, gdy, tx, bb, rq);
+        const int regs = std::max(rq.regs, 16);
+        int ctas = std::min(2048 / (tx + 32), 65536 / ((tx + 32) * ((regs + 7) / 8 * 8)));
+        ctas = std::max(ctas, 1);
+        // the Gaussian's long steps want at least three stages (one consumed,
+        // two in flight) more than one more resident CTA; the cheap kernels
+        // want resident CTAs. Settle for two stages when nothing deeper fits.
+        int ns = 0;
+        for (int min_ns = std::min(gau ? 3 : 2, want); min_ns >= 2 && ns < 2; --min_ns) {
+            for (int c = ctas; c >= 1; --c) {
+                const size_t budget = (size_t)227 * 1024 / c - 1024;
+                if (budget < sh.stage_off + (size_t)min_ns * stage) continue;
+                ns = (int)std::min<size_t>(want, (budget - sh.stage_off) / stage);
+                break;
+            }
+        }
+        if (ns < 2) continue;
+        sh.nstage = ns;
+        sh.smem = sh.stage_off + ns * stage;
+        *shape = sh;
+        return cudaSuccess;
+    }
+    return cudaErrorNotSupported;
+}
+
+int tiled_items(GatherParams *job, const GatherShape &shape)
+{
+    const int h = 2 * job->ry + 1;
+    const int slots = (job->ncy + h - 1) / h;
+    const int kmax = shape.kchain_max;
+    const int nb = std::max(1, (slots + kmax - 1) / kmax);
+    job->kchain = (slots + nb - 1) / nb;
+    job->nblk = nb;
+    job->seg = shape.seg;
+    job->nl = shape.nl;
+    job->nstage = shape.nstage;
+    job->stage_off = shape.stage_off;
+    job->dtop_off = shape.dtop_off;
+    if (job->ncx <= 0 || job->ncy <= 0) return 0;
+    const int tiles = (job->ncx + shape.tx - 1) / shape.tx;
+    return tiles * h * nb;
+}
+
+cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_bytes, cudaStream_t s)
+{
+    if (p_in.ncx <= 0 || p_in.ncy <= 0) return cudaSuccess;
+    GatherShape sh;
+    cudaError_t e = tiled_shape(kind, elem_bytes, p_in.gdx, p_in.gdy, 2 * p_in.rx + 1, p_in.B, p_in.nl,
+                                p_in.want_tx, p_in.want_stages, p_in.want_bb, &sh);
+    if (e != cudaSuccess) return e;
+    GatherParams p = p_in;
+    tiled_items(&p, sh);
+    if ((long long)(2 * p.ry + 1) * p.nblk > 65535) return cudaErrorNotSupported;
+    SingleLaunch L{&p, &sh, s};
+    return dispatch(kind, elem_bytes, p.gdx, p.gdy, sh.tx, sh.bb, L);
+}
+
+cudaError_t launch_gather_table(const GatherParams *d_jobs, const int *d_item_start, int n_jobs,
+                                int n_items, const GatherParams &shape_job, int kind, int elem_bytes,
+                                int gdx, int gdy, const GatherShape &shape, cudaStream_t s)
+{
+    (void)shape_job;
+    if (n_items <= 0) return cudaSuccess;
+    TableLaunch L{d_jobs, d_item_start, n_jobs, n_items, &shape, s};
+    return dispatch(kind, elem_bytes, gdx, gdy, shape.tx, shape.bb, L);
 }
 
 }  // namespace swih

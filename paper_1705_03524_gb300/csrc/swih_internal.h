@@ -100,6 +100,29 @@ cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaS
 constexpr int kTiledChainMax = 8;
 cudaError_t launch_gather_tiled(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
+// Shape shared by every job of one tiled-gather launch: shared-memory layout
+// and copy ring (a job = one kernel, window and centre rectangle over one set
+// of integral histograms).
+struct GatherShape {
+    int tx;          // centre columns per CTA (128 or 256)
+    int bb;          // bins per pipeline step
+    int seg, nl, nstage, stage_off, dtop_off;
+    int kchain_max;  // windows per chain
+    size_t smem;     // dynamic shared memory bytes
+};
+// Shape for jobs of one kind with the given fitted degrees, largest window
+// width and bin count; cudaErrorNotSupported when nothing fits.
+cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, int B, int nl_per_bin,
+                        int want_tx, int want_stages, int want_bb, GatherShape *shape);
+// Fill a job's shape fields and chain split; returns its number of work items
+// (column tiles x chains).
+int tiled_items(GatherParams *job, const GatherShape &shape);
+// One launch over a device table of jobs (all with the shape's fields set and
+// the same B): one CTA per work item; item_start[j] = first item of job j.
+cudaError_t launch_gather_table(const GatherParams *d_jobs, const int *d_item_start, int n_jobs,
+                                int n_items, const GatherParams &shape_job, int kind, int elem_bytes,
+                                int gdx, int gdy, const GatherShape &shape, cudaStream_t s);
+
 // ---------------------------------------------------------------- layout of a description
 // What a plan built from a description would use, computed on the host without
 // allocating anything.
