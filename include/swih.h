@@ -168,6 +168,76 @@ typedef struct swih_plan_info {
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
 
+/* ---------------------------------------------------------------- batches
+ * Many regions of interest (ROIs) of one frame, each with its own size,
+ * kernel, windows (scales) and target histogram, processed by a fixed set of
+ * launches: one quantisation over all ROIs, one integral-histogram scan over
+ * all ROIs, and one window-gather launch per group of jobs that share a kernel
+ * and fitted degree (a job = one ROI at one window). The sequence is captured
+ * into a CUDA graph once and replayed by swih_batch_run. This is the paper's
+ * search problem (Sec. 1, Sec. 4: likelihood maps for many candidate regions)
+ * run for many targets at once; the paper itself processes one region at a
+ * time. */
+#define SWIH_MAX_SCALES 8
+
+typedef struct swih_batch_desc {
+    int32_t height;            /* frame rows */
+    int32_t width;             /* frame columns */
+    int64_t pitch_bytes;       /* frame row stride in bytes */
+    int32_t pixel_type;        /* swih_pixel_type */
+    int32_t bitdepth;
+    int32_t bins;              /* B, shared by every ROI */
+    uint32_t kernel_mask;      /* kernels any ROI may use */
+    int32_t gauss_degree;      /* as in swih_plan_desc */
+    double gauss_sigma_frac;
+    int32_t precision;         /* swih_precision (AUTO: the widest any ROI needs) */
+    int32_t band_rows;         /* scan band height (0: automatic) */
+    uint64_t hbm_budget_bytes; /* reject batches whose workspace exceeds it (0: no limit) */
+} swih_batch_desc;
+
+typedef struct swih_roi_desc {
+    int32_t x0, y0;            /* top-left pixel of the ROI in the frame */
+    int32_t width, height;     /* ROI size (width <= 8192) */
+    int32_t kernel;            /* swih_kernel, must be in kernel_mask */
+    int32_t n_windows;         /* 1..SWIH_MAX_SCALES */
+    int32_t win_w[SWIH_MAX_SCALES], win_h[SWIH_MAX_SCALES];  /* odd, >= 3, <= ROI size */
+    const float *d_target;     /* device float32 [bins], q(b) >= 0 summing to 1 */
+    float *d_map[SWIH_MAX_SCALES]; /* device float32 [height-win_h+1][width-win_w+1] each */
+} swih_roi_desc;
+
+typedef struct swih_batch_s *swih_batch_t;
+
+/* Workspace a batch would allocate (host only). */
+swih_status swih_batch_workspace_bytes(const swih_batch_desc *desc, const swih_roi_desc *rois, int n_rois,
+                                       uint64_t *bytes);
+
+/* Validate, lay out and allocate a batch over the frame d_frame (device,
+ * height rows of pitch_bytes, owned by the caller, read at every run; the
+ * caller may rewrite its contents between runs). Targets and maps are the
+ * caller's and are bound to the batch. One integral-histogram term set and
+ * one ring serve every ROI: those a plan for the largest ROI with the largest
+ * window of any ROI would pick, so every ROI's results are exact in it.
+ * Errors of the batch calls are reported by swih_last_error(NULL) on the
+ * calling thread. SWIH_ERR_BUDGET when the workspace exceeds hbm_budget_bytes. */
+swih_status swih_batch_plan(const swih_batch_desc *desc, const swih_roi_desc *rois, int n_rois,
+                            const void *d_frame, swih_batch_t *out);
+
+/* Enqueue one pass over every ROI and window on the stream: a replay of the
+ * batch's CUDA graph (captured at the first run, and again after
+ * swih_batch_autotune). Maps are written; nothing is synchronised. */
+swih_status swih_batch_run(swih_batch_t batch, void *stream);
+
+/* Time candidate gather launch shapes (tile width, copy-ring depth, bins per
+ * step) for each job group on this batch's own data, keep the fastest, and
+ * capture the graph again. Synchronises the stream; results are unchanged. */
+swih_status swih_batch_autotune(swih_batch_t batch, void *stream);
+
+/* As swih_sync_status, for a batch. */
+swih_status swih_batch_sync_status(swih_batch_t batch, void *stream);
+
+/* Free the batch (synchronises the device). NULL is a no-op. */
+swih_status swih_batch_destroy(swih_batch_t batch);
+
 /* Launch shape of the tiled window gather for one kernel of this plan:
  * tile_cols = centre columns per CTA (128 or 256; 0 = automatic), stages =
  * depth of the shared-memory copy ring (2..8; 0 = automatic, the deepest that

@@ -147,32 +147,25 @@ __device__ __forceinline__ void add_state(const T *src, T (&acc)[E])
     }
 }
 
-template <typename T, int E, int NP>
-__global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
+// One (chain, band) tile of one image region r; ticket = its ticket number.
+template <typename T, int E>
+__device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r, const int ticket,
+                                          const int band, const int chain)
 {
-    __shared__ int s_ticket;
     __shared__ int s_flag;
-    __shared__ T s_warp[2][1][32];
-    (void)NP;
+    __shared__ T s_warp[2][32];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-
-    if (tid == 0) s_ticket = atomicAdd(p.ticket, 1);
-    __syncthreads();
-    const int ticket = s_ticket;
-    const int n_chains = p.B * p.n_q;
-    const int band = ticket / n_chains;
-    const int chain = ticket - band * n_chains;
     const int b = chain / p.n_q;
     const int qi = chain - b * p.n_q;
     const int q = p.q_val[qi];
     const int y_begin = band * p.band_rows;
-    const int y_end = min(y_begin + p.band_rows, p.H);
+    const int y_end = min(y_begin + p.band_rows, r.H);
     const int x0 = tid * E;
-    const bool has_cols = x0 < p.W;               // any real column in this thread
-    const bool in_pitch = x0 < p.ih_pitch;        // chunk lies inside a stored row
+    const bool has_cols = x0 < r.W;               // any real column in this thread
+    const bool in_pitch = x0 < r.ih_pitch;        // chunk lies inside a stored row
     const uint8_t bb = (uint8_t)b;
     if (ticket == p.stall_tile && band == 0) return;  // injected stall: publish nothing
 
@@ -184,16 +177,16 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
         for (int y = y_begin; y < y_end; ++y) {
             const T yq = ring_pow<T>((T)y, q);
             uint8_t v[E];
-            load_bins<E>(p.bins + (int64_t)y * p.bins_pitch, x0, v);
+            load_bins<E>(r.bins + (int64_t)y * r.bins_pitch, x0, v);
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (v[e] == bb && x0 + e < p.W) agg[e] += yq;
+                if (v[e] == bb && x0 + e < r.W) agg[e] += yq;
         }
     }
 
-    const int64_t state_row = ((int64_t)chain * p.n_bands + band) * p.ih_pitch;
-    int *my_flag = p.flags + (int64_t)chain * p.n_bands + band;
-    if (in_pitch) store_state<T, E>((band == 0 ? (T *)p.incl : (T *)p.agg) + state_row + x0, agg);
+    const int64_t state_row = ((int64_t)chain * r.n_bands + band) * r.ih_pitch;
+    int *my_flag = r.flags + (int64_t)chain * r.n_bands + band;
+    if (in_pitch) store_state<T, E>((band == 0 ? (T *)r.incl : (T *)r.agg) + state_row + x0, agg);
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -210,7 +203,7 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
         int j = band - 1;
         while (true) {
             if (tid == 0) {
-                const int *fp = p.flags + (int64_t)chain * p.n_bands + j;
+                const int *fp = r.flags + (int64_t)chain * r.n_bands + j;
                 int f = ld_acquire(fp);
                 long long it = 0;
                 while (f == kFlagEmpty) {
@@ -231,8 +224,8 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
                 failed = true;
                 break;
             }
-            const T *src = (f == kFlagInclusive ? (const T *)p.incl : (const T *)p.agg) +
-                           ((int64_t)chain * p.n_bands + j) * p.ih_pitch;
+            const T *src = (f == kFlagInclusive ? (const T *)r.incl : (const T *)r.agg) +
+                           ((int64_t)chain * r.n_bands + j) * r.ih_pitch;
             if (in_pitch) add_state<T, E>(src + x0, carry);
             if (f == kFlagInclusive || j == 0) break;
             --j;
@@ -242,7 +235,7 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
             T inc[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) inc[e] = carry[e] + agg[e];
-            store_state<T, E>((T *)p.incl + state_row + x0, inc);
+            store_state<T, E>((T *)r.incl + state_row + x0, inc);
         }
         __threadfence();
         __syncthreads();
@@ -265,17 +258,17 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
     for (int e = 0; e < E; ++e) cs[e] = carry[e];
     int parity = 0;
     uint8_t vnext[E];
-    if (has_cols && y_begin < y_end) load_bins<E>(p.bins + (int64_t)y_begin * p.bins_pitch, x0, vnext);
+    if (has_cols && y_begin < y_end) load_bins<E>(r.bins + (int64_t)y_begin * r.bins_pitch, x0, vnext);
     for (int y = y_begin; y < y_end; ++y) {
         if (has_cols) {
             uint8_t v[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = vnext[e];
-            if (y + 1 < y_end) load_bins<E>(p.bins + (int64_t)(y + 1) * p.bins_pitch, x0, vnext);
+            if (y + 1 < y_end) load_bins<E>(r.bins + (int64_t)(y + 1) * r.bins_pitch, x0, vnext);
             const T yq = ring_pow<T>((T)y, q);
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (v[e] == bb && x0 + e < p.W) cs[e] += yq;
+                if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
         }
         T cur[E];
         for (int k = 0; k < n_p; ++k) {
@@ -292,15 +285,15 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
                 const T n = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += n;
             }
-            if (lane == 31) s_warp[parity][0][warp] = inc;
+            if (lane == 31) s_warp[parity][warp] = inc;
             __syncthreads();
             T off = inc - tot;
-            for (int w = 0; w < warp; ++w) off += s_warp[parity][0][w];
+            for (int w = 0; w < warp; ++w) off += s_warp[parity][w];
 #pragma unroll
             for (int e = 0; e < E; ++e) val[e] += off;
             if (in_pitch) {
-                T *row = (T *)p.ih + ((int64_t)p.term[qi][k] * p.B + b) * p.plane +
-                         (int64_t)y * p.ih_pitch;
+                T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane +
+                         (int64_t)y * r.ih_pitch;
                 store_row<T, E>(row + x0, val);
             }
             parity ^= 1;
@@ -309,27 +302,73 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(ScanParams p)
 }
 
 template <typename T, int E>
-cudaError_t launch_typed(const ScanParams &p, int threads, cudaStream_t s)
+__global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_constant__ ScanParams p)
 {
-    const long long tiles = (long long)p.B * p.n_q * p.n_bands;
-    int np = 1;
-    for (int i = 0; i < p.n_q; ++i) np = p.p_count[i] > np ? p.p_count[i] : np;
-    if (np == 1)
-        ih_scan_kernel<T, E, 1><<<(unsigned)tiles, threads, 0, s>>>(p);
-    else if (np <= 3)
-        ih_scan_kernel<T, E, 3><<<(unsigned)tiles, threads, 0, s>>>(p);
+    __shared__ int s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(p.ticket, 1);
+    __syncthreads();
+    const int ticket = s_ticket;
+    const int n_chains = p.B * p.n_q;
+    const int band = ticket / n_chains;
+    ScanRoi r;
+    r.bins = p.bins;
+    r.bins_pitch = p.bins_pitch;
+    r.ih = p.ih;
+    r.ih_pitch = p.ih_pitch;
+    r.plane = p.plane;
+    r.agg = p.agg;
+    r.incl = p.incl;
+    r.flags = p.flags;
+    r.H = p.H;
+    r.W = p.W;
+    r.n_bands = p.n_bands;
+    r.ticket0 = 0;
+    scan_tile<T, E>(p, r, ticket, band, ticket - band * n_chains);
+}
+
+// Several image regions in one launch: region i owns the tickets
+// [table[i].ticket0, table[i + 1].ticket0), band-major, so every tile a tile
+// may wait for (the same chain, an earlier band, the same region) holds a
+// smaller ticket and has already started.
+template <typename T, int E>
+__global__ void __launch_bounds__(kMaxScanThreads)
+    ih_scan_table_kernel(const __grid_constant__ ScanParams p, const ScanRoi *__restrict__ table, int n)
+{
+    __shared__ int s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(p.ticket, 1);
+    __syncthreads();
+    const int ticket = s_ticket;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].ticket0 <= ticket) lo = mid; else hi = mid - 1;
+    }
+    const ScanRoi r = table[lo];
+    const int local = ticket - r.ticket0;
+    const int n_chains = p.B * p.n_q;
+    const int band = local / n_chains;
+    scan_tile<T, E>(p, r, ticket, band, local - band * n_chains);
+}
+
+template <typename T, int E>
+cudaError_t launch_typed(const ScanParams &p, int threads, const ScanRoi *table, int n_roi, long long tiles,
+                         cudaStream_t s)
+{
+    if (table)
+        ih_scan_table_kernel<T, E><<<(unsigned)tiles, threads, 0, s>>>(p, table, n_roi);
     else
-        ih_scan_kernel<T, E, 5><<<(unsigned)tiles, threads, 0, s>>>(p);
+        ih_scan_kernel<T, E><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_e(const ScanParams &p, int E, int threads, cudaStream_t s)
+cudaError_t launch_e(const ScanParams &p, int E, int threads, const ScanRoi *table, int n_roi, long long tiles,
+                     cudaStream_t s)
 {
     switch (E) {
-    case 4: return launch_typed<T, 4>(p, threads, s);
-    case 8: return launch_typed<T, 8>(p, threads, s);
-    case 16: return launch_typed<T, 16>(p, threads, s);
+    case 4: return launch_typed<T, 4>(p, threads, table, n_roi, tiles, s);
+    case 8: return launch_typed<T, 8>(p, threads, table, n_roi, tiles, s);
+    case 16: return launch_typed<T, 16>(p, threads, table, n_roi, tiles, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -339,8 +378,18 @@ cudaError_t launch_e(const ScanParams &p, int E, int threads, cudaStream_t s)
 cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads, cudaStream_t s)
 {
     if (threads < 32 || threads > kMaxScanThreads || threads % 32) return cudaErrorInvalidValue;
-    if (elem_bytes == 4) return launch_e<uint32_t>(p, E, threads, s);
-    if (elem_bytes == 8) return launch_e<unsigned long long>(p, E, threads, s);
+    if (elem_bytes == 4) return launch_e<uint32_t>(p, E, threads, nullptr, 0, 0, s);
+    if (elem_bytes == 8) return launch_e<unsigned long long>(p, E, threads, nullptr, 0, 0, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ih_scan_table(const ScanParams &p, const ScanRoi *d_table, int n_roi, long long tiles,
+                                 int elem_bytes, int E, int threads, cudaStream_t s)
+{
+    if (threads < 32 || threads > kMaxScanThreads || threads % 32) return cudaErrorInvalidValue;
+    if (tiles <= 0) return cudaSuccess;
+    if (elem_bytes == 4) return launch_e<uint32_t>(p, E, threads, d_table, n_roi, tiles, s);
+    if (elem_bytes == 8) return launch_e<unsigned long long>(p, E, threads, d_table, n_roi, tiles, s);
     return cudaErrorInvalidValue;
 }
 

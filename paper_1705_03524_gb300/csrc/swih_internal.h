@@ -33,6 +33,19 @@ struct QuantParams {
 };
 cudaError_t launch_quantize(const QuantParams &p, cudaStream_t s);
 
+// One image region of a batched quantisation.
+struct QuantRoi {
+    const uint8_t *image;  // first pixel of the region
+    int64_t pitch;         // bytes
+    int H, W;
+    uint8_t *bins;
+    int64_t bins_pitch;
+    long long chunk0;      // first 16-pixel chunk of the region; regions in chunk order
+    int vec;               // aligned 16-byte loads allowed
+};
+cudaError_t launch_quantize_table(const QuantRoi *d_table, int n, long long n_chunks, int B, int bitdepth,
+                                  int pixel_bytes, cudaStream_t s);
+
 // ---------------------------------------------------------------- K2 scan
 // One chain per (bin b, y-exponent q); a chain's bands are scanned top to
 // bottom with decoupled look-back on per-column state vectors.
@@ -60,6 +73,22 @@ struct ScanParams {
 // E = columns per thread, threads = ceil(W/E) rounded to a warp multiple
 cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads,
                            cudaStream_t s);
+
+// The per-region fields of a scan (one entry per image region of a batch).
+struct ScanRoi {
+    const uint8_t *bins;
+    int64_t bins_pitch;
+    void *ih;
+    int64_t ih_pitch, plane;
+    void *agg, *incl;
+    int *flags;
+    int H, W, n_bands;
+    int ticket0;  // first ticket of the region; regions are in ticket order
+};
+// One launch over several regions sharing B, terms, ring and band height;
+// p carries those plus ticket/status/spin_limit; tiles = total tiles.
+cudaError_t launch_ih_scan_table(const ScanParams &p, const ScanRoi *d_table, int n_roi, long long tiles,
+                                 int elem_bytes, int E, int threads, cudaStream_t s);
 
 // ---------------------------------------------------------------- K3 gather
 enum GatherKind { kGatherPlain = 0, kGatherManhattan = 1, kGatherEuclidean = 2, kGatherGaussian = 3 };

@@ -90,6 +90,41 @@ class swih_plan_info(ctypes.Structure):
     ]
 
 
+SWIH_MAX_SCALES = 8
+
+
+class swih_batch_desc(ctypes.Structure):
+    _fields_ = [
+        ("height", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("pitch_bytes", ctypes.c_int64),
+        ("pixel_type", ctypes.c_int32),
+        ("bitdepth", ctypes.c_int32),
+        ("bins", ctypes.c_int32),
+        ("kernel_mask", ctypes.c_uint32),
+        ("gauss_degree", ctypes.c_int32),
+        ("gauss_sigma_frac", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("band_rows", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+    ]
+
+
+class swih_roi_desc(ctypes.Structure):
+    _fields_ = [
+        ("x0", ctypes.c_int32),
+        ("y0", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("n_windows", ctypes.c_int32),
+        ("win_w", ctypes.c_int32 * SWIH_MAX_SCALES),
+        ("win_h", ctypes.c_int32 * SWIH_MAX_SCALES),
+        ("d_target", ctypes.c_void_p),
+        ("d_map", ctypes.c_void_p * SWIH_MAX_SCALES),
+    ]
+
+
 def _load() -> ctypes.CDLL:
     path = _build.LIB
     if not os.path.exists(path):
@@ -121,6 +156,16 @@ def _load() -> ctypes.CDLL:
     lib.swih_debug_inject.restype = S
     lib.swih_plan_get_info.argtypes = [P, ctypes.POINTER(swih_plan_info)]
     lib.swih_plan_get_info.restype = S
+    BD, RD = ctypes.POINTER(swih_batch_desc), ctypes.POINTER(swih_roi_desc)
+    lib.swih_batch_workspace_bytes.argtypes = [BD, RD, I, ctypes.POINTER(ctypes.c_uint64)]
+    lib.swih_batch_workspace_bytes.restype = S
+    lib.swih_batch_plan.argtypes = [BD, RD, I, P, ctypes.POINTER(P)]
+    lib.swih_batch_plan.restype = S
+    for name in ("swih_batch_run", "swih_batch_autotune", "swih_batch_sync_status"):
+        getattr(lib, name).argtypes = [P, P]
+        getattr(lib, name).restype = S
+    lib.swih_batch_destroy.argtypes = [P]
+    lib.swih_batch_destroy.restype = S
     return lib
 
 
@@ -277,6 +322,118 @@ class Plan:
     def close(self):
         if self.handle:
             swih_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+def make_batch_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8, bitdepth=None,
+                    bins=16, kernels=("manhattan",), gauss_degree=2, gauss_sigma_frac=0.25,
+                    precision=SWIH_PREC_AUTO, band_rows=0, hbm_budget_bytes=0) -> swih_batch_desc:
+    pb = 1 if pixel_type == SWIH_PIXEL_U8 else 2
+    mask = 0
+    for k in kernels:
+        mask |= kernel_bit(KERNELS[k] if isinstance(k, str) else int(k))
+    d = swih_batch_desc()
+    d.height, d.width = int(height), int(width)
+    d.pitch_bytes = int(pitch_bytes if pitch_bytes is not None else width * pb)
+    d.pixel_type = int(pixel_type)
+    d.bitdepth = int(bitdepth if bitdepth is not None else 8 * pb)
+    d.bins = int(bins)
+    d.kernel_mask = mask
+    d.gauss_degree = int(gauss_degree)
+    d.gauss_sigma_frac = float(gauss_sigma_frac)
+    d.precision = int(precision)
+    d.band_rows = int(band_rows)
+    d.hbm_budget_bytes = int(hbm_budget_bytes)
+    return d
+
+
+def make_roi(x0, y0, width, height, kernel, windows, target, maps) -> swih_roi_desc:
+    """windows: [(w, h), ...] (at most SWIH_MAX_SCALES); maps: one device buffer per window."""
+    if len(windows) != len(maps) or not 1 <= len(windows) <= SWIH_MAX_SCALES:
+        raise ValueError("need 1..SWIH_MAX_SCALES windows, one map each")
+    r = swih_roi_desc()
+    r.x0, r.y0, r.width, r.height = int(x0), int(y0), int(width), int(height)
+    r.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    r.n_windows = len(windows)
+    for k, (w, h) in enumerate(windows):
+        r.win_w[k], r.win_h[k] = int(w), int(h)
+        r.d_map[k] = _ptr(maps[k])
+    r.d_target = _ptr(target)
+    return r
+
+
+def _roi_array(rois):
+    arr = (swih_roi_desc * len(rois))()
+    for i, r in enumerate(rois):
+        arr[i] = r
+    return arr
+
+
+def swih_batch_workspace_bytes(desc: swih_batch_desc, rois) -> int:
+    out = ctypes.c_uint64(0)
+    arr = _roi_array(rois)
+    _check(LIB.swih_batch_workspace_bytes(ctypes.byref(desc), arr, len(rois), ctypes.byref(out)))
+    return int(out.value)
+
+
+def swih_batch_plan(desc: swih_batch_desc, rois, frame) -> int:
+    h = ctypes.c_void_p()
+    arr = _roi_array(rois)
+    _check(LIB.swih_batch_plan(ctypes.byref(desc), arr, len(rois), _ptr(frame), ctypes.byref(h)))
+    return int(h.value)
+
+
+def swih_batch_run(batch: int, stream=None) -> None:
+    _check(LIB.swih_batch_run(batch, _stream(stream)))
+
+
+def swih_batch_autotune(batch: int, stream=None) -> None:
+    _check(LIB.swih_batch_autotune(batch, _stream(stream)))
+
+
+def swih_batch_sync_status(batch: int, stream=None) -> None:
+    _check(LIB.swih_batch_sync_status(batch, _stream(stream)))
+
+
+def swih_batch_destroy(batch: int) -> None:
+    _check(LIB.swih_batch_destroy(batch))
+
+
+class Batch:
+    """Owning wrapper of a batch; keeps the frame, targets and maps it was given alive."""
+
+    def __init__(self, desc: swih_batch_desc, rois, frame, keep=()):
+        self.desc = desc
+        self.rois = list(rois)
+        self._keep = (frame, tuple(keep))
+        self.handle = swih_batch_plan(desc, self.rois, frame)
+
+    def run(self, stream=None):
+        swih_batch_run(self.handle, stream)
+
+    def autotune(self, stream=None):
+        swih_batch_autotune(self.handle, stream)
+
+    def sync_status(self, stream=None):
+        swih_batch_sync_status(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            swih_batch_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

@@ -25,6 +25,7 @@ __all__ = [
     "Scene",
     "config1",
     "config2",
+    "config3",
     "odd_window",
 ]
 
@@ -86,6 +87,26 @@ class Scene:
     params: list = field(default_factory=list)
 
 
+def _plant_ellipse(img: np.ndarray, rng: np.random.Generator, cx: int, cy: int, a: float, b: float,
+                   ang: float, mean: float, noise_std: float) -> None:
+    """Overwrite the pixels of an ellipse (semi-axes a, b, rotated by ang,
+    centred on (cx, cy)) with mean + N(0, noise_std) texture, drawn in
+    row-major order. Only the ellipse's bounding square is visited, which
+    gives the same pixels and draws as visiting the whole frame."""
+    h, w = img.shape
+    R = int(np.ceil(max(a, b))) + 1
+    ys, ye = max(cy - R, 0), min(cy + R + 1, h)
+    xs, xe = max(cx - R, 0), min(cx + R + 1, w)
+    yy, xx = np.mgrid[ys:ye, xs:xe]
+    ca, sa = np.cos(ang), np.sin(ang)
+    u = (xx - cx) * ca + (yy - cy) * sa
+    v = -(xx - cx) * sa + (yy - cy) * ca
+    inside = (u / a) ** 2 + (v / b) ** 2 <= 1.0
+    n_in = int(inside.sum())
+    sub = img[ys:ye, xs:xe]
+    sub[inside] = mean + rng.normal(0.0, noise_std, size=n_in)
+
+
 def blob_scene(h: int, w: int, bitdepth: int, seed: int, n_blobs: int,
                axes: tuple = (10, 60), octaves: int = 4, cell: float = 128.0,
                bg_mean_frac: float = 0.5, bg_amp_frac: float = 48.0 / 256.0,
@@ -102,7 +123,6 @@ def blob_scene(h: int, w: int, bitdepth: int, seed: int, n_blobs: int,
     rng = np.random.default_rng(seed)
     full = float(1 << bitdepth)
     img = bg_mean_frac * full + bg_amp_frac * full * fbm_value_noise(h, w, octaves, cell, rng)
-    yy, xx = np.mgrid[0:h, 0:w]
     centres = []
     params = []
     lo_mean = int(0.15625 * full)   # 40 for 8-bit
@@ -115,12 +135,7 @@ def blob_scene(h: int, w: int, bitdepth: int, seed: int, n_blobs: int,
         m = min(margin, h // 2 - 1, w // 2 - 1)
         cx = int(rng.integers(m, w - m))
         cy = int(rng.integers(m, h - m))
-        ca, sa = np.cos(ang), np.sin(ang)
-        u = (xx - cx) * ca + (yy - cy) * sa
-        v = -(xx - cx) * sa + (yy - cy) * ca
-        inside = (u / a) ** 2 + (v / b) ** 2 <= 1.0
-        n_in = int(inside.sum())
-        img[inside] = mean + rng.normal(0.0, noise_frac * full, size=n_in)
+        _plant_ellipse(img, rng, cx, cy, a, b, ang, mean, noise_frac * full)
         centres.append((cx, cy))
         params.append((a, b, ang, mean))
     img = np.clip(np.rint(img), 0, full - 1)
@@ -150,3 +165,42 @@ def config2(seed: int = 2, size: int = 1024) -> dict:
     return dict(image=sc.image, bitdepth=8, B=32,
                 kernels=("manhattan", "euclidean", "gaussian"), windows=(21, 41, 81),
                 target_centre=sc.centres[0], scene=sc)
+
+
+def config3(seed: int = 3, n_rois: int = 64, size: int = 4096, roi_range: tuple = (96, 768),
+            box_range: tuple = (24, 64)) -> dict:
+    """Batched search regions: a 4096 x 4096 uint16 frame (fBm background
+    spanning the 16-bit range with i.i.d. Gaussian texture of std 2% of the
+    range, plus one textured elliptical object per region), 64 regions with width and height drawn independently from
+    U[96, 768], each with a target box side s ~ U[24, 64] and windows at
+    0.8 s, s and 1.25 s rounded to odd sides; B = 64, Gaussian kernel.
+
+    The object of region i sits near the region's centre with semi-axes
+    about s / 2, so the region's search map has one true peak. Returns the
+    frame, the regions as (x0, y0, width, height), the window sides per
+    region, and the object centre per region (frame coordinates)."""
+    rng = np.random.default_rng(seed)
+    full = float(1 << 16)
+    img = 0.5 * full + 0.3 * full * fbm_value_noise(size, size, 5, 512.0, rng)
+    img += rng.normal(0.0, 0.02 * full, size=img.shape)  # sensor-like texture
+    rois, windows, centres = [], [], []
+    for _ in range(n_rois):
+        rw = int(rng.integers(roi_range[0], roi_range[1] + 1))
+        rh = int(rng.integers(roi_range[0], roi_range[1] + 1))
+        x0 = int(rng.integers(0, size - rw + 1))
+        y0 = int(rng.integers(0, size - rh + 1))
+        s = float(rng.uniform(box_range[0], box_range[1]))
+        wins = [odd_window(0.8 * s), odd_window(s), odd_window(1.25 * s)]
+        cx = x0 + rw // 2 + int(rng.integers(-rw // 8, rw // 8 + 1))
+        cy = y0 + rh // 2 + int(rng.integers(-rh // 8, rh // 8 + 1))
+        a = 0.5 * s * float(rng.uniform(0.7, 1.0))
+        b = 0.5 * s * float(rng.uniform(0.7, 1.0))
+        ang = float(rng.uniform(0.0, np.pi))
+        mean = float(rng.integers(int(0.15 * full), int(0.85 * full)))
+        _plant_ellipse(img, rng, cx, cy, a, b, ang, mean, 0.05 * full)
+        rois.append((x0, y0, rw, rh))
+        windows.append(wins)
+        centres.append((cx, cy))
+    img = np.clip(np.rint(img), 0, full - 1).astype(np.uint16)
+    return dict(image=img, bitdepth=16, B=64, kernel="gaussian", rois=rois, windows=windows,
+                object_centres=centres)

@@ -108,3 +108,99 @@ def test_null_plan_calls_fail_cleanly():
 
 def test_build_module_paths():
     assert B.LIB.endswith("libswih.so") and os.path.exists(B.LIB)
+
+
+# --------------------------------------------------------------------------- batches
+def test_batch_struct_layout_matches_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "swih.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(swih_batch_desc), offsetof(swih_batch_desc, gauss_sigma_frac),
+         offsetof(swih_batch_desc, hbm_budget_bytes), sizeof(swih_roi_desc), offsetof(swih_roi_desc, win_h),
+         offsetof(swih_roi_desc, d_target), offsetof(swih_roi_desc, d_map));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                               check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(S.swih_batch_desc), S.swih_batch_desc.gauss_sigma_frac.offset,
+                    S.swih_batch_desc.hbm_budget_bytes.offset, ctypes.sizeof(S.swih_roi_desc),
+                    S.swih_roi_desc.win_h.offset, S.swih_roi_desc.d_target.offset,
+                    S.swih_roi_desc.d_map.offset]
+
+
+FAKE = 1 << 20  # a non-NULL device address that host-side validation never touches
+
+
+def _roi(x0=0, y0=0, w=64, h=48, kernel="manhattan", windows=((9, 9),), target=FAKE, maps=None):
+    maps = maps if maps is not None else [FAKE] * len(windows)
+    return S.make_roi(x0, y0, w, h, kernel, list(windows), target, maps)
+
+
+def _bdesc(**kw):
+    base = dict(bins=16, kernels=("manhattan", "euclidean"))
+    base.update(kw)
+    return S.make_batch_desc(base.pop("height", 200), base.pop("width", 300), **base)
+
+
+@pytest.mark.parametrize("rois,kw,status", [
+    ([_roi(x0=250)], {}, S.SWIH_ERR_INVALID_ARG),               # leaves the frame on the right
+    ([_roi(y0=-1)], {}, S.SWIH_ERR_INVALID_ARG),
+    ([_roi(w=2)], {}, S.SWIH_ERR_INVALID_ARG),
+    ([_roi(kernel="gaussian")], {}, S.SWIH_ERR_INVALID_ARG),    # not in kernel_mask
+    ([_roi(windows=((8, 9),))], {}, S.SWIH_ERR_INVALID_ARG),    # even side
+    ([_roi(windows=((65, 9),))], {}, S.SWIH_ERR_INVALID_ARG),   # wider than the ROI
+    ([_roi(target=0)], {}, S.SWIH_ERR_INVALID_ARG),
+    ([_roi(maps=[0])], {}, S.SWIH_ERR_INVALID_ARG),
+    ([_roi()], dict(bins=0), S.SWIH_ERR_INVALID_ARG),
+    ([_roi()], dict(bitdepth=9), S.SWIH_ERR_INVALID_ARG),
+    ([_roi()], dict(pitch_bytes=299), S.SWIH_ERR_INVALID_ARG),
+    ([_roi(w=300, h=200, kernel="gaussian", windows=((255, 199),))], dict(kernels=("gaussian",)),
+     S.SWIH_ERR_UNSUPPORTED),                                   # Gaussian moments beyond 2^64
+    ([_roi(), "nine_scales"], {}, S.SWIH_ERR_INVALID_ARG),
+])
+def test_batch_validation(rois, kw, status):
+    if "nine_scales" in rois:  # n_windows above SWIH_MAX_SCALES, built without make_roi's check
+        r = _roi(x0=10)
+        r.n_windows = S.SWIH_MAX_SCALES + 1
+        rois = [rois[0], r]
+    with pytest.raises(S.SwihError) as ei:
+        S.swih_batch_workspace_bytes(_bdesc(**kw), rois)
+    assert ei.value.status == status
+    assert S.swih_last_error()
+
+
+def test_batch_budget_and_null_arguments():
+    rois = [_roi(), _roi(x0=100, y0=20, w=120, h=90, windows=((9, 9), (21, 15)))]
+    need = S.swih_batch_workspace_bytes(_bdesc(), rois)
+    with pytest.raises(S.SwihError) as ei:
+        S.swih_batch_plan(_bdesc(hbm_budget_bytes=need - 1), rois, FAKE)  # before any CUDA call
+    assert ei.value.status == S.SWIH_ERR_BUDGET
+    with pytest.raises(S.SwihError) as ei:
+        S.swih_batch_plan(_bdesc(), rois, 0)
+    assert ei.value.status == S.SWIH_ERR_INVALID_ARG
+    with pytest.raises(S.SwihError) as ei:
+        S.swih_batch_plan(_bdesc(pixel_type=S.SWIH_PIXEL_U16, pitch_bytes=600), rois, FAKE + 1)
+    assert ei.value.status == S.SWIH_ERR_INVALID_ARG  # odd address for 16-bit pixels
+    for fn in (S.LIB.swih_batch_run, S.LIB.swih_batch_autotune, S.LIB.swih_batch_sync_status):
+        assert fn(None, None) == S.SWIH_ERR_INVALID_ARG
+    assert S.LIB.swih_batch_destroy(None) == S.SWIH_OK
+
+
+def test_batch_workspace_grows_with_rois_and_terms():
+    one = [_roi()]
+    two = [_roi(), _roi(x0=100, y0=20, w=120, h=90)]
+    n1 = S.swih_batch_workspace_bytes(_bdesc(), one)
+    n2 = S.swih_batch_workspace_bytes(_bdesc(), two)
+    # Manhattan + Euclidean: five terms, 32-bit ring; the second ROI adds its planes
+    assert n2 - n1 >= 5 * 16 * 90 * 128 * 4
+    # the Gaussian in the mask switches every ROI to 25 terms in the 64-bit ring
+    g = S.swih_batch_workspace_bytes(_bdesc(kernels=("manhattan", "gaussian")), two)
+    assert g >= 25 * 16 * (48 * 64 + 90 * 128) * 8
