@@ -309,6 +309,94 @@ swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const void *d_imag
 #define SWIH_INJECT_DIRECT_GATHER 2
 swih_status swih_debug_inject(swih_plan_t plan, int what);
 
+/* ---------------------------------------------------------------- serving
+ * A server answers tracking queries (a crop of a resident frame, B, a kernel,
+ * 1..8 target histograms and 1..SWIH_MAX_SCALES windows) as they arrive. A
+ * scheduler thread inside the library admits waiting queries in micro-batches
+ * as stream slots and device memory free up (continuous batching): queries
+ * that share a frame, B and kernel run as one work set whose overlapping
+ * crops share integral histograms (merged only where that adds no pixels),
+ * and each micro-batch runs on its own stream, so micro-batches overlap on
+ * the device. All device memory the work needs comes from one arena of
+ * hbm_budget_bytes allocated at creation; a query waits until its work fits
+ * and is refused at submission if it can never fit. Results do not depend on
+ * which other queries share a micro-batch (integer integral histograms are
+ * exact wherever their origin lies). Errors of the server calls are reported
+ * by swih_last_error(NULL) on the calling thread. */
+typedef struct swih_server_s *swih_server_t;
+
+typedef struct swih_server_desc {
+    uint64_t hbm_budget_bytes;  /* device arena for work (bins, IHs, scan state, tables) */
+    int32_t max_inflight;       /* micro-batches on the device at once, 1..32 (one stream each) */
+    int32_t max_batch_queries;  /* queries admitted into one micro-batch, >= 1 */
+    int32_t merge_regions;      /* 1: overlapping crops of one frame share integral histograms */
+    int32_t gauss_degree;       /* as in swih_plan_desc */
+    double gauss_sigma_frac;
+    uint64_t staging_bytes;     /* pinned host staging for job tables (0: 64 MiB) */
+} swih_server_desc;
+
+typedef struct swih_frame_desc {
+    const void *d_pixels;       /* device frame, owned by the caller, read by every query on it */
+    int32_t height, width;
+    int64_t pitch_bytes;
+    int32_t pixel_type;         /* swih_pixel_type */
+    int32_t bitdepth;
+} swih_frame_desc;
+
+#define SWIH_MAX_TARGETS 8
+
+typedef struct swih_query {
+    int32_t frame;              /* id returned by swih_server_add_frame */
+    int32_t x0, y0, width, height;  /* crop, inside the frame, width <= 8192 */
+    int32_t bins;               /* B, 1..256 */
+    int32_t kernel;             /* swih_kernel */
+    int32_t n_targets;          /* 1..SWIH_MAX_TARGETS */
+    int32_t n_scales;           /* 1..SWIH_MAX_SCALES */
+    int32_t win_w[SWIH_MAX_SCALES], win_h[SWIH_MAX_SCALES];  /* odd, >= 3, <= crop */
+    const float *d_targets;     /* device [n_targets][bins] */
+    float *d_out;               /* device: n_targets * n_scales maps, target-major, each
+                                   (height - win_h + 1) x (width - win_w + 1), packed */
+    uint64_t user_tag;          /* returned in the completion */
+} swih_query;
+
+typedef struct swih_completion {
+    uint64_t id;                /* from swih_server_submit */
+    uint64_t user_tag;
+    int32_t status;             /* swih_status of the query's work */
+    int32_t batch_queries;      /* queries in its micro-batch */
+    uint64_t submit_ns, start_ns, done_ns;  /* steady-clock (CLOCK_MONOTONIC) times */
+} swih_completion;
+
+/* Create a server on the current device: allocates the arena and staging
+ * and starts the scheduler thread. */
+swih_status swih_server_create(const swih_server_desc *desc, swih_server_t *out);
+
+/* Register a resident frame; *frame_id is its handle for queries. The caller
+ * may rewrite the pixels between queries (not while queries on it run). */
+swih_status swih_server_add_frame(swih_server_t server, const swih_frame_desc *frame, int32_t *frame_id);
+
+/* Floats d_out must hold for a query (host only, no server needed). */
+swih_status swih_query_out_elems(const swih_query *query, uint64_t *elems);
+
+/* Arena bytes the query needs when it runs alone (host only). */
+swih_status swih_server_query_bytes(swih_server_t server, const swih_query *query, uint64_t *bytes);
+
+/* Validate and queue a query; returns at once. SWIH_ERR_BUDGET when the
+ * query alone needs more than the arena. */
+swih_status swih_server_submit(swih_server_t server, const swih_query *query, uint64_t *id);
+
+/* Move up to max completions into out (*n of them), waiting up to wait_us
+ * microseconds for the first when none is ready. */
+swih_status swih_server_poll(swih_server_t server, swih_completion *out, int32_t max, int32_t *n,
+                             int32_t wait_us);
+
+/* Block until every submitted query has completed (completions stay queued
+ * for swih_server_poll). */
+swih_status swih_server_drain(swih_server_t server);
+
+/* Drain, stop the scheduler and free the server. NULL is a no-op. */
+swih_status swih_server_destroy(swih_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

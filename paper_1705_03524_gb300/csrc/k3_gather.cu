@@ -93,10 +93,14 @@ __device__ __forceinline__ void axis_bernstein(const T (&R)[5], T c1, T c2, T c3
 template <int KIND, typename T>
 __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
 {
-    extern __shared__ float s_sq[];  // sqrt(q(b))
+    extern __shared__ float s_sq[];  // sqrt(q_t(b)), target-major
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int NT = p.n_targets;
     if (p.target) {
-        for (int i = tid; i < p.B; i += blockDim.x * blockDim.y) s_sq[i] = sqrtf(fmaxf(p.target[i], 0.f));
+        for (int i = tid; i < NT * p.B; i += blockDim.x * blockDim.y) {
+            const int t = i / p.B;
+            s_sq[i] = sqrtf(fmaxf(p.target[t * p.target_stride + (i - t * p.B)], 0.f));
+        }
         __syncthreads();
     }
     int ix = blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,7 +113,9 @@ __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
     const int Y0 = yc - p.ry - 1, Y1 = yc, Y2 = yc + p.ry;
     const T txc = (T)xc, tyc = (T)yc;
 
-    float acc = 0.f;
+    float acc[kMaxTargets];
+#pragma unroll
+    for (int t = 0; t < kMaxTargets; ++t) acc[t] = 0.f;
     float *hist = p.hist ? p.hist + ((int64_t)iy * p.ncx + ix) * p.B : nullptr;
     for (int b = 0; b < p.B; ++b) {
         float h;
@@ -186,9 +192,18 @@ __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
             h = s;
         }
         if (hist && valid) hist[b] = h;
-        if (p.target) acc = fmaf(sqrtf(h), s_sq[b], acc);
+        if (p.target) {
+            const float sq = sqrtf(h);
+#pragma unroll
+            for (int t = 0; t < kMaxTargets; ++t)
+                if (t < NT) acc[t] = fmaf(sq, s_sq[t * p.B + b], acc[t]);
+        }
     }
-    if (p.map && valid) p.map[(int64_t)iy * p.ncx + ix] = acc;
+    if (p.map && valid) {
+#pragma unroll
+        for (int t = 0; t < kMaxTargets; ++t)
+            if (t < NT) p.map[t * p.map_stride + (int64_t)iy * p.ncx + ix] = acc[t];
+    }
 }
 
 template <typename T>
@@ -196,7 +211,7 @@ cudaError_t launch_kind(const GatherParams &p, int kind, cudaStream_t s)
 {
     const dim3 block(32, 4);
     const dim3 grid((unsigned)((p.ncx + 31) / 32), (unsigned)((p.ncy + 3) / 4));
-    const size_t smem = sizeof(float) * (size_t)p.B;
+    const size_t smem = sizeof(float) * (size_t)p.B * (size_t)p.n_targets;
     switch (kind) {
     case kGatherPlain: gather_kernel<kGatherPlain, T><<<grid, block, smem, s>>>(p); break;
     case kGatherManhattan: gather_kernel<kGatherManhattan, T><<<grid, block, smem, s>>>(p); break;

@@ -189,7 +189,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);
     uint64_t *empty = full + kMaxStages;
     float *s_sq = reinterpret_cast<float *>(sm + 16 * kMaxStages);
-    float *s_acc = s_sq + p.B;
+    float *s_acc = s_sq + p.n_targets * p.B;
     T *stages = reinterpret_cast<T *>(sm + p.stage_off);
 
     constexpr int NWARP = TX / 32;
@@ -237,9 +237,15 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
         }
         mbar_init_fence();
     }
-    for (int i = tid; i < p.B; i += TX + 32) s_sq[i] = p.target ? sqrtf(fmaxf(p.target[i], 0.f)) : 0.f;
+    // sqrt(q_t(b)) of every target; one accumulator per (target, window, column)
+    const int NT = p.n_targets;
+    const int KC = p.kchain;
+    for (int i = tid; i < NT * p.B; i += TX + 32) {
+        const int t = i / p.B;
+        s_sq[i] = p.target ? sqrtf(fmaxf(p.target[t * p.target_stride + (i - t * p.B)], 0.f)) : 0.f;
+    }
     if (!producer)
-        for (int k = 0; k < KMAX; ++k) s_acc[k * TX + tid] = 0.f;
+        for (int k = 0; k < NT * KC; ++k) s_acc[k * TX + tid] = 0.f;
     if (xlo < 0) {  // column -1 of the integral histogram is 0; copies never land there
         for (int i = tid; i < NS * p.nl; i += TX + 32) stages[(size_t)i * p.seg + (A - 1)] = T(0);
     }
@@ -451,7 +457,12 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                                 const int yc = yc0 + done_k * h;
                                 p.hist[((int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)) * p.B + b] = hval;
                             }
-                            if (hval != 0.f) step_acc += sqrtf(hval) * s_sq[b];
+                            if (hval != 0.f) {
+                                const float sq = sqrtf(hval);
+                                step_acc += sq * s_sq[b];
+                                for (int t = 1; t < NT; ++t)
+                                    s_acc[(t * KC + done_k) * TX + tid] += sq * s_sq[t * p.B + b];
+                            }
                         }
                     }
                     if (done_k >= 0 && p.target) s_acc[done_k * TX + tid] += step_acc;
@@ -484,7 +495,10 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                     }
                     if (p.hist && valid_x)
                         p.hist[((int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)) * p.B + b0] = acc;
-                    if (p.target && occupied) s_acc[k * TX + tid] += sqrtf(acc) * s_sq[b0];
+                    if (p.target && occupied) {
+                        const float sq = sqrtf(acc);
+                        for (int t = 0; t < NT; ++t) s_acc[(t * KC + k) * TX + tid] += sq * s_sq[t * p.B + b0];
+                    }
                 }
             }
         }
@@ -494,10 +508,11 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
         return;
     }
     if (p.map && valid_x) {
-        for (int k = 0; k < K; ++k) {
-            const int yc = yc0 + k * h;
-            p.map[(int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)] = s_acc[k * TX + tid];
-        }
+        for (int t = 0; t < NT; ++t)
+            for (int k = 0; k < K; ++k) {
+                const int yc = yc0 + k * h;
+                p.map[t * p.map_stride + (int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)] = s_acc[(t * KC + k) * TX + tid];
+            }
     }
 }
 
@@ -644,7 +659,7 @@ struct TableLaunch {
 }  // namespace
 
 cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, int B, int nl_per_bin,
-                        int want_tx, int want_stages, int want_bb, GatherShape *shape)
+                        int n_targets, int want_tx, int want_stages, int want_bb, GatherShape *shape)
 {
     const bool gau = kind == kGatherGaussian;
     const int A = 16 / elem_bytes;
@@ -670,8 +685,9 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         sh.seg = (tx + max_w + 2 * A + A - 1) / A * A;
         sh.nl = bb * per_bin;
         sh.kchain_max = gau ? KMAX : KMAX / 2;
-        // shared memory: barriers | sqrt(target) | window sums | [Gaussian carry] | stages
-        sh.dtop_off = (16 * kMaxStages + 4 * B + 4 * KMAX * tx + 15) / 16 * 16;
+        sh.n_targets = std::max(1, std::min(n_targets, kMaxTargets));
+        // shared memory: barriers | sqrt(targets) | likelihood sums | [Gaussian carry] | stages
+        sh.dtop_off = (16 * kMaxStages + 4 * sh.n_targets * B + 4 * sh.n_targets * sh.kchain_max * tx + 15) / 16 * 16;
         const int carry = gau ? (2 * gdx + 1) * (2 * gdy + 1) * tx * 8 : 0;
         sh.stage_off = (sh.dtop_off + carry + 127) / 128 * 128;
         const size_t stage = (size_t)sh.nl * sh.seg * elem_bytes;
@@ -726,7 +742,7 @@ cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_byt
     if (p_in.ncx <= 0 || p_in.ncy <= 0) return cudaSuccess;
     GatherShape sh;
     cudaError_t e = tiled_shape(kind, elem_bytes, p_in.gdx, p_in.gdy, 2 * p_in.rx + 1, p_in.B, p_in.nl,
-                                p_in.want_tx, p_in.want_stages, p_in.want_bb, &sh);
+                                p_in.n_targets, p_in.want_tx, p_in.want_stages, p_in.want_bb, &sh);
     if (e != cudaSuccess) return e;
     GatherParams p = p_in;
     tiled_items(&p, sh);

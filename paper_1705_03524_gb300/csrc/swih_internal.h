@@ -106,8 +106,10 @@ struct GatherParams {
     unsigned long long rx2, rx4, ry2, ry4;  // r^2, r^4 per axis (ring constants)
     float gamma[3][3];      // Gaussian: beta_x[i] beta_y[j] / (rx^2Dx ry^2Dy M)
     float inv_mass;         // 1 / M (plain, Manhattan, Euclidean)
-    const float *target;    // [B] or null
-    float *map;             // [ncy][ncx] or null
+    const float *target;    // [n_targets][target_stride] (first B of each row used) or null
+    float *map;             // n_targets maps of [ncy][ncx], map_stride floats apart, or null
+    int n_targets;          // 1..kMaxTargets: one histogram per window, scored against each
+    int64_t target_stride, map_stride;
     float *hist;            // [ncy][ncx][B] or null
     // tiled gather only
     uint32_t *status;       // error bits (bounded waits)
@@ -127,6 +129,7 @@ cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaS
 // Tiled gather; returns cudaErrorNotSupported when a window's row segments do
 // not fit in shared memory (the caller then uses launch_gather).
 constexpr int kTiledChainMax = 8;
+constexpr int kMaxTargets = 8;
 cudaError_t launch_gather_tiled(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
 // Shape shared by every job of one tiled-gather launch: shared-memory layout
@@ -137,12 +140,13 @@ struct GatherShape {
     int bb;          // bins per pipeline step
     int seg, nl, nstage, stage_off, dtop_off;
     int kchain_max;  // windows per chain
+    int n_targets;   // likelihood accumulators per window (largest n_targets of the jobs)
     size_t smem;     // dynamic shared memory bytes
 };
 // Shape for jobs of one kind with the given fitted degrees, largest window
 // width and bin count; cudaErrorNotSupported when nothing fits.
 cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, int B, int nl_per_bin,
-                        int want_tx, int want_stages, int want_bb, GatherShape *shape);
+                        int n_targets, int want_tx, int want_stages, int want_bb, GatherShape *shape);
 // Fill a job's shape fields and chain split; returns its number of work items
 // (column tiles x chains).
 int tiled_items(GatherParams *job, const GatherShape &shape);

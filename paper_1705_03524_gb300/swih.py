@@ -125,6 +125,63 @@ class swih_roi_desc(ctypes.Structure):
     ]
 
 
+SWIH_MAX_TARGETS = 8
+
+
+class swih_server_desc(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_uint64),
+        ("max_inflight", ctypes.c_int32),
+        ("max_batch_queries", ctypes.c_int32),
+        ("merge_regions", ctypes.c_int32),
+        ("gauss_degree", ctypes.c_int32),
+        ("gauss_sigma_frac", ctypes.c_double),
+        ("staging_bytes", ctypes.c_uint64),
+    ]
+
+
+class swih_frame_desc(ctypes.Structure):
+    _fields_ = [
+        ("d_pixels", ctypes.c_void_p),
+        ("height", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("pitch_bytes", ctypes.c_int64),
+        ("pixel_type", ctypes.c_int32),
+        ("bitdepth", ctypes.c_int32),
+    ]
+
+
+class swih_query(ctypes.Structure):
+    _fields_ = [
+        ("frame", ctypes.c_int32),
+        ("x0", ctypes.c_int32),
+        ("y0", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("bins", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("n_targets", ctypes.c_int32),
+        ("n_scales", ctypes.c_int32),
+        ("win_w", ctypes.c_int32 * SWIH_MAX_SCALES),
+        ("win_h", ctypes.c_int32 * SWIH_MAX_SCALES),
+        ("d_targets", ctypes.c_void_p),
+        ("d_out", ctypes.c_void_p),
+        ("user_tag", ctypes.c_uint64),
+    ]
+
+
+class swih_completion(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_uint64),
+        ("user_tag", ctypes.c_uint64),
+        ("status", ctypes.c_int32),
+        ("batch_queries", ctypes.c_int32),
+        ("submit_ns", ctypes.c_uint64),
+        ("start_ns", ctypes.c_uint64),
+        ("done_ns", ctypes.c_uint64),
+    ]
+
+
 def _load() -> ctypes.CDLL:
     path = _build.LIB
     if not os.path.exists(path):
@@ -166,6 +223,22 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = S
     lib.swih_batch_destroy.argtypes = [P]
     lib.swih_batch_destroy.restype = S
+    SD, FD, QD = (ctypes.POINTER(swih_server_desc), ctypes.POINTER(swih_frame_desc),
+                  ctypes.POINTER(swih_query))
+    U64P = ctypes.POINTER(ctypes.c_uint64)
+    lib.swih_server_create.argtypes = [SD, ctypes.POINTER(P)]
+    lib.swih_server_add_frame.argtypes = [P, FD, ctypes.POINTER(ctypes.c_int32)]
+    lib.swih_query_out_elems.argtypes = [QD, U64P]
+    lib.swih_server_query_bytes.argtypes = [P, QD, U64P]
+    lib.swih_server_submit.argtypes = [P, QD, U64P]
+    lib.swih_server_poll.argtypes = [P, ctypes.POINTER(swih_completion), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+    lib.swih_server_drain.argtypes = [P]
+    lib.swih_server_destroy.argtypes = [P]
+    for name in ("swih_server_create", "swih_server_add_frame", "swih_query_out_elems",
+                 "swih_server_query_bytes", "swih_server_submit", "swih_server_poll",
+                 "swih_server_drain", "swih_server_destroy"):
+        getattr(lib, name).restype = S
     return lib
 
 
@@ -434,6 +507,115 @@ class Batch:
     def close(self):
         if self.handle:
             swih_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+
+def make_query(frame, x0, y0, width, height, bins, kernel, windows, targets, out, n_targets=1,
+               user_tag=0) -> swih_query:
+    """windows: [(w, h), ...]; targets: device [n_targets][bins]; out: device buffer of
+    swih_query_out_elems(q) floats (maps target-major, then scale, packed)."""
+    if not 1 <= len(windows) <= SWIH_MAX_SCALES:
+        raise ValueError("need 1..SWIH_MAX_SCALES windows")
+    q = swih_query()
+    q.frame, q.x0, q.y0, q.width, q.height = int(frame), int(x0), int(y0), int(width), int(height)
+    q.bins = int(bins)
+    q.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    q.n_targets = int(n_targets)
+    q.n_scales = len(windows)
+    for k, (w, h) in enumerate(windows):
+        q.win_w[k], q.win_h[k] = int(w), int(h)
+    q.d_targets = _ptr(targets)
+    q.d_out = _ptr(out)
+    q.user_tag = int(user_tag)
+    return q
+
+
+def swih_query_out_elems(q: swih_query) -> int:
+    out = ctypes.c_uint64(0)
+    _check(LIB.swih_query_out_elems(ctypes.byref(q), ctypes.byref(out)))
+    return int(out.value)
+
+
+def query_map_shapes(q: swih_query):
+    """[(offset, (rows, cols))] of every map in d_out, target-major then scale."""
+    shapes = []
+    off = 0
+    for _t in range(q.n_targets):
+        for k in range(q.n_scales):
+            r, c = q.height - q.win_h[k] + 1, q.width - q.win_w[k] + 1
+            shapes.append((off, (r, c)))
+            off += r * c
+    return shapes
+
+
+class Server:
+    """Owning wrapper of swih_server_*; frames are device buffers kept alive here."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=4, max_batch_queries=16, merge_regions=True,
+                 gauss_degree=0, gauss_sigma_frac=0.0, staging_bytes=0):
+        d = swih_server_desc()
+        d.hbm_budget_bytes = int(hbm_budget_bytes)
+        d.max_inflight = int(max_inflight)
+        d.max_batch_queries = int(max_batch_queries)
+        d.merge_regions = 1 if merge_regions else 0
+        d.gauss_degree = int(gauss_degree)
+        d.gauss_sigma_frac = float(gauss_sigma_frac)
+        d.staging_bytes = int(staging_bytes)
+        h = ctypes.c_void_p()
+        _check(LIB.swih_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = int(h.value)
+        self._frames = []
+
+    def add_frame(self, pixels, height, width, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8,
+                  bitdepth=None) -> int:
+        pb = 1 if pixel_type == SWIH_PIXEL_U8 else 2
+        f = swih_frame_desc()
+        f.d_pixels = _ptr(pixels)
+        f.height, f.width = int(height), int(width)
+        f.pitch_bytes = int(pitch_bytes if pitch_bytes is not None else width * pb)
+        f.pixel_type = int(pixel_type)
+        f.bitdepth = int(bitdepth if bitdepth is not None else 8 * pb)
+        fid = ctypes.c_int32(0)
+        _check(LIB.swih_server_add_frame(self.handle, ctypes.byref(f), ctypes.byref(fid)))
+        self._frames.append(pixels)
+        return int(fid.value)
+
+    def query_bytes(self, q: swih_query) -> int:
+        out = ctypes.c_uint64(0)
+        _check(LIB.swih_server_query_bytes(self.handle, ctypes.byref(q), ctypes.byref(out)))
+        return int(out.value)
+
+    def submit(self, q: swih_query) -> int:
+        qid = ctypes.c_uint64(0)
+        _check(LIB.swih_server_submit(self.handle, ctypes.byref(q), ctypes.byref(qid)))
+        return int(qid.value)
+
+    def poll(self, max_n=256, wait_us=0):
+        buf = (swih_completion * max_n)()
+        n = ctypes.c_int32(0)
+        _check(LIB.swih_server_poll(self.handle, buf, int(max_n), ctypes.byref(n), int(wait_us)))
+        return [buf[i] for i in range(n.value)]
+
+    def drain(self):
+        _check(LIB.swih_server_drain(self.handle))
+
+    def close(self):
+        if self.handle:
+            _check(LIB.swih_server_destroy(self.handle))
             self.handle = 0
 
     def __enter__(self):

@@ -26,6 +26,8 @@ __all__ = [
     "config1",
     "config2",
     "config3",
+    "config5_frames",
+    "config5_queries",
     "odd_window",
 ]
 
@@ -204,3 +206,70 @@ def config3(seed: int = 3, n_rois: int = 64, size: int = 4096, roi_range: tuple 
     img = np.clip(np.rint(img), 0, full - 1).astype(np.uint16)
     return dict(image=img, bitdepth=16, B=64, kernel="gaussian", rois=rois, windows=windows,
                 object_centres=centres)
+
+
+SERVE_WINDOWS = (15, 25, 43, 75, 127)
+
+
+def config5_frames(seed: int = 5, n_frames: int = 16, size: int = 2048, n_blobs: int = 50) -> list:
+    """Resident frames for the serving workload: one fBm background (16-bit
+    range, 2% Gaussian texture) shifted a few pixels per frame, with n_blobs
+    textured ellipses of 8-40 px moving at constant velocities; frame i holds
+    them at their positions at time i. Even frames are uint8 (the 16-bit
+    values >> 8), odd frames uint16. Returns [(image, bitdepth)]."""
+    rng = np.random.default_rng(seed)
+    full = float(1 << 16)
+    bg = 0.5 * full + 0.3 * full * fbm_value_noise(size + 64, size + 64, 4, 256.0, rng)
+    blobs = []
+    for _ in range(n_blobs):
+        a = float(rng.uniform(4, 20))
+        b = float(rng.uniform(4, 20))
+        blobs.append((float(rng.uniform(64, size - 64)), float(rng.uniform(64, size - 64)),
+                      float(rng.uniform(-6, 6)), float(rng.uniform(-6, 6)), a, b,
+                      float(rng.uniform(0, np.pi)), float(rng.integers(int(0.15 * full), int(0.85 * full)))))
+    frames = []
+    for i in range(n_frames):
+        dx, dy = (3 * i) % 64, (2 * i) % 64
+        img = bg[dy: dy + size, dx: dx + size].copy()
+        img += rng.normal(0.0, 0.02 * full, size=img.shape)
+        for (x, y, vx, vy, a, b, ang, mean) in blobs:
+            cx = int(np.clip(x + vx * i, 0, size - 1))
+            cy = int(np.clip(y + vy * i, 0, size - 1))
+            _plant_ellipse(img, rng, cx, cy, a, b, ang, mean, 0.05 * full)
+        img = np.clip(np.rint(img), 0, full - 1)
+        if i % 2 == 0:
+            frames.append(((img.astype(np.uint32) >> 8).astype(np.uint8), 8))
+        else:
+            frames.append((img.astype(np.uint16), 16))
+    return frames
+
+
+def config5_queries(seed: int = 5, n: int = 1000, rate: float = 2000.0, n_frames: int = 16,
+                    size: int = 2048, crop_range: tuple = (64, 1024)) -> list:
+    """A Poisson stream of tracking queries: arrival times with mean rate
+    ``rate`` per second, a frame drawn uniformly, crop width and height drawn
+    independently from U{64..1024} at a uniform position, B from {16, 32, 64},
+    kernel from {Manhattan, Euclidean, Gaussian}, 1-8 targets (seeded
+    normalised histograms) and 1-5 windows drawn from the sizes
+    15/25/43/75/127 that fit the crop. Returns a list of dicts."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    kernels = ("manhattan", "euclidean", "gaussian")
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        w = int(rng.integers(crop_range[0], crop_range[1] + 1))
+        h = int(rng.integers(crop_range[0], crop_range[1] + 1))
+        x0 = int(rng.integers(0, size - w + 1))
+        y0 = int(rng.integers(0, size - h + 1))
+        B = int(rng.choice([16, 32, 64]))
+        kernel = kernels[int(rng.integers(0, 3))]
+        nt = int(rng.integers(1, 9))
+        fit = [s for s in SERVE_WINDOWS if s <= min(w, h)]
+        ns = min(int(rng.integers(1, 6)), len(fit))
+        wins = sorted(int(v) for v in rng.choice(fit, ns, replace=False))
+        targets = rng.gamma(0.5, 1.0, size=(nt, B))
+        targets /= targets.sum(1, keepdims=True)
+        out.append(dict(t=t, frame=int(rng.integers(0, n_frames)), x0=x0, y0=y0, w=w, h=h, B=B,
+                        kernel=kernel, windows=[(v, v) for v in wins], targets=targets.astype(np.float32)))
+    return out
