@@ -16,6 +16,12 @@ dominant kernel (CUDA events on the launching stream), SM clocks sampled
 during the timed region, and the CPU oracle timed on the host cores on a
 bounded sample of the same workload.
 
+At N = 1 the line also carries two measurements of the many-region paths:
+"batched_regions" (64 search regions of a 4096x4096 u16 frame, one batch
+replayed as a CUDA graph against one plan per region) and "serving" (a Poisson
+stream of tracking queries at 2000/s against 16 resident frames: the server's
+continuous batching against one plan per query, with p50/p99 latency).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swih|reference]
 """
 from __future__ import annotations
@@ -38,7 +44,7 @@ sys.path.insert(0, ROOT)
 
 KERNELS = ("manhattan", "euclidean", "gaussian")
 WINDOWS = (21, 41, 81)
-METRIC = "SWIH windows/s"
+METRIC = "SWIH windows/s & HBM-roofline %; served p50/p99 latency vs plain per-ROI path"
 WORKLOAD = ("1024x1024 u8 synthetic tracking scene (fBm background + 8 textured ellipses), "
             "B=32, Manhattan/Euclidean/Gaussian(sigma=w/4) kernels x windows 21/41/81, "
             "full valid likelihood map per kernel and window")
@@ -357,6 +363,193 @@ def run_swih(args, rank, world, local_rank):
     return line
 
 
+# ----------------------------------------------------------------------------- batches
+def run_regions(args, dev):
+    """64 search regions of 96-768 px from a 4096x4096 u16 frame (B = 64,
+    Gaussian, 3 scales): one batch (CUDA graph: one quantise, one scan, one
+    gather launch per job group) against one plan per region (its own
+    quantise, scan and three gathers), each timed with CUDA events over
+    whole steps."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    cfg = synth.config3()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    d_img = torch.from_numpy(img.view(np.int16)).to(dev)
+    ptr, pitch = d_img.data_ptr(), W * 2
+    stream = torch.cuda.Stream(device=dev)
+    rois, wins = cfg["rois"], cfg["windows"]
+    wps = sum((w - k + 1) * (h - k + 1) for (_, _, w, h), ks in zip(rois, wins) for k in ks)
+    maps = [[torch.empty((h - k + 1, w - k + 1), device=dev) for k in ks] for (_, _, w, h), ks in zip(rois, wins)]
+    targets = torch.empty((len(rois), B), device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(3, min(args.steps, 10))
+
+    # one plan per region; targets = each region's object window at scale 1 (set-up)
+    plans = []
+    for i, ((x0, y0, w, h), ks, (ox, oy)) in enumerate(zip(rois, wins, cfg["object_centres"])):
+        p = S.Plan(S.make_desc(h, w, pitch_bytes=pitch, pixel_type=S.SWIH_PIXEL_U16, bitdepth=16, bins=B,
+                               kernels=("gaussian",), max_win=(max(ks), max(ks))))
+        p.build_ih(ptr + y0 * pitch + x0 * 2, stream)
+        r = ks[1] // 2
+        p.local_hist("gaussian", ks[1], ks[1], min(max(ox - x0, r), w - 1 - r), min(max(oy - y0, r), h - 1 - r),
+                     1, 1, targets[i], stream)
+        plans.append(p)
+
+    def per_roi_step():
+        for p, (x0, y0, w, h), ks, ms, i in zip(plans, rois, wins, maps, range(len(rois))):
+            p.build_ih(ptr + y0 * pitch + x0 * 2, stream)
+            for k, m in zip(ks, ms):
+                p.likelihood("gaussian", k, k, targets[i], m, stream)
+
+    for _ in range(2):
+        per_roi_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        per_roi_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_roi_ms = e0.elapsed_time(e1) / steps
+    for p in plans:
+        p.sync_status(stream)
+        p.close()
+    ref = [[m.clone() for m in ms] for ms in maps]
+    plans = None
+    torch.cuda.empty_cache()
+
+    desc = S.make_batch_desc(H, W, pitch_bytes=pitch, pixel_type=S.SWIH_PIXEL_U16, bitdepth=16, bins=B,
+                             kernels=("gaussian",))
+    rl = [S.make_roi(x0, y0, w, h, "gaussian", [(k, k) for k in ks], targets[i], ms)
+          for i, ((x0, y0, w, h), ks, ms) in enumerate(zip(rois, wins, maps))]
+    ws_bytes = S.swih_batch_workspace_bytes(desc, rl)
+    with S.Batch(desc, rl, ptr) as b:
+        b.autotune(stream)
+        for _ in range(2):
+            b.run(stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            b.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.sync_status(stream)
+        batch_ms = e0.elapsed_time(e1) / steps
+    diff = max((m - r).abs().max().item() for ms, rs in zip(maps, ref) for m, r in zip(ms, rs))
+    del maps, ref
+    torch.cuda.empty_cache()
+    return {
+        "workload": ("64 regions of U{96..768}^2 px from a 4096x4096 u16 frame, B=64, Gaussian "
+                     "(sigma=w/4), 3 scales 0.8/1/1.25 x a 24-64 px box, full valid maps"),
+        "windows_per_step": wps, "steps": steps,
+        "batch": {"ms_per_step": batch_ms, "windows_per_s": wps / (batch_ms * 1e-3),
+                  "launches_per_step": "1 quantise + 1 scan + 1 gather per job group (graph replay)",
+                  "workspace_gb": ws_bytes / 1e9},
+        "per_region_plans": {"ms_per_step": per_roi_ms, "windows_per_s": wps / (per_roi_ms * 1e-3),
+                             "launches_per_step": 6 * len(rois)},
+        "speedup": per_roi_ms / batch_ms,
+        "max_abs_diff_batch_vs_per_region": diff,
+    }
+
+
+# ----------------------------------------------------------------------------- serving
+def run_serving(args, dev, n_queries=400, rate=2000.0):
+    """A Poisson stream of tracking queries against 16 resident 2048x2048
+    frames: the server (continuous batching) against the plain path (one plan
+    per query, processed one at a time in arrival order). Latency = completion
+    - arrival (host monotonic clock); the same stream and arrival times for
+    both."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    frames = synth.config5_frames()
+    qs = synth.config5_queries(n=n_queries, rate=rate)
+    d_frames = [torch.from_numpy(img if img.dtype == np.uint8 else img.view(np.int16)).to(dev) for img, _ in frames]
+    targets = [torch.from_numpy(q["targets"]).to(dev) for q in qs]
+
+    def n_eval(q):
+        return len(q["targets"]) * sum((q["h"] - h + 1) * (q["w"] - w + 1) for w, h in q["windows"])
+
+    total = sum(n_eval(q) for q in qs)
+    outs = [torch.empty(n_eval(q), device=dev) for q in qs]
+    torch.cuda.synchronize()
+
+    def stats(lat_ms, span_s):
+        return {"queries_per_s": len(lat_ms) / span_s, "windows_per_s": total / span_s,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "span_s": span_s}
+
+    srv_cfg = dict(hbm_budget_bytes=96 << 30, max_inflight=8, max_batch_queries=8, merge_regions=True)
+    with S.Server(**srv_cfg) as srv:
+        ids = []
+        for (img, bd), d in zip(frames, d_frames):
+            pt = S.SWIH_PIXEL_U8 if img.dtype == np.uint8 else S.SWIH_PIXEL_U16
+            ids.append(srv.add_frame(d, img.shape[0], img.shape[1], pixel_type=pt, bitdepth=bd))
+        qq = [S.make_query(ids[q["frame"]], q["x0"], q["y0"], q["w"], q["h"], q["B"], q["kernel"], q["windows"],
+                           targets[i], outs[i], n_targets=len(q["targets"]), user_tag=i) for i, q in enumerate(qs)]
+        for i in range(8):  # warm-up
+            srv.submit(qq[i])
+        srv.drain()
+        srv.poll(64)
+        t0 = time.monotonic_ns()
+        arrival = []
+        for i, q in enumerate(qs):
+            a = t0 + int(q["t"] * 1e9)
+            while time.monotonic_ns() < a:
+                pass
+            arrival.append(a)
+            srv.submit(qq[i])
+        srv.drain()
+        comps = srv.poll(n_queries + 16)
+    bad = sum(c.status != 0 for c in comps)
+    lat = [(c.done_ns - arrival[c.user_tag]) / 1e6 for c in comps]
+    server = stats(lat, (max(c.done_ns for c in comps) - t0) / 1e9)
+    server.update({"mean_queries_per_micro_batch": float(np.mean([c.batch_queries for c in comps])),
+                   "failed": bad, "config": {k: v for k, v in srv_cfg.items()}})
+    server_out = [o.clone() for o in outs]
+
+    stream = torch.cuda.Stream(device=dev)
+    lat = []
+    t0 = time.monotonic_ns()
+    for i, q in enumerate(qs):
+        a = t0 + int(q["t"] * 1e9)
+        while time.monotonic_ns() < a:
+            pass
+        img, bd = frames[q["frame"]]
+        pb = img.dtype.itemsize
+        W = img.shape[1]
+        mw = max(w for w, _ in q["windows"])
+        desc = S.make_desc(q["h"], q["w"], pitch_bytes=W * pb, pixel_type=S.SWIH_PIXEL_U8 if pb == 1 else S.SWIH_PIXEL_U16,
+                           bitdepth=bd, bins=q["B"], kernels=(q["kernel"],), max_win=(mw, mw))
+        with S.Plan(desc) as p:
+            p.build_ih(d_frames[q["frame"]].data_ptr() + (q["y0"] * W + q["x0"]) * pb, stream)
+            off = 0
+            for t in range(len(q["targets"])):
+                for (w, h) in q["windows"]:
+                    p.likelihood(q["kernel"], w, h, targets[i][t], outs[i].data_ptr() + 4 * off, stream)
+                    off += (q["h"] - h + 1) * (q["w"] - w + 1)
+            p.sync_status(stream)
+        lat.append((time.monotonic_ns() - a) / 1e6)
+    plain = stats(lat, (time.monotonic_ns() - t0) / 1e9)
+    diff = max((a - b).abs().max().item() for a, b in zip(outs, server_out))
+    return {
+        "workload": (f"{n_queries} queries, Poisson {rate:.0f}/s, 16 resident 2048x2048 u8/u16 frames, crops "
+                     "U{64..1024}^2, B in {16,32,64}, M/E/G kernel, 1-8 targets, 1-5 windows of "
+                     "15/25/43/75/127"),
+        "windows_per_query_mean": total / n_queries,
+        "server": server, "plain_per_query": plain,
+        "p99_ratio_plain_over_server": plain["p99_ms"] / server["p99_ms"],
+        "throughput_ratio_server_over_plain": server["queries_per_s"] / plain["queries_per_s"],
+        "max_abs_diff_server_vs_plain": diff,
+    }
+
+
 # ----------------------------------------------------------------------------- oracle
 def oracle_sample(budget_s: float, seed: int = 7):
     """Time the CPU oracle on random valid centres of the same workload (all nine
@@ -439,6 +632,9 @@ def main():
     ap.add_argument("--impl", choices=("swih", "reference"), default="swih")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-regions and serving measurements (profiling runs)")
+    ap.add_argument("--serve-queries", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "swih":
         args.warmup = 3
@@ -463,6 +659,12 @@ def main():
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     line = run_swih(args, rank, world, local_rank)
+    if world == 1 and not args.no_extras:
+        import torch
+        torch.cuda.empty_cache()
+        dev = torch.device("cuda", local_rank)
+        line["batched_regions"] = run_regions(args, dev)
+        line["serving"] = run_serving(args, dev, n_queries=args.serve_queries)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(args.cpu_seconds)
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -309,6 +309,47 @@ swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const void *d_imag
 #define SWIH_INJECT_DIRECT_GATHER 2
 swih_status swih_debug_inject(swih_plan_t plan, int what);
 
+/* ---------------------------------------------------------------- streamed frames
+ * Likelihood maps over a frame whose integral histograms do not fit in device
+ * memory at once (the paper's wide-area imagery, Sec. 4). The frame is cut
+ * into bands of band_height centre rows; a band's integral histograms cover
+ * its rows plus a halo of (tallest window - 1) rows, are built, gathered for
+ * every job's centres in the band and then overwritten by the next band's.
+ * Results equal those of one plan over the whole frame (integer integral
+ * histograms are exact at any origin). The pass over all bands is captured
+ * into a CUDA graph at the first run. */
+typedef struct swih_frame_job {
+    int32_t kernel;             /* swih_kernel, in the desc's kernel_mask */
+    int32_t win_w, win_h;       /* odd, >= 3 */
+    const float *d_target;      /* device [bins] */
+    float *d_map;               /* device [(height - win_h + 1) x (width - win_w + 1)], the frame's valid map */
+} swih_frame_job;
+
+typedef struct swih_stream_s *swih_stream_t;
+
+/* Plan a streamed pass over the frame d_image (device, desc->height rows of
+ * desc->pitch_bytes, caller-owned, read at every run; the caller may rewrite
+ * its contents between runs). desc->max_win_w/max_win_h are ignored (taken
+ * from the jobs); desc->band_rows is the scan's band height as for plans.
+ * band_height = centre rows per band; 0 picks the largest that keeps the
+ * workspace within desc->hbm_budget_bytes (which must then be set).
+ * SWIH_ERR_BUDGET when even 1-row bands do not fit. */
+swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *jobs, int n_jobs,
+                             const void *d_image, int32_t band_height, swih_stream_t *out);
+
+/* Enqueue one pass (every band, every job) on the stream. */
+swih_status swih_stream_run(swih_stream_t st, void *stream);
+
+/* As swih_sync_status, for a streamed pass. */
+swih_status swih_stream_sync_status(swih_stream_t st, void *stream);
+
+/* Band height, band count and device workspace of a streamed pass. */
+swih_status swih_stream_get_info(swih_stream_t st, int32_t *band_height, int32_t *n_bands,
+                                 uint64_t *workspace_bytes);
+
+/* Free it (synchronises the device). NULL is a no-op. */
+swih_status swih_stream_destroy(swih_stream_t st);
+
 /* ---------------------------------------------------------------- serving
  * A server answers tracking queries (a crop of a resident frame, B, a kernel,
  * 1..8 target histograms and 1..SWIH_MAX_SCALES windows) as they arrive. A

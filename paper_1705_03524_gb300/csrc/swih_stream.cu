@@ -1,0 +1,279 @@
+// Streamed frames (swih_stream_*): likelihood maps over a frame whose
+// integral histograms do not fit in device memory, one band of rows at a time.
+//
+// With R = (tallest window - 1) / 2, band k owns the centre rows
+// [R + k Hb, R + (k+1) Hb) (the first band from row 0, the last up to the
+// frame's end, so that shorter windows keep every valid centre); its region
+// is the frame rows [k Hb, (k+1) Hb + 2R), which holds every window around
+// those centres. Each band is a work set over one region whose jobs write
+// straight into the frame-sized maps at the rows the band owns. All bands use
+// the same device memory in turn: on one stream, band k+1's table upload and
+// launches follow band k's gathers, so nothing is overwritten early.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "swih_host.h"
+
+using namespace swih;
+
+struct swih_stream_s {
+    swih_plan_desc desc;
+    std::vector<swih_frame_job> jobs;
+    const void *image = nullptr;
+    int band_h = 0, n_bands = 0, R = 0;
+    std::vector<std::unique_ptr<WorkSet>> bands;
+    char *d_mem = nullptr;
+    uint64_t bytes = 0;
+    char *h_tables = nullptr;  // pinned copies of every band's tables
+    std::vector<uint64_t> tab_off;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+swih_status tfail(swih_status st, const std::string &msg)
+{
+    thread_error() = msg;
+    return st;
+}
+
+WorkSpec spec_of(const swih_plan_desc &d)
+{
+    WorkSpec sp;
+    sp.pixel_type = d.pixel_type;
+    sp.bitdepth = d.bitdepth;
+    sp.bins = d.bins;
+    sp.kernel_mask = d.kernel_mask;
+    sp.gauss_degree = d.gauss_degree;
+    sp.gauss_sigma_frac = d.gauss_sigma_frac;
+    sp.precision = d.precision;
+    sp.band_rows = d.band_rows;
+    return sp;
+}
+
+// Lay out band k of a pass with band height Hb (host only).
+swih_status plan_band(const swih_stream_s &S, int Hb, int n_bands, int k, WorkSet &ws, std::string &err)
+{
+    const int H = S.desc.height, W = S.desc.width, R = S.R;
+    const int y0 = k * Hb;
+    const int y1 = k == n_bands - 1 ? H : std::min(H, (k + 1) * Hb + 2 * R);
+    const int lo = k == 0 ? 0 : R + k * Hb;
+    const int hi = k == n_bands - 1 ? H : R + (k + 1) * Hb;
+    WorkRegion reg;
+    reg.image = static_cast<const uint8_t *>(S.image) + (int64_t)y0 * S.desc.pitch_bytes;
+    reg.pitch = S.desc.pitch_bytes;
+    reg.H = y1 - y0;
+    reg.W = W;
+    std::vector<WorkJob> jobs;
+    for (const swih_frame_job &fj : S.jobs) {
+        const int rx = (fj.win_w - 1) / 2, ry = (fj.win_h - 1) / 2;
+        const int c_lo = std::max(lo, ry), c_hi = std::min(hi, H - ry);
+        if (c_hi <= c_lo) continue;
+        WorkJob jb;
+        jb.region = 0;
+        jb.kernel = fj.kernel;
+        jb.w = fj.win_w;
+        jb.h = fj.win_h;
+        jb.cx0 = rx;
+        jb.ncx = W - fj.win_w + 1;
+        jb.cy0 = c_lo - y0;
+        jb.ncy = c_hi - c_lo;
+        jb.target = fj.d_target;
+        jb.map = fj.d_map + (int64_t)(c_lo - ry) * jb.ncx;
+        jobs.push_back(jb);
+    }
+    return ws.plan(spec_of(S.desc), {reg}, jobs, err);
+}
+
+// Every band for band height Hb; bytes = the largest band's memory.
+swih_status plan_bands(swih_stream_s &S, int Hb, std::vector<std::unique_ptr<WorkSet>> &out, uint64_t &bytes,
+                       std::string &err)
+{
+    const int rows = S.desc.height - 2 * S.R;  // centre rows of the tallest window
+    const int n = std::max(1, (rows + Hb - 1) / Hb);
+    out.clear();
+    bytes = 0;
+    for (int k = 0; k < n; ++k) {
+        std::unique_ptr<WorkSet> ws(new WorkSet());
+        const swih_status st = plan_band(S, Hb, n, k, *ws, err);
+        if (st != SWIH_OK) return st;
+        bytes = std::max(bytes, ws->bytes());
+        out.push_back(std::move(ws));
+    }
+    return SWIH_OK;
+}
+
+swih_status capture(swih_stream_s *S)
+{
+    cudaError_t e = cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaStreamBeginCapture", e);
+    cudaError_t le = cudaSuccess;
+    for (size_t k = 0; k < S->bands.size() && le == cudaSuccess; ++k) {
+        WorkSet &ws = *S->bands[k];
+        le = cudaMemcpyAsync(ws.tables_device(), S->h_tables + S->tab_off[k], ws.tables_bytes(),
+                             cudaMemcpyHostToDevice, S->cap);
+        if (le == cudaSuccess) le = ws.enqueue(S->cap, false);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(S->cap, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(nullptr, "streamed pass launch (capture)", le);
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaStreamEndCapture", e);
+    S->graph = g;
+    e = cudaGraphInstantiate(&S->exec, g, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaGraphInstantiate", e);
+    return SWIH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *jobs, int n_jobs, const void *d_image,
+                             int32_t band_height, swih_stream_t *out)
+{
+    if (!out) return tfail(SWIH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc || !jobs || n_jobs < 1 || !d_image)
+        return tfail(SWIH_ERR_INVALID_ARG, "desc, jobs (n_jobs >= 1) and d_image are required");
+    if (band_height < 0) return tfail(SWIH_ERR_INVALID_ARG, "band_height must be >= 0");
+    if (band_height == 0 && desc->hbm_budget_bytes == 0)
+        return tfail(SWIH_ERR_INVALID_ARG, "band_height 0 needs hbm_budget_bytes");
+    if (desc->height < 3 || desc->width < 3) return tfail(SWIH_ERR_INVALID_ARG, "frame must be at least 3 x 3");
+    std::unique_ptr<swih_stream_s> S(new swih_stream_s());
+    S->desc = *desc;
+    S->jobs.assign(jobs, jobs + n_jobs);
+    S->image = d_image;
+    int hmax = 3;
+    for (int j = 0; j < n_jobs; ++j) {
+        const swih_frame_job &fj = jobs[j];
+        if (!odd_window(fj.win_w) || !odd_window(fj.win_h) || fj.win_w > desc->width || fj.win_h > desc->height)
+            return tfail(SWIH_ERR_INVALID_ARG, "job " + std::to_string(j) + ": window must be odd, >= 3, inside the frame");
+        if (!fj.d_target || !fj.d_map) return tfail(SWIH_ERR_INVALID_ARG, "job " + std::to_string(j) + ": NULL target or map");
+        hmax = std::max(hmax, fj.win_h);
+    }
+    S->R = (hmax - 1) / 2;
+    const int rows = desc->height - 2 * S->R;
+    std::string err;
+    uint64_t bytes = 0;
+    int Hb = band_height > 0 ? std::min(band_height, std::max(1, rows)) : 0;
+    if (Hb == 0) {
+        // the largest band height whose band fits the budget (memory grows with it)
+        int lo = 1, hi = std::max(1, rows), best = 0;
+        while (lo <= hi) {
+            const int mid = lo + (hi - lo) / 2;
+            std::unique_ptr<WorkSet> ws(new WorkSet());
+            const int n = std::max(1, (rows + mid - 1) / mid);
+            swih_status st = plan_band(*S, mid, n, n > 1 ? 1 : 0, *ws, err);
+            if (st == SWIH_OK && n > 1) {  // the first band can be the tallest region too
+                std::unique_ptr<WorkSet> w0(new WorkSet());
+                st = plan_band(*S, mid, n, 0, *w0, err);
+                if (st == SWIH_OK && w0->bytes() > ws->bytes()) ws = std::move(w0);
+            }
+            if (st != SWIH_OK) return tfail(st, err);
+            if (ws->bytes() <= desc->hbm_budget_bytes) {
+                best = mid;
+                lo = mid + 1;
+            } else {
+                hi = mid - 1;
+            }
+        }
+        if (best == 0) return tfail(SWIH_ERR_BUDGET, "even one-row bands exceed hbm_budget_bytes");
+        Hb = best;
+    }
+    for (;;) {
+        const swih_status st = plan_bands(*S, Hb, S->bands, bytes, err);
+        if (st != SWIH_OK) return tfail(st, err);
+        if (!desc->hbm_budget_bytes || bytes <= desc->hbm_budget_bytes) break;
+        if (Hb == 1) return tfail(SWIH_ERR_BUDGET, "even one-row bands exceed hbm_budget_bytes");
+        Hb = std::max(1, Hb - std::max(1, Hb / 16));  // a last band taller than the probe: shrink
+    }
+    S->band_h = Hb;
+    S->n_bands = (int)S->bands.size();
+    S->bytes = bytes;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->d_mem), bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(nullptr, "cudaMalloc(stream workspace)", e);
+    }
+    uint64_t tab_total = 0;
+    for (auto &ws : S->bands) {
+        const swih_status st = ws->bind(S->d_mem, err);
+        if (st != SWIH_OK) {
+            cudaFree(S->d_mem);
+            return tfail(st, err);
+        }
+        S->tab_off.push_back(tab_total);
+        tab_total += (ws->tables_bytes() + 255) / 256 * 256;
+    }
+    e = cudaMallocHost(reinterpret_cast<void **>(&S->h_tables), std::max<uint64_t>(tab_total, 256));
+    if (e == cudaSuccess) e = cudaMemset(S->d_mem, 0, 256);  // status word
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        swih_stream_destroy(S.release());
+        return cuda_fail(nullptr, "stream set-up", e);
+    }
+    for (size_t k = 0; k < S->bands.size(); ++k)
+        std::memcpy(S->h_tables + S->tab_off[k], S->bands[k]->tables(), S->bands[k]->tables_bytes());
+    *out = S.release();
+    return SWIH_OK;
+}
+
+swih_status swih_stream_run(swih_stream_t S, void *stream)
+{
+    if (!S) return tfail(SWIH_ERR_INVALID_ARG, "stream plan is NULL");
+    if (!S->exec) {
+        const swih_status st = capture(S);
+        if (st != SWIH_OK) return st;
+    }
+    const cudaError_t e = cudaGraphLaunch(S->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaGraphLaunch", e);
+    return SWIH_OK;
+}
+
+swih_status swih_stream_sync_status(swih_stream_t S, void *stream)
+{
+    if (!S) return tfail(SWIH_ERR_INVALID_ARG, "stream plan is NULL");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaStreamSynchronize", e);
+    uint32_t word = 0;
+    e = cudaMemcpy(&word, S->d_mem, sizeof word, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaMemcpy(status)", e);
+    if (word) {
+        cudaMemset(S->d_mem, 0, sizeof word);
+        if (word & kStatusTimeout) return tfail(SWIH_ERR_TIMEOUT, "a bounded device wait gave up");
+    }
+    return SWIH_OK;
+}
+
+swih_status swih_stream_get_info(swih_stream_t S, int32_t *band_height, int32_t *n_bands, uint64_t *workspace_bytes)
+{
+    if (!S) return tfail(SWIH_ERR_INVALID_ARG, "stream plan is NULL");
+    if (band_height) *band_height = S->band_h;
+    if (n_bands) *n_bands = S->n_bands;
+    if (workspace_bytes) *workspace_bytes = S->bytes;
+    return SWIH_OK;
+}
+
+swih_status swih_stream_destroy(swih_stream_t S)
+{
+    if (!S) return SWIH_OK;
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->cap) cudaStreamDestroy(S->cap);
+    cudaError_t e = cudaSuccess;
+    if (S->d_mem) e = cudaFree(S->d_mem);
+    if (S->h_tables) cudaFreeHost(S->h_tables);
+    delete S;
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cudaFree", e);
+    return SWIH_OK;
+}
+
+}  // extern "C"

@@ -182,6 +182,16 @@ class swih_completion(ctypes.Structure):
     ]
 
 
+class swih_frame_job(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_int32),
+        ("win_w", ctypes.c_int32),
+        ("win_h", ctypes.c_int32),
+        ("d_target", ctypes.c_void_p),
+        ("d_map", ctypes.c_void_p),
+    ]
+
+
 def _load() -> ctypes.CDLL:
     path = _build.LIB
     if not os.path.exists(path):
@@ -235,6 +245,16 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.swih_server_drain.argtypes = [P]
     lib.swih_server_destroy.argtypes = [P]
+    lib.swih_stream_plan.argtypes = [ctypes.POINTER(swih_plan_desc), ctypes.POINTER(swih_frame_job), I, P,
+                                     ctypes.c_int32, ctypes.POINTER(P)]
+    lib.swih_stream_run.argtypes = [P, P]
+    lib.swih_stream_sync_status.argtypes = [P, P]
+    lib.swih_stream_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+    lib.swih_stream_destroy.argtypes = [P]
+    for name in ("swih_stream_plan", "swih_stream_run", "swih_stream_sync_status", "swih_stream_get_info",
+                 "swih_stream_destroy"):
+        getattr(lib, name).restype = S
     for name in ("swih_server_create", "swih_server_add_frame", "swih_query_out_elems",
                  "swih_server_query_bytes", "swih_server_submit", "swih_server_poll",
                  "swih_server_drain", "swih_server_destroy"):
@@ -616,6 +636,59 @@ class Server:
     def close(self):
         if self.handle:
             _check(LIB.swih_server_destroy(self.handle))
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- streamed frames
+
+def make_frame_job(kernel, win_w, win_h, target, out_map) -> swih_frame_job:
+    j = swih_frame_job()
+    j.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    j.win_w, j.win_h = int(win_w), int(win_h)
+    j.d_target = _ptr(target)
+    j.d_map = _ptr(out_map)
+    return j
+
+
+class Stream:
+    """Owning wrapper of swih_stream_*: likelihood maps of a large frame, band by band."""
+
+    def __init__(self, desc: swih_plan_desc, jobs, image, band_height=0, keep=()):
+        arr = (swih_frame_job * len(jobs))()
+        for i, j in enumerate(jobs):
+            arr[i] = j
+        h = ctypes.c_void_p()
+        _check(LIB.swih_stream_plan(ctypes.byref(desc), arr, len(jobs), _ptr(image), int(band_height),
+                                    ctypes.byref(h)))
+        self.handle = int(h.value)
+        self._keep = (image, tuple(keep))
+
+    def run(self, stream=None):
+        _check(LIB.swih_stream_run(self.handle, _stream(stream)))
+
+    def sync_status(self, stream=None):
+        _check(LIB.swih_stream_sync_status(self.handle, _stream(stream)))
+
+    def info(self):
+        bh, nb, wb = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_uint64(0)
+        _check(LIB.swih_stream_get_info(self.handle, ctypes.byref(bh), ctypes.byref(nb), ctypes.byref(wb)))
+        return dict(band_height=bh.value, n_bands=nb.value, workspace_bytes=wb.value)
+
+    def close(self):
+        if self.handle:
+            _check(LIB.swih_stream_destroy(self.handle))
             self.handle = 0
 
     def __enter__(self):
