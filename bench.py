@@ -20,7 +20,9 @@ At N = 1 the line also carries two measurements of the many-region paths:
 "batched_regions" (64 search regions of a 4096x4096 u16 frame, one batch
 replayed as a CUDA graph against one plan per region) and "serving" (a Poisson
 stream of tracking queries at 2000/s against 16 resident frames: the server's
-continuous batching against one plan per query, with p50/p99 latency).
+continuous batching against one plan per query, with p50/p99 latency), and
+"large_frame" (an 8192x8192 u16 frame whose integral histograms exceed device
+memory, streamed in bands).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swih|reference]
 """
@@ -280,7 +282,7 @@ def run_swih(args, rank, world, local_rank):
     dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
     peak, peak_kind = read_peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    src = "k2_ih_scan.cu" if dom.startswith("ih_scan") else "k3_gather.cu"
+    src = "k2_ih_scan.cu" if dom.startswith("ih_scan") else "k3_gather_tiled.cu"
     prof = "ih_scan_gaussian_1024" if dom.startswith("ih_scan (G") else (
         "gather_gaussian_1024" if dom == "gather Gaussian" else None)
     if H != 1024 or B != 32:
@@ -456,6 +458,60 @@ def run_regions(args, dev):
     }
 
 
+# ----------------------------------------------------------------------------- large frame
+def run_large_frame(args, dev, budget_gb=100):
+    """8192x8192 u16 frame, B = 64, Gaussian and Euclidean kernels at windows
+    15/25/43/75/127: the integral histograms (25 terms, 64-bit) would need
+    ~860 GB, so the frame is streamed in bands within budget_gb of device
+    memory; one pass = every band's quantise + scan + 10 gathers (CUDA graph)."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    cfg = synth.config4()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    d_img = torch.from_numpy(img.view(np.int16)).to(dev)
+    del img
+    stream = torch.cuda.Stream(device=dev)
+    tgt = torch.rand((len(cfg["kernels"]) * len(cfg["windows"]), B), device=dev) + 0.01
+    tgt /= tgt.sum(1, keepdim=True)  # targets: positive normalised histograms (set-up)
+    jobs, maps = [], []
+    for k in cfg["kernels"]:
+        for w in cfg["windows"]:
+            m = torch.empty((H - w + 1, W - w + 1), device=dev)
+            jobs.append(S.make_frame_job(k, w, w, tgt[len(maps)], m))
+            maps.append(m)
+    wpp = sum(m.numel() for m in maps)
+    desc = S.make_desc(H, W, pixel_type=S.SWIH_PIXEL_U16, bitdepth=16, bins=B, kernels=cfg["kernels"],
+                       max_win=(127, 127), hbm_budget_bytes=budget_gb << 30)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    passes = 3
+    with S.Stream(desc, jobs, d_img) as st:
+        info = st.info()
+        st.run(stream)
+        st.sync_status(stream)
+        e0.record(stream)
+        for _ in range(passes):
+            st.run(stream)
+        e1.record(stream)
+        st.sync_status(stream)
+    ms = e0.elapsed_time(e1) / passes
+    del maps
+    torch.cuda.empty_cache()
+    return {
+        "workload": ("8192x8192 u16 fractal terrain + 200 blobs, B=64, Gaussian + Euclidean x windows "
+                     "15/25/43/75/127, full valid maps, streamed in bands"),
+        "windows_per_pass": wpp, "ms_per_pass": ms, "windows_per_s": wpp / (ms * 1e-3),
+        "band_height": info["band_height"], "n_bands": info["n_bands"],
+        "workspace_gb": info["workspace_bytes"] / 1e9,
+        "halo_rows_per_band": 126,
+        "whole_frame_ih_gb": 25 * B * H * W * 8 / 1e9,
+    }
+
+
 # ----------------------------------------------------------------------------- serving
 def run_serving(args, dev, n_queries=400, rate=2000.0):
     """A Poisson stream of tracking queries against 16 resident 2048x2048
@@ -550,6 +606,75 @@ def run_serving(args, dev, n_queries=400, rate=2000.0):
     }
 
 
+# ----------------------------------------------------------------------------- Fig. 6
+def run_fig6(args):
+    """Time per likelihood map against window size (the experiment of Fig. 6):
+    SWIH on the GPU (quantise + integral histograms + gather, CUDA events, and
+    the gather alone) and the brute-force oracle on the host cores (timed on a
+    sample of centres and scaled to the whole map), on 640x480 and 1024x1024
+    frames of the benchmark's scene generator, B = 32."""
+    import torch
+
+    from oracle import swih_oracle as O
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    O.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    B = 32
+    rows = []
+    for (H, W) in ((480, 640), (1024, 1024)):
+        sc = synth.blob_scene(H, W, 8, seed=2, n_blobs=8)
+        img = sc.image
+        d_img = torch.from_numpy(img).to(dev)
+        bins = O.quantize(img, 8, B)
+        for kind in ("manhattan", "euclidean", "gaussian"):
+            wins = [w for w in (11, 21, 41, 61, 81, 121, 161, 201, 301, 401) if w < min(H, W)]
+            if kind == "gaussian":
+                wins = [w for w in wins if w <= 121]  # exact 64-bit moments: w h rx^4 ry^4 < 2^64
+            for w in wins:
+                desc = S.make_desc(H, W, bins=B, kernels=(kind,), max_win=(w, w))
+                with S.Plan(desc) as p:
+                    q = torch.full((B,), 1.0 / B, device=dev)
+                    m = torch.empty((H - w + 1, W - w + 1), device=dev)
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    for _ in range(3):
+                        p.build_ih(d_img, stream)
+                        p.likelihood(kind, w, w, q, m, stream)
+                    reps = 10
+                    t_all, t_g = 0.0, 0.0
+                    for _ in range(reps):
+                        ev[0].record(stream)
+                        p.build_ih(d_img, stream)
+                        ev[1].record(stream)
+                        p.likelihood(kind, w, w, q, m, stream)
+                        ev[2].record(stream)
+                        torch.cuda.synchronize()
+                        t_all += ev[0].elapsed_time(ev[2])
+                        t_g += ev[1].elapsed_time(ev[2])
+                    p.sync_status(stream)
+                K = O.kernel_weights(kind, w, w)
+                r = w // 2
+                n_c = (H - w + 1) * (W - w + 1)
+                rng = np.random.default_rng(w)
+                n_s = int(max(256, min(n_c, 2e8 / (w * w))))
+                cx = rng.integers(r, W - r, n_s)
+                cy = rng.integers(r, H - r, n_s)
+                t0 = time.perf_counter()
+                O.likelihood_at(bins, B, K, np.full(B, 1.0 / B), cx, cy)
+                t_cpu = (time.perf_counter() - t0) / n_s * n_c * 1e3
+                rows.append({"frame": f"{W}x{H}", "kernel": kind, "window": w, "centres": n_c,
+                             "swih_ms": t_all / reps, "swih_gather_ms": t_g / reps,
+                             "brute_force_cpu_ms": t_cpu, "cpu_threads": O.threads(),
+                             "cpu_sample_centres": n_s})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return {"fig6": rows, "bins": B,
+            "note": ("SWIH: GPU time per map (quantise + integral histograms + gather) and the gather "
+                     "alone; brute force: the FP64 oracle on the host cores, timed on a sample of "
+                     "centres and scaled to the map")}
+
+
 # ----------------------------------------------------------------------------- oracle
 def oracle_sample(budget_s: float, seed: int = 7):
     """Time the CPU oracle on random valid centres of the same workload (all nine
@@ -635,12 +760,18 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-regions and serving measurements (profiling runs)")
     ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--fig6", action="store_true",
+                    help="time per map against window size (SWIH on the GPU vs the brute-force oracle)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "swih":
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.fig6:
+        print(json.dumps(run_fig6(args)), flush=True)
+        return
 
     if args.impl == "reference":
         line = run_reference(args, rank, world)
@@ -665,6 +796,7 @@ def main():
         dev = torch.device("cuda", local_rank)
         line["batched_regions"] = run_regions(args, dev)
         line["serving"] = run_serving(args, dev, n_queries=args.serve_queries)
+        line["large_frame"] = run_large_frame(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(args.cpu_seconds)
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}

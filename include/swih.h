@@ -52,7 +52,7 @@ typedef enum swih_status {
 
 typedef enum swih_pixel_type { SWIH_PIXEL_U8 = 0, SWIH_PIXEL_U16 = 1 } swih_pixel_type;
 
-/* Spatial kernels K(dx, dy), dx = x - xc, dy = y - yc (Fig. 1):
+/* Spatial kernels K(dx, dy), dx = x - xc, dy = y - yc (Fig. 1, Fig. 4):
  *   PLAIN      K = 1 (Porikli's local histogram)
  *   MANHATTAN  K = (rx-|dx|) + (ry-|dy|): Eq. 1's city-block distance taken
  *              from its corner value, zero at the window corners, largest at
@@ -62,12 +62,20 @@ typedef enum swih_pixel_type { SWIH_PIXEL_U8 = 0, SWIH_PIXEL_U16 = 1 } swih_pixe
  *   GAUSSIAN   K = Px(dx^2/rx^2) * Py(dy^2/ry^2), P the least-squares
  *              polynomial of degree min(D, r) fitted to exp(-d^2/(2 s^2)) on
  *              d = -r..r, s = gauss_sigma_frac * window side (the paper names
- *              the Gaussian without a decomposition)                         */
+ *              the Gaussian without a decomposition)
+ *   WEDDING    the wedding-cake approximation of Sec. 2 (Fig. 4(a)) to the
+ *              Manhattan kernel: n nested windows around the centre with
+ *              half-sides floor((2 i r + n) / (2 n)), i = 1..n, per axis; the
+ *              ring between nested windows i-1 and i weighs the mean of the
+ *              Manhattan kernel over that ring's pixels. Computed from plain
+ *              (unweighted) integral histograms only; n = wedding_rings.
+ *              The paper names the scheme without ring sizes or weights.    */
 typedef enum swih_kernel {
     SWIH_KERNEL_PLAIN = 0,
     SWIH_KERNEL_MANHATTAN = 1,
     SWIH_KERNEL_EUCLIDEAN = 2,
-    SWIH_KERNEL_GAUSSIAN = 3
+    SWIH_KERNEL_GAUSSIAN = 3,
+    SWIH_KERNEL_WEDDING = 4
 } swih_kernel;
 
 #define SWIH_KERNEL_BIT(k) (1u << (unsigned)(k))
@@ -103,6 +111,7 @@ typedef struct swih_plan_desc {
     int32_t precision;         /* swih_precision */
     int32_t band_rows;         /* rows per scan band (0: automatic) */
     uint64_t hbm_budget_bytes; /* reject plans whose workspace exceeds it (0: no limit) */
+    int32_t wedding_rings;     /* nested windows of the WEDDING kernel, 1..16 (0: 4) */
 } swih_plan_desc;
 
 typedef struct swih_plan_s *swih_plan_t;

@@ -168,8 +168,36 @@ def gauss_axis(r: int, sigma: float, degree: int) -> np.ndarray:
     return sum(ci * t ** i for i, ci in enumerate(c))
 
 
+def wedding_half_sides(r: int, n: int) -> list:
+    """Half-sides of the n nested windows of one axis (Sec. 2, Fig. 4(a): the
+    paper gives no sizes): i * r / n rounded half up, i = 1..n."""
+    return [int(np.floor(i * r / n + 0.5)) for i in range(1, n + 1)]
+
+
+def wedding_weights(w: int, h: int, rings: int = 4) -> np.ndarray:
+    """Wedding-cake approximation (Sec. 2, Fig. 4(a)) of the Manhattan kernel:
+    n nested windows around the centre split the window into rings (the
+    innermost window is the first ring); every pixel of a ring gets the mean
+    Manhattan weight of that ring's pixels. Reading: the paper only says the
+    ring histograms are 'weighted appropriately with respect to their distance
+    from P'; the ring mean is the least-squares ring-constant fit, and it keeps
+    the kernel's total weight."""
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    K = kernel_weights("manhattan", w, h)
+    dx = np.abs(np.arange(-rx, rx + 1))[None, :]
+    dy = np.abs(np.arange(-ry, ry + 1))[:, None]
+    out = np.zeros_like(K)
+    taken = np.zeros(K.shape, dtype=bool)
+    for a, b in zip(wedding_half_sides(rx, rings), wedding_half_sides(ry, rings)):
+        ring = (dx <= a) & (dy <= b) & ~taken
+        if ring.any():
+            out[ring] = K[ring].mean()
+            taken |= ring
+    return out
+
+
 def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
-                   sigma_frac: float = 0.25) -> np.ndarray:
+                   sigma_frac: float = 0.25, rings: int = 4) -> np.ndarray:
     """Weight table K[dy + ry, dx + rx] (float64, h x w) of one window.
 
     * plain: K = 1 (Porikli's unweighted local histogram).
@@ -185,6 +213,8 @@ def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
     * gaussian: K = Px(dx^2 / rx^2) * Py(dy^2 / ry^2), each factor the
       least-squares polynomial (gauss_fit) of the axis Gaussian with
       sigma = sigma_frac * (window length along that axis).
+    * wedding: the wedding-cake approximation of the Manhattan kernel with
+      ``rings`` nested windows (wedding_weights).
     """
     if w < 3 or h < 3 or w % 2 == 0 or h % 2 == 0:
         raise ValueError("window sides must be odd and >= 3")
@@ -197,6 +227,8 @@ def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
         return (rx - np.abs(dx)) + (ry - np.abs(dy))
     if kind == "euclidean":
         return (rx * rx - dx * dx) + (ry * ry - dy * dy)
+    if kind == "wedding":
+        return wedding_weights(w, h, rings)
     if kind == "gaussian":
         gx = gauss_axis(rx, sigma_frac * w, degree)[None, :]
         gy = gauss_axis(ry, sigma_frac * h, degree)[:, None]

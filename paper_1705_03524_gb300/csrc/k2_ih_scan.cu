@@ -148,7 +148,7 @@ __device__ __forceinline__ void add_state(const T *src, T (&acc)[E])
 }
 
 // One (chain, band) tile of one image region r; ticket = its ticket number.
-template <typename T, int E>
+template <typename T, int E, int NP>
 __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r, const int ticket,
                                           const int band, const int chain)
 {
@@ -252,7 +252,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     // barrier per scan). The values x^k cs(x) are built by repeated
     // multiplication by x (x < 2^13); the next row's bins are loaded while the
     // current row is scanned.
-    const int n_p = p.p_count[qi];  // the chain's x-exponents are 0..n_p-1
+    const int n_p = p.p_count[qi];  // the chain's x-exponents are 0..n_p-1 (n_p <= NP)
     T cs[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) cs[e] = carry[e];
@@ -271,7 +271,9 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
                 if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
         }
         T cur[E];
-        for (int k = 0; k < n_p; ++k) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            if (k >= n_p) break;
             T val[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -301,7 +303,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     }
 }
 
-template <typename T, int E>
+template <typename T, int E, int NP>
 __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_constant__ ScanParams p)
 {
     __shared__ int s_ticket;
@@ -323,14 +325,14 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_c
     r.W = p.W;
     r.n_bands = p.n_bands;
     r.ticket0 = 0;
-    scan_tile<T, E>(p, r, ticket, band, ticket - band * n_chains);
+    scan_tile<T, E, NP>(p, r, ticket, band, ticket - band * n_chains);
 }
 
 // Several image regions in one launch: region i owns the tickets
 // [table[i].ticket0, table[i + 1].ticket0), band-major, so every tile a tile
 // may wait for (the same chain, an earlier band, the same region) holds a
 // smaller ticket and has already started.
-template <typename T, int E>
+template <typename T, int E, int NP>
 __global__ void __launch_bounds__(kMaxScanThreads)
     ih_scan_table_kernel(const __grid_constant__ ScanParams p, const ScanRoi *__restrict__ table, int n)
 {
@@ -347,30 +349,44 @@ __global__ void __launch_bounds__(kMaxScanThreads)
     const int local = ticket - r.ticket0;
     const int n_chains = p.B * p.n_q;
     const int band = local / n_chains;
-    scan_tile<T, E>(p, r, ticket, band, local - band * n_chains);
+    scan_tile<T, E, NP>(p, r, ticket, band, local - band * n_chains);
 }
 
-template <typename T, int E>
+template <typename T, int E, int NP>
 cudaError_t launch_typed(const ScanParams &p, int threads, const ScanRoi *table, int n_roi, long long tiles,
                          cudaStream_t s)
 {
     if (table)
-        ih_scan_table_kernel<T, E><<<(unsigned)tiles, threads, 0, s>>>(p, table, n_roi);
+        ih_scan_table_kernel<T, E, NP><<<(unsigned)tiles, threads, 0, s>>>(p, table, n_roi);
     else
-        ih_scan_kernel<T, E><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, 0, s>>>(p);
+        ih_scan_kernel<T, E, NP><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+// NP: a compile-time bound on the x-exponents per chain (1: plain; 3: up to
+// the Euclidean terms; 5: the Gaussian), so the per-row term loop unrolls
+template <typename T, int NP>
+cudaError_t launch_np(const ScanParams &p, int E, int threads, const ScanRoi *table, int n_roi, long long tiles,
+                      cudaStream_t s)
+{
+    switch (E) {
+    case 4: return launch_typed<T, 4, NP>(p, threads, table, n_roi, tiles, s);
+    case 8: return launch_typed<T, 8, NP>(p, threads, table, n_roi, tiles, s);
+    case 16: return launch_typed<T, 16, NP>(p, threads, table, n_roi, tiles, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
 cudaError_t launch_e(const ScanParams &p, int E, int threads, const ScanRoi *table, int n_roi, long long tiles,
                      cudaStream_t s)
 {
-    switch (E) {
-    case 4: return launch_typed<T, 4>(p, threads, table, n_roi, tiles, s);
-    case 8: return launch_typed<T, 8>(p, threads, table, n_roi, tiles, s);
-    case 16: return launch_typed<T, 16>(p, threads, table, n_roi, tiles, s);
-    default: return cudaErrorInvalidValue;
-    }
+    int np = 1;
+    for (int i = 0; i < p.n_q; ++i) np = p.p_count[i] > np ? p.p_count[i] : np;
+    if (np <= 1) return launch_np<T, 1>(p, E, threads, table, n_roi, tiles, s);
+    if (np <= 3) return launch_np<T, 3>(p, E, threads, table, n_roi, tiles, s);
+    if (np <= 5) return launch_np<T, 5>(p, E, threads, table, n_roi, tiles, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace

@@ -122,6 +122,16 @@ __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
         if constexpr (KIND == kGatherPlain) {
             const T U = plane_of<T>(p, p.t1, b).rect(X0, X2, Y0, Y2);
             h = to_float(U) * p.inv_mass;
+        } else if constexpr (KIND == kGatherWedding) {
+            // nested windows i: plain counts, weighted by c_i = w_i - w_{i+1}
+            const Plane<T> P1 = plane_of<T>(p, p.t1, b);
+            float u = 0.f;
+            for (int i = 0; i < p.n_rings; ++i) {
+                const int a = p.ring_rx[i], c = p.ring_ry[i];
+                const T n = P1.rect(xc - a - 1, xc + a, yc - c - 1, yc + c);
+                u = fmaf(p.ring_c[i], to_float(n), u);
+            }
+            h = u * p.inv_mass;
         } else if constexpr (KIND == kGatherManhattan) {
             const Plane<T> P1 = plane_of<T>(p, p.t1, b);
             const Plane<T> Px = plane_of<T>(p, p.tx, b);
@@ -216,6 +226,7 @@ cudaError_t launch_kind(const GatherParams &p, int kind, cudaStream_t s)
     case kGatherPlain: gather_kernel<kGatherPlain, T><<<grid, block, smem, s>>>(p); break;
     case kGatherManhattan: gather_kernel<kGatherManhattan, T><<<grid, block, smem, s>>>(p); break;
     case kGatherEuclidean: gather_kernel<kGatherEuclidean, T><<<grid, block, smem, s>>>(p); break;
+    case kGatherWedding: gather_kernel<kGatherWedding, T><<<grid, block, smem, s>>>(p); break;
     case kGatherGaussian:
         if constexpr (sizeof(T) == 8) {
             gather_kernel<kGatherGaussian, T><<<grid, block, smem, s>>>(p);

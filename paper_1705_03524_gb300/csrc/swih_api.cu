@@ -155,8 +155,10 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "pitch_bytes of a U16 image must be even");
     if (d->bins < 1 || d->bins > 256)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "bins must be in [1, 256]");
-    if (d->kernel_mask == 0 || (d->kernel_mask & ~0xFu))
-        return fail(nullptr, SWIH_ERR_INVALID_ARG, "kernel_mask must name kernels 0..3");
+    if (d->kernel_mask == 0 || (d->kernel_mask & ~0x1Fu))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "kernel_mask must name kernels 0..4");
+    if (d->wedding_rings < 0 || d->wedding_rings > kMaxRings)
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "wedding_rings must be in [0, 16]");
     if (!odd_window(d->max_win_w) || !odd_window(d->max_win_h))
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "max window sides must be odd and >= 3");
     if (d->max_win_w > d->width || d->max_win_h > d->height)
@@ -216,6 +218,8 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     for (int k = SWIH_KERNEL_PLAIN; k <= SWIH_KERNEL_EUCLIDEAN; ++k)
         if (d->kernel_mask & SWIH_KERNEL_BIT(k))
             need = std::max(need, int_kernel_mass(k, d->max_win_w, d->max_win_h));
+    if (d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_WEDDING))  // rectangle counts
+        need = std::max(need, int_kernel_mass(SWIH_KERNEL_PLAIN, d->max_win_w, d->max_win_h));
     const bool fits32 = !want_gau && need < 4294967296.0L;
     if (want_gau && gauss_bound(d->max_win_w, d->max_win_h, D) >= 18446744073709551616.0L)
         return fail(nullptr, SWIH_ERR_UNSUPPORTED,
@@ -264,7 +268,7 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
 
 swih_status check_window(swih_plan_s *pl, int kernel, int w, int h)
 {
-    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_GAUSSIAN)
+    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_WEDDING)
         return fail(pl, SWIH_ERR_INVALID_ARG, "unknown kernel");
     if (!(pl->desc.kernel_mask & SWIH_KERNEL_BIT(kernel)))
         return fail(pl, SWIH_ERR_INVALID_ARG, "kernel not in the plan's kernel_mask");
@@ -274,6 +278,33 @@ swih_status check_window(swih_plan_s *pl, int kernel, int w, int h)
         return fail(pl, SWIH_ERR_INVALID_ARG, "window larger than the plan's max window");
     if (!pl->built) return fail(pl, SWIH_ERR_INVALID_ARG, "swih_build_ih has not been called");
     return SWIH_OK;
+}
+
+// Wedding-cake rings of a w x h window: nested half-sides floor((2 i r + n) /
+// (2 n)), i = 1..n, per axis (repeats dropped), each ring weighted by the
+// mean Manhattan weight over its pixels. Sums are exact integers:
+// sum over |dx| <= a, |dy| <= b of (rx - |dx|) + (ry - |dy|)
+//   = (2b+1) ((2a+1) rx - a (a+1)) + (2a+1) ((2b+1) ry - b (b+1)).
+int wedding_rings(int w, int h, int n, int *rx_i, int *ry_i, double *weight)
+{
+    const long long rx = (w - 1) / 2, ry = (h - 1) / 2;
+    auto rect_sum = [&](long long a, long long b) -> long long {
+        return (2 * b + 1) * ((2 * a + 1) * rx - a * (a + 1)) + (2 * a + 1) * ((2 * b + 1) * ry - b * (b + 1));
+    };
+    int m = 0;
+    long long prev_sum = 0, prev_cnt = 0;
+    for (int i = 1; i <= n; ++i) {
+        const int a = (int)((2LL * i * rx + n) / (2LL * n)), b = (int)((2LL * i * ry + n) / (2LL * n));
+        if (m > 0 && a == rx_i[m - 1] && b == ry_i[m - 1]) continue;
+        const long long cnt = (2LL * a + 1) * (2LL * b + 1), sum = rect_sum(a, b);
+        rx_i[m] = a;
+        ry_i[m] = b;
+        weight[m] = (double)(sum - prev_sum) / (double)(cnt - prev_cnt);
+        prev_sum = sum;
+        prev_cnt = cnt;
+        ++m;
+    }
+    return m;
 }
 
 swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams &g, int &kind)
@@ -326,6 +357,18 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
             for (int k = 0; k <= kx; ++k) g.load_even[g.n_load_even++] = g.tg[k][l];
         g.n_load_odd = 0;
         g.nl = g.n_load_even;
+    } else if (kernel == SWIH_KERNEL_WEDDING) {
+        kind = kGatherWedding;
+        double wt[kMaxRings];
+        const int n = pl->desc.wedding_rings ? pl->desc.wedding_rings : 4;
+        g.n_rings = wedding_rings(w, h, n, g.ring_rx, g.ring_ry, wt);
+        for (int i = 0; i < g.n_rings; ++i) g.ring_c[i] = (float)(wt[i] - (i + 1 < g.n_rings ? wt[i + 1] : 0.0));
+        // the rings partition the window and carry the Manhattan kernel's mass
+        g.inv_mass = (float)(1.0L / int_kernel_mass(SWIH_KERNEL_MANHATTAN, w, h));
+        g.load_even[0] = g.t1;
+        g.n_load_even = 1;
+        g.n_load_odd = 0;
+        g.nl = 1;
     } else {
         g.inv_mass = (float)(1.0L / int_kernel_mass(kernel, w, h));
         kind = kernel == SWIH_KERNEL_PLAIN ? kGatherPlain
@@ -623,7 +666,7 @@ swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, in
                                    int bins_per_step)
 {
     if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
-    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_GAUSSIAN)
+    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_WEDDING)
         return fail(pl, SWIH_ERR_INVALID_ARG, "unknown kernel");
     if (tile_cols != 0 && tile_cols != 128 && tile_cols != 256)
         return fail(pl, SWIH_ERR_INVALID_ARG, "tile_cols must be 0, 128 or 256");

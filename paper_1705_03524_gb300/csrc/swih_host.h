@@ -35,9 +35,9 @@ struct swih_plan_s {
     bool built = false;
     int inject = 0;  // SWIH_INJECT_* for the next swih_build_ih
     int gather_path = 0;  // 0: tiled when it fits, 1: direct gather only
-    int cfg_tx[4] = {0, 0, 0, 0};      // tiled gather tile width per kernel (0: automatic)
-    int cfg_stages[4] = {0, 0, 0, 0};  // tiled gather ring depth per kernel (0: automatic)
-    int cfg_bb[4] = {0, 0, 0, 0};      // tiled gather bins per step per kernel (0: automatic)
+    int cfg_tx[5] = {0, 0, 0, 0, 0};      // tiled gather tile width per kernel (0: automatic)
+    int cfg_stages[5] = {0, 0, 0, 0, 0};  // tiled gather ring depth per kernel (0: automatic)
+    int cfg_bb[5] = {0, 0, 0, 0, 0};      // tiled gather bins per step per kernel (0: automatic)
     std::string err;
 };
 

@@ -91,7 +91,8 @@ cudaError_t launch_ih_scan_table(const ScanParams &p, const ScanRoi *d_table, in
                                  int elem_bytes, int E, int threads, cudaStream_t s);
 
 // ---------------------------------------------------------------- K3 gather
-enum GatherKind { kGatherPlain = 0, kGatherManhattan = 1, kGatherEuclidean = 2, kGatherGaussian = 3 };
+enum GatherKind { kGatherPlain = 0, kGatherManhattan = 1, kGatherEuclidean = 2, kGatherGaussian = 3, kGatherWedding = 4 };
+constexpr int kMaxRings = 16;
 
 struct GatherParams {
     const void *ih;
@@ -105,7 +106,10 @@ struct GatherParams {
     int gdx, gdy;           // Gaussian: fitted degree per axis (1 or 2)
     unsigned long long rx2, rx4, ry2, ry4;  // r^2, r^4 per axis (ring constants)
     float gamma[3][3];      // Gaussian: beta_x[i] beta_y[j] / (rx^2Dx ry^2Dy M)
-    float inv_mass;         // 1 / M (plain, Manhattan, Euclidean)
+    float inv_mass;         // 1 / M (plain, Manhattan, Euclidean, wedding cake)
+    int n_rings;            // wedding cake: nested windows, half-sides and weights
+    int ring_rx[kMaxRings], ring_ry[kMaxRings];
+    float ring_c[kMaxRings];  // weight of ring i minus weight of ring i+1
     const float *target;    // [n_targets][target_stride] (first B of each row used) or null
     float *map;             // n_targets maps of [ncy][ncx], map_stride floats apart, or null
     int n_targets;          // 1..kMaxTargets: one histogram per window, scored against each

@@ -32,13 +32,15 @@ SWIH_KERNEL_PLAIN = 0
 SWIH_KERNEL_MANHATTAN = 1
 SWIH_KERNEL_EUCLIDEAN = 2
 SWIH_KERNEL_GAUSSIAN = 3
+SWIH_KERNEL_WEDDING = 4
 
 SWIH_PREC_AUTO = 0
 SWIH_PREC_RING32 = 1
 SWIH_PREC_RING64 = 2
 
 KERNELS = {"plain": SWIH_KERNEL_PLAIN, "manhattan": SWIH_KERNEL_MANHATTAN,
-           "euclidean": SWIH_KERNEL_EUCLIDEAN, "gaussian": SWIH_KERNEL_GAUSSIAN}
+           "euclidean": SWIH_KERNEL_EUCLIDEAN, "gaussian": SWIH_KERNEL_GAUSSIAN,
+           "wedding": SWIH_KERNEL_WEDDING}
 
 
 def kernel_bit(k: int) -> int:
@@ -67,6 +69,7 @@ class swih_plan_desc(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("band_rows", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_uint64),
+        ("wedding_rings", ctypes.c_int32),
     ]
 
 
@@ -297,7 +300,8 @@ def _check(status: int, plan=None):
 
 def make_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8, bitdepth=None,
               bins=16, kernels=("manhattan",), gauss_degree=2, gauss_sigma_frac=0.25,
-              max_win=(3, 3), precision=SWIH_PREC_AUTO, band_rows=0, hbm_budget_bytes=0):
+              max_win=(3, 3), precision=SWIH_PREC_AUTO, band_rows=0, hbm_budget_bytes=0,
+              wedding_rings=0):
     pb = 1 if pixel_type == SWIH_PIXEL_U8 else 2
     mask = 0
     for k in kernels:
@@ -315,6 +319,7 @@ def make_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8, bitd
     d.precision = int(precision)
     d.band_rows = int(band_rows)
     d.hbm_budget_bytes = int(hbm_budget_bytes)
+    d.wedding_rings = int(wedding_rings)
     return d
 
 

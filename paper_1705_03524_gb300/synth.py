@@ -26,6 +26,7 @@ __all__ = [
     "config1",
     "config2",
     "config3",
+    "config4",
     "config5_frames",
     "config5_queries",
     "odd_window",
@@ -273,3 +274,62 @@ def config5_queries(seed: int = 5, n: int = 1000, rate: float = 2000.0, n_frames
         out.append(dict(t=t, frame=int(rng.integers(0, n_frames)), x0=x0, y0=y0, w=w, h=h, B=B,
                         kernel=kernel, windows=[(v, v) for v in wins], targets=targets.astype(np.float32)))
     return out
+
+
+def fbm_value_noise_rows(h: int, w: int, octaves: int, cell: float, rng: np.random.Generator,
+                         gain: float = 0.5, chunk: int = 512) -> np.ndarray:
+    """fbm_value_noise computed in float32, a block of rows at a time (for
+    frames of tens of megapixels). The lattices are drawn in the same order;
+    values agree with fbm_value_noise to float32 rounding."""
+    lats = []
+    for o in range(octaves):
+        c = max(cell / (2.0 ** o), 2.0)
+        gy = int(np.ceil(h / c)) + 2
+        gx = int(np.ceil(w / c)) + 2
+        lats.append((c, rng.uniform(-1.0, 1.0, size=(gy, gx)).astype(np.float32)))
+    out = np.zeros((h, w), dtype=np.float32)
+    norm = sum(gain ** o for o in range(octaves))
+    for o, (c, lat) in enumerate(lats):
+        amp = np.float32(gain ** o / norm)
+        xs = np.arange(w) / c
+        x0 = np.floor(xs).astype(np.int64)
+        fx = _quintic_fade(xs - x0).astype(np.float32)[None, :]
+        for r0 in range(0, h, chunk):
+            ys = np.arange(r0, min(h, r0 + chunk)) / c
+            y0 = np.floor(ys).astype(np.int64)
+            fy = _quintic_fade(ys - y0).astype(np.float32)[:, None]
+            l0 = lat[y0]
+            l1 = lat[y0 + 1]
+            top = l0[:, x0] + (l0[:, x0 + 1] - l0[:, x0]) * fx
+            bot = l1[:, x0] + (l1[:, x0 + 1] - l1[:, x0]) * fx
+            out[r0: r0 + len(ys)] += amp * (top + (bot - top) * fy)
+    return out
+
+
+def config4(seed: int = 4, size: int = 8192, n_blobs: int = 200, frame_index: int = 0) -> dict:
+    """Large single frame: 8192 x 8192 uint16 wide-area-like synthetic, a
+    fractal terrain (6 octaves of value noise, lattice 1024 px, 0.5 +- 0.35 of
+    the range, 2% Gaussian texture) plus 200 textured ellipses of 8-40 px
+    moving at constant velocities (shown at time frame_index); B = 64,
+    Gaussian and Euclidean kernels, windows 15/25/43/75/127 (geometric)."""
+    rng = np.random.default_rng(seed)
+    full = float(1 << 16)
+    img = 0.5 * full + 0.35 * full * fbm_value_noise_rows(size, size, 6, 1024.0, rng)
+    img += rng.normal(0.0, 0.02 * full, size=img.shape).astype(np.float32)
+    centres = []
+    for _ in range(n_blobs):
+        x, y = float(rng.uniform(64, size - 64)), float(rng.uniform(64, size - 64))
+        vx, vy = float(rng.uniform(-8, 8)), float(rng.uniform(-8, 8))
+        d = float(rng.uniform(8, 40))
+        a = 0.5 * d
+        b = 0.5 * d * float(rng.uniform(0.5, 1.0))
+        ang = float(rng.uniform(0, np.pi))
+        mean = float(rng.integers(int(0.1 * full), int(0.9 * full)))
+        cx = int(np.clip(x + vx * frame_index, 0, size - 1))
+        cy = int(np.clip(y + vy * frame_index, 0, size - 1))
+        _plant_ellipse(img, rng, cx, cy, a, b, ang, mean, 0.05 * full)
+        centres.append((cx, cy))
+    np.rint(img, out=img)
+    np.clip(img, 0, full - 1, out=img)
+    return dict(image=img.astype(np.uint16), bitdepth=16, B=64, kernels=("gaussian", "euclidean"),
+                windows=SERVE_WINDOWS, object_centres=centres)

@@ -307,3 +307,55 @@ def test_benchmark_workload_sampled_centres():
     finally:
         for _, p in plans:
             p.close()
+
+
+# --------------------------------------------------------------------------- wedding cake
+@pytest.mark.parametrize("rings", [1, 2, 4, 8, 16])
+def test_wedding_cake_parity(rings):
+    img = synth.uniform_image(90, 120, 8, seed=20 + rings)
+    B = 12
+    plan, _buf = make_plan(img, 8, B, ("manhattan", "wedding"), (41, 31), wedding_rings=rings)
+    with plan:
+        bins = oracle_bins(img, 8, B)
+        for (w, h) in [(3, 3), (9, 9), (41, 21), (7, 31), (41, 31)]:
+            K = O.kernel_weights("wedding", w, h, rings=rings)
+            x0, y0, nx, ny = O.valid_centres(90, 120, w, h)
+            hist = torch.empty((ny, nx, B), dtype=torch.float32, device=DEV)
+            plan.local_hist("wedding", w, h, x0, y0, nx, ny, hist)
+            ref_h = O.normalise(O.hist_rect(bins, B, K, x0, y0, nx, ny))
+            assert np.abs(hist.cpu().numpy() - ref_h).max() <= TOL, (w, h)
+            q = O.target_hist(bins, B, K, x0 + nx // 2, y0 + ny // 3)
+            m = torch.empty((ny, nx), device=DEV)
+            plan.likelihood("wedding", w, h, torch.tensor(q, dtype=torch.float32, device=DEV), m)
+            ref = O.likelihood_map(bins, B, K, q)
+            assert np.abs(m.cpu().numpy() - ref).max() <= TOL, (w, h)
+        plan.sync_status()
+
+
+def test_wedding_cake_and_plain_are_approximations_swih_is_exact():
+    """Fig. 5: likelihood maps of the weighted (Manhattan) target against the
+    brute-force weighted map: SWIH within 1e-5, the wedding cake and the
+    plain histogram off by more (printed: max and mean abs error)."""
+    cfg = synth.config2()
+    img = np.ascontiguousarray(cfg["image"][300:556, 400:656])
+    B = cfg["B"]
+    bins = oracle_bins(img, 8, B)
+    w = 41
+    Km = O.kernel_weights("manhattan", w, w)
+    q = O.target_hist(bins, B, Km, 128, 128)
+    ref = O.likelihood_map(bins, B, Km, q)
+    qd = torch.tensor(q, dtype=torch.float32, device=DEV)
+    errs = {}
+    for kind, rings in [("manhattan", 0), ("plain", 0), ("wedding", 2), ("wedding", 4), ("wedding", 8)]:
+        plan, _buf = make_plan(img, 8, B, (kind,), (w, w), wedding_rings=rings)
+        with plan:
+            m = torch.empty(ref.shape, device=DEV)
+            plan.likelihood(kind, w, w, qd, m)
+            plan.sync_status()
+            d = np.abs(m.cpu().numpy() - ref)
+            errs[f"{kind}{rings or ''}"] = (float(d.max()), float(d.mean()))
+    print("likelihood error vs brute force (max, mean):", errs)
+    assert errs["manhattan"][0] <= TOL
+    for k in ("plain", "wedding2", "wedding4", "wedding8"):
+        assert errs[k][0] > 100 * TOL, k
+    assert errs["wedding8"][1] < errs["plain"][1]

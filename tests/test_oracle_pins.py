@@ -365,3 +365,36 @@ def test_gauss_approximant_distance_from_true_gaussian():
     for w in (21, 41, 81):
         err = np.abs(O.kernel_weights("gaussian", w, w) - O.true_gaussian(w, w)).max()
         assert err < 0.05, (w, err)
+
+
+# --------------------------------------------------------------------------- wedding cake
+def test_wedding_cake_hand_case():
+    """5 x 5 window, 2 nested windows (half-sides 1 and 2). Manhattan weights
+    (2 - |dx|) + (2 - |dy|): the inner 3 x 3 holds 4 (centre), 3 (x4), 2 (x4)
+    = 24 over 9 pixels; the outer ring holds the rest of the total 40
+    (h rx^2 + w ry^2 = 5*4 + 5*4) = 16 over 16 pixels."""
+    K = O.kernel_weights("wedding", 5, 5, rings=2)
+    want = np.ones((5, 5))
+    want[1:4, 1:4] = 24.0 / 9.0
+    assert np.allclose(K, want, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("w,h,rings", [(5, 5, 1), (31, 31, 4), (41, 21, 3), (9, 45, 8), (7, 7, 16), (3, 3, 4)])
+def test_wedding_cake_keeps_the_manhattan_mass(w, h, rings):
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    K = O.kernel_weights("wedding", w, h, rings=rings)
+    assert abs(K.sum() - (h * rx * rx + w * ry * ry)) <= 1e-9 * K.sum()
+    # ring weights do not increase away from the centre (Manhattan falls off)
+    prof = [K[ry, rx + d] for d in range(rx + 1)]
+    assert all(a >= b - 1e-12 for a, b in zip(prof, prof[1:]))
+
+
+def test_wedding_cake_with_one_ring_is_the_plain_histogram():
+    rng = np.random.default_rng(4)
+    bins = rng.integers(0, 6, size=(30, 40)).astype(np.uint8)
+    Kw = O.kernel_weights("wedding", 11, 9, rings=1)
+    Kp = O.kernel_weights("plain", 11, 9)
+    cx, cy = rng.integers(5, 35, 20), rng.integers(4, 26, 20)
+    hw = O.normalise(O.hist_at(bins, 6, Kw, cx, cy))
+    hp = O.normalise(O.hist_at(bins, 6, Kp, cx, cy))
+    assert np.abs(hw - hp).max() <= 1e-14
