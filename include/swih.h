@@ -47,7 +47,8 @@ typedef enum swih_status {
     SWIH_ERR_OOM = 3,         /* device allocation failed */
     SWIH_ERR_BUDGET = 4,      /* workspace larger than hbm_budget_bytes */
     SWIH_ERR_CUDA = 5,        /* a CUDA runtime call failed (message has the name) */
-    SWIH_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (scan look-back) */
+    SWIH_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (scan look-back) */
+    SWIH_ERR_CANCELLED = 7    /* a server query cancelled before it was admitted */
 } swih_status;
 
 typedef enum swih_pixel_type { SWIH_PIXEL_U8 = 0, SWIH_PIXEL_U16 = 1 } swih_pixel_type;
@@ -143,7 +144,12 @@ swih_status swih_local_hist(swih_plan_t plan, int kernel, int win_w, int win_h, 
 /* Steps (3)-(5) of Sec. 1 plus the matching of Sec. 2 / Fig. 3 for every valid
  * centre: L(c) = sum_b sqrt(H_c(b) * q(b)) (Bhattacharyya coefficient).
  * d_target: float32 [B], q(b) >= 0, summing to 1 (not checked on the device).
- * d_map: float32 [H-win_h+1][W-win_w+1], written, row-major. */
+ * d_map: float32 [H-win_h+1][W-win_w+1], written, row-major.
+ * A launch that would leave the GPU partly idle in its last wave splits each
+ * window's bins over several CTAs; their partial sums go to a scratch area
+ * inside the plan and a second launch adds them in a fixed order (results
+ * are deterministic). Calls on one plan therefore must not overlap on the
+ * GPU: enqueue them on one stream, or order them with events. */
 swih_status swih_likelihood(swih_plan_t plan, int kernel, int win_w, int win_h,
                             const float *d_target, float *d_map, void *stream);
 
@@ -439,6 +445,12 @@ swih_status swih_server_submit(swih_server_t server, const swih_query *query, ui
  * microseconds for the first when none is ready. */
 swih_status swih_server_poll(swih_server_t server, swih_completion *out, int32_t max, int32_t *n,
                              int32_t wait_us);
+
+/* Cancel a query that is still waiting for admission: it completes at once
+ * with status SWIH_ERR_CANCELLED and nothing of it runs. A query already
+ * admitted (or finished, or unknown) is left alone and SWIH_ERR_INVALID_ARG
+ * is returned. */
+swih_status swih_server_cancel(swih_server_t server, uint64_t id);
 
 /* Block until every submitted query has completed (completions stay queued
  * for swih_server_poll). */

@@ -182,7 +182,7 @@ __device__ __forceinline__ void axis_bernstein(const unsigned long long (&R)[5],
 
 // One work item: column tile `tile` and chain `cy` (phase-major) of job p.
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
-__device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const int tile, const int cy)
+__device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const int tile, const int cy, const int bg)
 {
     using u64 = unsigned long long;
     extern __shared__ __align__(128) unsigned char sm[];
@@ -208,7 +208,12 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     const int n_slots = (p.ncy - phase + h - 1) / h;
     const int slot0 = blk * p.kchain;
     const int K = min(p.kchain, n_slots - slot0);
-    if (K <= 0) return;  // whole CTA, before any barrier
+    // bin group bg takes the bin blocks [bb0, bb1)
+    const int NBB = (p.B + BB - 1) / BB;
+    const int per_group = (NBB + p.nbg - 1) / p.nbg;
+    const int bb0 = bg * per_group;
+    const int bb1 = min(NBB, bb0 + per_group);
+    if (K <= 0 || bb0 >= bb1) return;  // whole CTA, before any barrier
 
     const int xs = p.cx0 + tile * TX;
     int xc = xs + (producer ? 0 : tid);
@@ -216,8 +221,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     xc = min(xc, p.cx0 + p.ncx - 1);
     const int yc0 = p.cy0 + phase + slot0 * h;
     const int S = kMan ? 2 * K + 1 : K + 1;  // lattice rows
-    const int NBB = (p.B + BB - 1) / BB;     // bin blocks
-    const int steps = NBB * S * G;
+    const int steps = (bb1 - bb0) * S * G;
     const int NS = p.nstage;
 
     // row segment [xs-rx-1, xs+TX+rx) of every plane, copied from a 16-byte boundary
@@ -263,7 +267,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     // consumers have released that stage's previous step
     if (producer) {
         if (lane != 0) return;
-        int g = 0, s = 0, bb = 0;
+        int g = 0, s = 0, bb = bb0;
         for (int m = 0; m < steps; ++m) {
             const int st_i = m % NS;
             if (m >= NS && !mbar_wait(&empty[st_i], (uint32_t)(((m / NS) - 1) & 1))) {
@@ -341,7 +345,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     int n = 0;          // step index
     int cs = 0;         // consumer stage
     uint32_t cpar = 0;  // its parity
-    for (int bb = 0; bb < NBB && !stop; ++bb) {
+    for (int bb = bb0; bb < bb1 && !stop; ++bb) {
         const int b0 = bb * BB;
         const int nb = min(BB, p.B - b0);
         for (int s = 0; s < S && !stop; ++s) {
@@ -511,7 +515,12 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
         for (int t = 0; t < NT; ++t)
             for (int k = 0; k < K; ++k) {
                 const int yc = yc0 + k * h;
-                p.map[t * p.map_stride + (int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)] = s_acc[(t * KC + k) * TX + tid];
+                const int64_t at = (int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0);
+                const float v = s_acc[(t * KC + k) * TX + tid];
+                if (p.nbg == 1)
+                    p.map[t * p.map_stride + at] = v;
+                else  // this group's share, summed over the groups by gather_reduce_kernel
+                    p.partial[((int64_t)bg * NT + t) * p.ncy * p.ncx + at] = v;
             }
     }
 }
@@ -520,7 +529,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
 __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(const __grid_constant__ GatherParams p)
 {
-    gather_tiled_body<KIND, T, TX, DX, DY, BB>(p, blockIdx.x, blockIdx.y);
+    gather_tiled_body<KIND, T, TX, DX, DY, BB>(p, blockIdx.x, blockIdx.y / p.nbg, blockIdx.y % p.nbg);
 }
 
 // A table of jobs sharing one shape: one CTA per work item, items of job j
@@ -538,7 +547,23 @@ __global__ void __launch_bounds__(TX + 32)
     const GatherParams &p = jobs[lo];
     const int li = item - item_start[lo];
     const int tiles = (p.ncx + TX - 1) / TX;
-    gather_tiled_body<KIND, T, TX, DX, DY, BB>(p, li % tiles, li / tiles);
+    const int rest = li / tiles;
+    gather_tiled_body<KIND, T, TX, DX, DY, BB>(p, li % tiles, rest / p.nbg, rest % p.nbg);
+}
+
+// map[t][i] = sum over bin groups g (in order) of partial[g][t][i]
+__global__ void __launch_bounds__(256)
+    gather_reduce_kernel(const float *__restrict__ partial, float *__restrict__ map, int nbg, int nt,
+                         int64_t n, int64_t map_stride)
+{
+    const int64_t total = n * nt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / n, j = i - t * n;
+        float v = 0.f;
+        for (int g = 0; g < nbg; ++g) v += partial[((int64_t)g * nt + t) * n + j];
+        map[t * map_stride + j] = v;
+    }
 }
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
@@ -633,7 +658,7 @@ struct SingleLaunch {
         cudaError_t e = set_smem(fn, sh->smem);
         if (e != cudaSuccess) return e;
         const int h = 2 * p->ry + 1;
-        const dim3 grid((unsigned)((p->ncx + TX - 1) / TX), (unsigned)(h * p->nblk));
+        const dim3 grid((unsigned)((p->ncx + TX - 1) / TX), (unsigned)(h * p->nblk * p->nbg));
         fn<<<grid, TX + 32, sh->smem, s>>>(*p);
         return cudaGetLastError();
     }
@@ -713,6 +738,7 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         if (ns < 2) continue;
         sh.nstage = ns;
         sh.smem = sh.stage_off + ns * stage;
+        sh.ctas_per_sm = std::max(1, std::min(ctas, (int)((size_t)227 * 1024 / (sh.smem + 1024))));
         *shape = sh;
         return cudaSuccess;
     }
@@ -732,10 +758,44 @@ int tiled_items(GatherParams *job, const GatherShape &shape)
     job->nstage = shape.nstage;
     job->stage_off = shape.stage_off;
     job->dtop_off = shape.dtop_off;
+    if (job->nbg < 1) job->nbg = 1;
     if (job->ncx <= 0 || job->ncy <= 0) return 0;
     const int tiles = (job->ncx + shape.tx - 1) / shape.tx;
-    return tiles * h * nb;
+    return tiles * h * nb * job->nbg;
 }
+
+namespace {
+
+// Bin groups for one launch: the count (1, 2, 4 or 8) that minimises the
+// modelled time, (waves of resident CTAs) x (bin blocks per CTA + c), with c
+// one bin block of fixed cost per CTA (pipeline fill, set-up, output), so a
+// launch of 1.6 waves is split into many short CTAs rather than leaving its
+// second wave 40% empty.
+int choose_bin_groups(const GatherParams &p, const GatherShape &sh, long long base_ctas)
+{
+    if (!p.map || !p.partial || p.partial_cap <= 0) return 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long res = (long long)std::max(1, sms) * sh.ctas_per_sm;
+    const int nbb = (p.B + sh.bb - 1) / sh.bb;
+    const double c = 1.0;
+    int best = 1;
+    double best_cost = (double)((base_ctas + res - 1) / res) * (nbb + c);
+    for (int g = 2; g <= 8 && g <= nbb; g *= 2) {
+        if ((long long)g * p.n_targets * p.ncx * p.ncy > p.partial_cap) break;
+        const int per = (nbb + g - 1) / g;
+        if ((g - 1) * per >= nbb) continue;  // a group without bins would leave its partials unwritten
+        const double cost = (double)((base_ctas * g + res - 1) / res) * (per + c);
+        if (cost < 0.97 * best_cost) {
+            best = g;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+}  // namespace
 
 cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_bytes, cudaStream_t s)
 {
@@ -746,10 +806,22 @@ cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_byt
                                 p_in.n_targets, p_in.want_tx, p_in.want_stages, p_in.want_bb, &sh);
     if (e != cudaSuccess) return e;
     GatherParams p = p_in;
-    tiled_items(&p, sh);
+    p.nbg = 1;
+    const long long base = tiled_items(&p, sh);
+    p.nbg = choose_bin_groups(p, sh, base);
+    if ((long long)(2 * p.ry + 1) * p.nblk * p.nbg > 65535) p.nbg = 1;
     if ((long long)(2 * p.ry + 1) * p.nblk > 65535) return cudaErrorNotSupported;
     SingleLaunch L{&p, &sh, s};
-    return dispatch(kind, elem_bytes, p.gdx, p.gdy, sh.tx, sh.bb, L);
+    e = dispatch(kind, elem_bytes, p.gdx, p.gdy, sh.tx, sh.bb, L);
+    if (e != cudaSuccess || p.nbg == 1) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n = (int64_t)p.ncx * p.ncy;
+    const long long blocks = std::min<long long>((n * p.n_targets + 255) / 256, (long long)std::max(1, sms) * 8);
+    gather_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(p.partial, p.map, p.nbg, p.n_targets, n,
+                                                          p.n_targets > 1 ? p.map_stride : 0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather_table(const GatherParams *d_jobs, const int *d_item_start, int n_jobs,

@@ -255,6 +255,10 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     pl->off_incl = take(n_chains * pl->n_bands * pl->ih_pitch * es);
     pl->flags_bytes = (n_chains * pl->n_bands + 1) * sizeof(int);  // flags + ticket
     pl->off_flags = take(pl->flags_bytes);
+    // per-bin-group likelihoods of a split gather: up to 8 groups of the
+    // largest map, at most 64 MB
+    pl->partial_floats = std::min<uint64_t>((uint64_t)8 * H * W, (64ull << 20) / sizeof(float));
+    pl->off_partial = take(pl->partial_floats * sizeof(float));
     take(sizeof(uint32_t) * 64);  // status word
     pl->total = off;
     if (d->hbm_budget_bytes && pl->total > d->hbm_budget_bytes) {
@@ -329,6 +333,9 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
     g.n_targets = 1;
     g.target_stride = pl->desc.bins;
     g.map_stride = 0;
+    g.nbg = 1;
+    g.partial = pl->partial_floats ? reinterpret_cast<float *>(pl->d_mem + pl->off_partial) : nullptr;
+    g.partial_cap = (int64_t)pl->partial_floats;
     g.want_tx = pl->cfg_tx[kernel];
     g.want_stages = pl->cfg_stages[kernel];
     g.want_bb = pl->cfg_bb[kernel];

@@ -29,6 +29,7 @@ struct swih_plan_s {
     int scan_E = 4, scan_threads = 32;
     uint64_t off_ih = 0, off_agg = 0, off_incl = 0, off_flags = 0, total = 0;
     uint64_t flags_bytes = 0;
+    uint64_t off_partial = 0, partial_floats = 0;  // split-gather scratch
     char *d_mem = nullptr;
     uint32_t *d_status = nullptr;
     int device = 0;

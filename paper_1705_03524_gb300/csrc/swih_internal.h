@@ -127,6 +127,9 @@ struct GatherParams {
     int want_tx;            // requested tile width, 128 or 256 (0: default)
     int want_bb;            // requested bins per pipeline step, 4 or 8 (0: default)
     int kchain, nblk;       // windows per chain, chains per phase (set by the launcher)
+    int nbg;                // bin groups: CTAs that split a chain's bins (1: one CTA, writes the map)
+    float *partial;         // nbg > 1: per-group likelihoods [nbg][n_targets][ncy][ncx], then summed
+    int64_t partial_cap;    // floats available at partial (0: no splitting)
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
@@ -145,6 +148,7 @@ struct GatherShape {
     int seg, nl, nstage, stage_off, dtop_off;
     int kchain_max;  // windows per chain
     int n_targets;   // likelihood accumulators per window (largest n_targets of the jobs)
+    int ctas_per_sm; // resident CTAs per SM this shape allows (registers, shared memory, threads)
     size_t smem;     // dynamic shared memory bytes
 };
 // Shape for jobs of one kind with the given fitted degrees, largest window

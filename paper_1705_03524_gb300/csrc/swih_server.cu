@@ -54,6 +54,7 @@ struct Query {
     uint64_t id = 0;
     uint64_t submit_ns = 0;
     uint64_t start_ns = 0;
+    bool admitting = false;  // copied by the scheduler for a micro-batch being built
 };
 
 struct MicroBatch {
@@ -439,6 +440,7 @@ void swih_server_s::run()
         int si;
         while (!mem_blocked && !queue.empty() && (si = free_slot()) >= 0) {
             const size_t k = std::min<size_t>((size_t)std::max(1, desc.max_batch_queries), queue.size());
+            for (size_t i = 0; i < k; ++i) queue[i].admitting = true;  // cancel leaves these alone
             std::vector<Query> cand(queue.begin(), queue.begin() + (long)k);
             lk.unlock();
             MicroBatch *mb = nullptr;
@@ -465,6 +467,9 @@ void swih_server_s::run()
                 take = 1;
             }
             lk.lock();
+            // the candidates are still the queue's first k entries: cancel skips
+            // them and submissions only append
+            for (size_t i = 0; i < k; ++i) queue[i].admitting = false;
             if (!mb && !fatal) {
                 if (take > 1 || !idle()) {
                     mem_blocked = true;  // wait for a retirement
@@ -639,6 +644,31 @@ swih_status swih_server_poll(swih_server_t S, swih_completion *out, int32_t max,
         S->completions.pop_front();
     }
     return SWIH_OK;
+}
+
+swih_status swih_server_cancel(swih_server_t S, uint64_t id)
+{
+    if (!S) return sfail(SWIH_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+            if (it->id != id) continue;
+            if (it->admitting) return sfail(SWIH_ERR_INVALID_ARG, "query is being admitted");
+            swih_completion c;
+            c.id = it->id;
+            c.user_tag = it->q.user_tag;
+            c.status = SWIH_ERR_CANCELLED;
+            c.batch_queries = 0;
+            c.submit_ns = it->submit_ns;
+            c.start_ns = c.done_ns = now_ns();
+            S->queue.erase(it);
+            S->completions.push_back(c);
+            --S->outstanding;
+            S->cv_done.notify_all();
+            return SWIH_OK;
+        }
+    }
+    return sfail(SWIH_ERR_INVALID_ARG, "query " + std::to_string(id) + " is not waiting for admission");
 }
 
 swih_status swih_server_drain(swih_server_t S)

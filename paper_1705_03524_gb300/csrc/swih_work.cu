@@ -213,6 +213,9 @@ swih_status WorkSet::build_jobs(std::string &err)
         g.target = jb.target;
         g.map = jb.map;
         g.hist = nullptr;
+        g.nbg = 1;  // table launches span many waves already; no split-gather scratch here
+        g.partial = nullptr;
+        g.partial_cap = 0;
         g.n_targets = jb.n_targets;
         g.target_stride = jb.n_targets > 1 ? jb.target_stride : spec_.bins;
         g.map_stride = jb.n_targets > 1 ? jb.map_stride : 0;

@@ -24,6 +24,7 @@ SWIH_ERR_OOM = 3
 SWIH_ERR_BUDGET = 4
 SWIH_ERR_CUDA = 5
 SWIH_ERR_TIMEOUT = 6
+SWIH_ERR_CANCELLED = 7
 
 SWIH_PIXEL_U8 = 0
 SWIH_PIXEL_U16 = 1
@@ -247,6 +248,7 @@ def _load() -> ctypes.CDLL:
     lib.swih_server_poll.argtypes = [P, ctypes.POINTER(swih_completion), ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.swih_server_drain.argtypes = [P]
+    lib.swih_server_cancel.argtypes = [P, ctypes.c_uint64]
     lib.swih_server_destroy.argtypes = [P]
     lib.swih_stream_plan.argtypes = [ctypes.POINTER(swih_plan_desc), ctypes.POINTER(swih_frame_job), I, P,
                                      ctypes.c_int32, ctypes.POINTER(P)]
@@ -260,7 +262,7 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = S
     for name in ("swih_server_create", "swih_server_add_frame", "swih_query_out_elems",
                  "swih_server_query_bytes", "swih_server_submit", "swih_server_poll",
-                 "swih_server_drain", "swih_server_destroy"):
+                 "swih_server_drain", "swih_server_destroy", "swih_server_cancel"):
         getattr(lib, name).restype = S
     return lib
 
@@ -637,6 +639,9 @@ class Server:
 
     def drain(self):
         _check(LIB.swih_server_drain(self.handle))
+
+    def cancel(self, qid: int):
+        _check(LIB.swih_server_cancel(self.handle, int(qid)))
 
     def close(self):
         if self.handle:

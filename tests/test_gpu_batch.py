@@ -228,3 +228,36 @@ def test_search_regions_workload_sampled():
                 if k == 1:  # the target window itself scores 1
                     tx, ty = sp.t
                     assert abs(got[ty - y0, tx - x0] - 1.0) <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["plain", "manhattan", "euclidean", "gaussian"])
+def test_every_binary_4x4_image_in_one_batch(kernel):
+    """All 2^16 binary 4 x 4 images, B = 2, 3 x 3 windows: 65536 regions in one
+    batched launch. Image t sits at tile (t % 256, t // 256) of a 1024 x 1024
+    frame, pixel (i, j) = 255 * bit (4 i + j) of t. The 3 x 3 windows around a
+    tile's four centres stay inside the tile, so the oracle on the tiled frame
+    gives every image's own answer."""
+    t = np.arange(1 << 16, dtype=np.int64)
+    bits = (t[:, None] >> np.arange(16)[None, :]) & 1          # [image][4 i + j]
+    tiles = (bits.reshape(256, 256, 4, 4) * 255).astype(np.uint8)  # [ty][tx][i][j]
+    img = np.ascontiguousarray(tiles.transpose(0, 2, 1, 3).reshape(1024, 1024))
+    B = 2
+    q = np.array([0.3, 0.7])
+    target = torch.tensor(q, dtype=torch.float32, device=DEV)
+    maps = torch.full((1 << 16, 2, 2), -1.0, device=DEV)
+    buf, ptr, pitch = upload(img)
+    rois = [S.make_roi(4 * (k % 256), 4 * (k // 256), 4, 4, kernel, [(3, 3)], target, [maps[k]])
+            for k in range(1 << 16)]
+    desc = S.make_batch_desc(1024, 1024, pitch_bytes=pitch, bins=B, kernels=(kernel,))
+    with S.Batch(desc, rois, ptr, keep=[buf, target, maps]) as b:
+        b.run()
+        b.sync_status()
+    got = maps.cpu().numpy()
+    bins = oracle_bins(img, 8, B)
+    K = O.kernel_weights(kernel, 3, 3)
+    ty, tx = np.divmod(np.arange(1 << 16), 256)
+    for dy in (0, 1):
+        for dx in (0, 1):
+            ref = O.likelihood_at(bins, B, K, q, 4 * tx + 1 + dx, 4 * ty + 1 + dy)
+            err = np.abs(got[:, dy, dx] - ref).max()
+            assert err <= TOL, (kernel, dx, dy, err)

@@ -247,3 +247,35 @@ def test_wide_window_multi_target_uses_direct_gather():
             m = got[off: off + r * cc].reshape(r, cc)
             err = np.abs(m[cy - y0, cx - x0] - ref).max()
             assert err <= TOL, (t, ww, err)
+
+
+def test_cancel_queued_queries():
+    scene = Scene(seed=12)
+    specs = make_specs(scene, 30, seed=13, overlap=False)
+    outs = [sp.new_out() for sp in specs]
+    cancelled, refused = set(), 0
+    with S.Server(hbm_budget_bytes=8 << 30, max_inflight=1, max_batch_queries=1) as srv:
+        ids = scene.register(srv)
+        qids = [srv.submit(sp.query(ids, o, tag=i)) for i, (sp, o) in enumerate(zip(specs, outs))]
+        for i in range(10, 30, 2):
+            try:
+                srv.cancel(qids[i])
+                cancelled.add(qids[i])
+            except S.SwihError as e:  # already admitted or being admitted
+                assert e.status == S.SWIH_ERR_INVALID_ARG
+                refused += 1
+        with pytest.raises(S.SwihError):
+            srv.cancel(10 ** 9)  # unknown id
+        srv.drain()
+        comps = srv.poll(64)
+    assert len(comps) == 30 and len(cancelled) >= 5
+    for c in comps:
+        i = c.user_tag
+        if c.id in cancelled:
+            assert c.status == S.SWIH_ERR_CANCELLED
+            assert (outs[i] == -1.0).all(), "a cancelled query wrote its maps"
+        else:
+            assert c.status == S.SWIH_OK
+    for i in (0, 1, 11, 29):
+        if qids[i] not in cancelled:
+            check_oracle(scene, specs[i], outs[i])
