@@ -282,7 +282,7 @@ def run_swih(args, rank, world, local_rank):
     dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
     peak, peak_kind = read_peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    src = "k2_ih_scan.cu" if dom.startswith("ih_scan") else "k3_gather_tiled.cu"
+    src = "k2_ih_scan.cu" if dom.startswith("ih_scan") else "k3_tiled_kernels.cuh"
     prof = "ih_scan_gaussian_1024" if dom.startswith("ih_scan (G") else (
         "gather_gaussian_1024" if dom == "gather Gaussian" else None)
     if H != 1024 or B != 32:

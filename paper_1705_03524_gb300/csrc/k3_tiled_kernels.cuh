@@ -1,0 +1,636 @@
+// K3 (tiled): the window gather of Sec. 2.1 with lattice-row reuse.
+//
+// Computes exactly what k3_gather.cu computes (same ring arithmetic, same
+// translation, same normalisation and Bhattacharyya sum), organised so that each
+// integral-histogram element is fetched about once per launch instead of four
+// to nine times:
+//
+// * A CTA owns TX consecutive centre columns (one thread per column) and a
+//   chain of up to KMAX centre rows spaced exactly one window height h apart.
+//   Window k's bottom corner row is window k+1's top corner row, so the chain
+//   walks K+1 lattice rows for K windows (Manhattan adds each window's centre
+//   row, which splits it into top and bottom halves: 2K+1 rows).
+// * Work is a sequence of pipeline steps (bin block, lattice row, plane group).
+//   A step carries BB bins (several for the cheap kernels, one for the
+//   Gaussian) and, for the Gaussian, one y-exponent l, i.e. the planes
+//   x^0..x^2Dx y^l. A dedicated producer warp (one lane) issues, for each step,
+//   TMA bulk copies (cp.async.bulk, completion counted on a "full" mbarrier)
+//   of the row segments [xs-rx-1, xs+TX+rx) into one stage of a ring of NS
+//   shared-memory stages, up to NS steps ahead of the consumers. Each consumer
+//   warp releases a stage through an "empty" mbarrier, and the producer refills
+//   a stage only after every consumer warp has released it.
+// * Every thread forms its horizontal differences I(X2) - I(X0) (and the
+//   centre split for Manhattan) from shared memory; the vertical difference is
+//   taken against the previous lattice row's values held in registers.
+//   For the Gaussian the carried values are already translated to the centre
+//   column and mapped to the Bernstein basis along x (a linear map, so it
+//   commutes with the vertical difference).
+// * The likelihood of each of the K windows accumulates over bins in shared
+//   memory (one slot per window and column) and is written once at the end.
+// CTAs are ordered with the column tiles fastest and the chains of one phase
+// adjacent, so the halo columns of neighbouring tiles and the boundary row of
+// neighbouring chains are shared through L2 while both are resident.
+// Every mbarrier wait is bounded; a wait that gives up sets the status word and
+// stops the waiting warp. Copies already issued always land in shared memory
+// that stays allocated until the consumer warps, which wait for them, exit.
+//
+// This header holds the device code; k3_tiled_<kind>.cu instantiate it, one
+// kernel kind per translation unit, and k3_gather_tiled.cu holds the host side.
+#pragma once
+
+#include "k3_tiled.h"
+
+namespace swih {
+namespace {
+
+
+constexpr int KMAX = kTiledChainMax;
+constexpr int kMaxStages = kTiledMaxStages;
+
+template <typename T>
+struct template_tag {
+    using type = T;
+};
+template <int V>
+struct int_tag {
+    static constexpr int value = V;
+};
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr uint32_t kSuspendHintNs = 200000;                   // sleep up to 0.2 ms per try
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// test the phase; the thread may sleep (up to the hint) until it completes
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendHintNs)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait (about 2 s of wall time); false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// a * b for a 64-bit ring element and a 32-bit factor (two IMADs)
+__device__ __forceinline__ unsigned long long mul_u32(unsigned long long a, uint32_t b)
+{
+    const unsigned long long lo = (unsigned long long)(uint32_t)a * b;
+    const uint32_t hi = (uint32_t)(a >> 32) * b;
+    return lo + ((unsigned long long)hi << 32);
+}
+
+// non-negative 64-bit integer to float via two 32-bit conversions
+__device__ __forceinline__ float u64_to_float(unsigned long long v)
+{
+    return fmaf(__uint2float_rn((uint32_t)(v >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)v));
+}
+
+template <typename T>
+__device__ __forceinline__ float ring_to_float(T v)
+{
+    if constexpr (sizeof(T) == 4)
+        return __uint2float_rn((uint32_t)v);
+    else
+        return u64_to_float((unsigned long long)v);
+}
+
+// Even centred moments of one axis from raw moments R[0..2D] (Horner in the
+// centre c: sum_k C(m,k) (-c)^(m-k) R_k), then the Bernstein map of degree D:
+//   out_i = sum over the axis of C(D,i) d^2i (r^2 - d^2)^(D-i).
+// c (a centre coordinate) and r2 = r^2 fit 32 bits; r4 = r^4 may not (r > 255).
+template <int D>
+__device__ __forceinline__ void axis_bernstein(const unsigned long long (&R)[5], uint32_t c, uint32_t r2,
+                                               unsigned long long r4, unsigned long long (&out)[3])
+{
+    using u64 = unsigned long long;
+    // m2 = R2 - 2c R1 + c^2 R0
+    u64 t = R[0];
+    t = 2 * R[1] - mul_u32(t, c);
+    const u64 m2 = R[2] - mul_u32(t, c);
+    if constexpr (D == 1) {
+        out[0] = mul_u32(R[0], r2) - m2;
+        out[1] = m2;
+        out[2] = 0;
+    } else {
+        // m4 = R4 - 4c R3 + 6c^2 R2 - 4c^3 R1 + c^4 R0
+        u64 v = R[0];
+        v = 4 * R[1] - mul_u32(v, c);
+        v = 6 * R[2] - mul_u32(v, c);
+        v = 4 * R[3] - mul_u32(v, c);
+        const u64 m4 = R[4] - mul_u32(v, c);
+        const u64 r2m2 = mul_u32(m2, r2);
+        out[0] = R[0] * r4 - 2 * r2m2 + m4;
+        out[1] = 2 * (r2m2 - m4);
+        out[2] = m4;
+    }
+}
+
+// One work item: column tile `tile` and chain `cy` (phase-major) of job p.
+template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SPLIT>
+__device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const int tile, const int cy, const int bg)
+{
+    using u64 = unsigned long long;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);
+    uint64_t *empty = full + kMaxStages;
+    float *s_sq = reinterpret_cast<float *>(sm + 16 * kMaxStages);
+    float *s_acc = s_sq + p.n_targets * p.B;
+    T *stages = reinterpret_cast<T *>(sm + p.stage_off);
+
+    constexpr int NWARP = TX / 32;
+    constexpr bool kMan = KIND == kGatherManhattan;
+    constexpr bool kGau = KIND == kGatherGaussian;
+    constexpr int KX = 2 * DX, KY = 2 * DY;  // Gaussian raw-moment orders
+    constexpr int G = kGau ? KY + 1 : 1;     // plane groups per lattice row
+    static_assert(!kGau || BB == 1, "the Gaussian carries one bin per step");
+
+    const int tid = threadIdx.x;  // threads [0, TX): consumers; warp TX/32: producer
+    const int lane = tid & 31;
+    const bool producer = tid >= TX;
+    const int h = 2 * p.ry + 1;
+    const int blk = cy % p.nblk;
+    const int phase = cy / p.nblk;
+    const int n_slots = (p.ncy - phase + h - 1) / h;
+    const int slot0 = blk * p.kchain;
+    const int K = min(p.kchain, n_slots - slot0);
+    // bin blocks [bb0, bb1): all of them, or bin group bg's share of a split launch
+    const int NBB = (p.B + BB - 1) / BB;
+    int bb0 = 0, bb1 = NBB;
+    if constexpr (SPLIT) {
+        const int per_group = (NBB + p.nbg - 1) / p.nbg;
+        bb0 = bg * per_group;
+        bb1 = min(NBB, bb0 + per_group);
+    }
+    if (K <= 0 || bb0 >= bb1) return;  // whole CTA, before any barrier
+
+    const int xs = p.cx0 + tile * TX;
+    int xc = xs + (producer ? 0 : tid);
+    const bool valid_x = xc < p.cx0 + p.ncx;
+    xc = min(xc, p.cx0 + p.ncx - 1);
+    const int yc0 = p.cy0 + phase + slot0 * h;
+    const int S = kMan ? 2 * K + 1 : K + 1;  // lattice rows
+    const int steps = (bb1 - bb0) * S * G;
+    const int NS = p.nstage;
+
+    // row segment [xs-rx-1, xs+TX+rx) of every plane, copied from a 16-byte boundary
+    constexpr int A = 16 / (int)sizeof(T);
+    const int xlo = xs - p.rx - 1;  // >= -1
+    const int xo = xlo >= 0 ? (xlo / A) * A : -A;
+    const int x_begin = xo > 0 ? xo : 0;
+    const int x_end = min(xs + TX + p.rx, p.W);
+    const uint32_t seg_bytes = (uint32_t)(((x_end - x_begin) * (int)sizeof(T) + 15) & ~15);
+    const int land = x_begin - xo;
+    const int stage_elems = p.nl * p.seg;  // nl = slots per stage (BB * planes per step)
+
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], NWARP);  // consumer warps
+        }
+        mbar_init_fence();
+    }
+    // sqrt(q_t(b)) of every target; one accumulator per (target, window, column)
+    const int NT = p.n_targets;
+    const int KC = p.kchain;
+    for (int i = tid; i < NT * p.B; i += TX + 32) {
+        const int t = i / p.B;
+        s_sq[i] = p.target ? sqrtf(fmaxf(p.target[t * p.target_stride + (i - t * p.B)], 0.f)) : 0.f;
+    }
+    if (!producer)
+        for (int k = 0; k < NT * KC; ++k) s_acc[k * TX + tid] = 0.f;
+    if (xlo < 0) {  // column -1 of the integral histogram is 0; copies never land there
+        for (int i = tid; i < NS * p.nl; i += TX + 32) stages[(size_t)i * p.seg + (A - 1)] = T(0);
+    }
+    __syncthreads();
+
+    auto row_of = [&](int s) -> int {
+        if constexpr (kMan) {
+            const int k = s >> 1;
+            return (s & 1) ? yc0 + k * h : yc0 + k * h - p.ry - 1;
+        } else {
+            return yc0 + s * h - p.ry - 1;
+        }
+    };
+    // producer warp, lane 0: steps in order, each into stage m % NS once the
+    // consumers have released that stage's previous step
+    if (producer) {
+        if (lane != 0) return;
+        int g = 0, s = 0, bb = bb0;
+        for (int m = 0; m < steps; ++m) {
+            const int st_i = m % NS;
+            if (m >= NS && !mbar_wait(&empty[st_i], (uint32_t)(((m / NS) - 1) & 1))) {
+                atomicOr(p.status, kStatusTimeout);
+                return;
+            }
+            const int Y = row_of(s);
+            uint64_t *br = &full[st_i];
+            if (Y < 0) {  // the zero row above the image: nothing to copy
+                mbar_arrive(br);
+            } else {
+                int nt;
+                const int *list;
+                if constexpr (kGau) {
+                    nt = KX + 1;
+                    list = p.load_even + g * (KX + 1);
+                } else {
+                    const bool odd = kMan && (s & 1);
+                    nt = odd ? p.n_load_odd : p.n_load_even;
+                    list = odd ? p.load_odd : p.load_even;
+                }
+                const int b0 = bb * BB;
+                const int nb = min(BB, p.B - b0);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(br, (uint32_t)(nb * nt) * seg_bytes);
+                T *dst = stages + (size_t)st_i * stage_elems + land;
+                const T *row = reinterpret_cast<const T *>(p.ih) + (int64_t)Y * p.pitch + x_begin;
+                for (int j = 0; j < nb; ++j)
+                    for (int t = 0; t < nt; ++t) {
+                        const T *src = row + ((int64_t)list[t] * p.B + b0 + j) * p.plane;
+                        bulk_copy_g2s(dst + (size_t)(j * nt + t) * p.seg, src, seg_bytes, br);
+                    }
+            }
+            if (++g == G) {
+                g = 0;
+                if (++s == S) {
+                    s = 0;
+                    ++bb;
+                }
+            }
+        }
+        return;
+    }
+
+    const int i0 = xc - p.rx - 1 - xo;  // smem index of X0 (column -1 reads the zeroed word)
+    const int i1 = xc - xo;
+    const int i2 = xc + p.rx - xo;
+    const T txc = (T)xc;
+
+    // carried values of the previous lattice row, per bin of the block
+    T top[BB][5];
+    T mid1[BB], midy[BB];
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+        mid1[j] = midy[j] = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) top[j][i] = 0;
+    }
+    // Gaussian: raw row differences of the previous lattice row (shared memory,
+    // one column per thread), and the current window's x-translated Bernstein
+    // moments per y-exponent (registers)
+    u64 *dtop = reinterpret_cast<u64 *>(sm + p.dtop_off) + tid;
+    if constexpr (kGau) {
+#pragma unroll
+        for (int i = 0; i < (KX + 1) * (KY + 1); ++i) dtop[i * TX] = 0;
+    }
+    u64 E[3][5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int l = 0; l < 5; ++l) E[i][l] = 0;
+    bool occupied = false;  // Gaussian: the bin has pixels in the current window
+
+    bool stop = false;
+    int n = 0;          // step index
+    int cs = 0;         // consumer stage
+    uint32_t cpar = 0;  // its parity
+    for (int bb = bb0; bb < bb1 && !stop; ++bb) {
+        const int b0 = bb * BB;
+        const int nb = min(BB, p.B - b0);
+        for (int s = 0; s < S && !stop; ++s) {
+            const bool zero_row = row_of(s) < 0;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (!mbar_wait(&full[cs], cpar)) stop = true;
+                if (stop) break;
+                const T *st = stages + (size_t)cs * stage_elems;
+
+                if constexpr (kGau) {
+                    // planes x^0..x^KX of y^g: window sums R = this row's horizontal
+                    // differences minus the previous lattice row's
+                    u64 R[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+                    for (int k = 0; k <= KX; ++k) {
+                        const u64 d = zero_row ? 0ull : (u64)st[k * p.seg + i2] - (u64)st[k * p.seg + i0];
+                        R[k] = d - dtop[(g * (KX + 1) + k) * TX];
+                        dtop[(g * (KX + 1) + k) * TX] = d;
+                    }
+                    // a bin with no pixel in the window has every moment zero: its
+                    // translation is skipped (the pixel count is the x^0 y^0 plane)
+                    if (g == 0) occupied = s > 0 && R[0] != 0;
+                    if (occupied) {
+                        u64 ex[3] = {0, 0, 0};
+                        axis_bernstein<DX>(R, (uint32_t)xc, (uint32_t)p.rx2, p.rx4, ex);
+#pragma unroll
+                        for (int i = 0; i <= DX; ++i) E[i][g] = ex[i];
+                    }
+                } else {
+                    // the window completed by this lattice row (if any); its
+                    // likelihood terms for the step's bins are summed in a register
+                    const int done_k = kMan ? ((s & 1) || s == 0 ? -1 : (s >> 1) - 1) : s - 1;
+                    float step_acc = 0.f;
+#pragma unroll
+                    for (int j = 0; j < BB; ++j) {
+                        if (j >= nb) break;
+                        const int b = b0 + j;
+                        // h stays 0 for a bin with no pixel in the window: the
+                        // combination, conversion and square root are skipped
+                        float hval = 0.f;
+                        if constexpr (KIND == kGatherPlain) {
+                            const T *q = st + (size_t)j * p.seg;
+                            const T d = zero_row ? T(0) : (T)(q[i2] - q[i0]);
+                            if (done_k >= 0) {
+                                const T U = d - top[j][0];
+                                if (U != 0) hval = ring_to_float<T>(U) * p.inv_mass;
+                            }
+                            top[j][0] = d;
+                        } else if constexpr (kMan) {
+                            if (s & 1) {  // centre row: full-width sums of IH_1 and IH_y
+                                const T *q = st + (size_t)(j * 2) * p.seg;
+                                mid1[j] = q[i2] - q[i0];
+                                midy[j] = q[p.seg + i2] - q[p.seg + i0];
+                            } else {
+                                T d1l = 0, d1r = 0, dxl = 0, dxr = 0, dyf = 0;
+                                if (!zero_row) {
+                                    const T *q = st + (size_t)(j * 3) * p.seg;
+                                    const T a0 = q[i0], a1 = q[i1], a2 = q[i2];
+                                    const T *sx = q + p.seg;
+                                    const T *sy = q + 2 * p.seg;
+                                    d1l = a1 - a0;
+                                    d1r = a2 - a1;
+                                    dxl = sx[i1] - sx[i0];
+                                    dxr = sx[i2] - sx[i1];
+                                    dyf = sy[i2] - sy[i0];
+                                }
+                                if (done_k >= 0) {
+                                    const T R1l = d1l - top[j][0], R1r = d1r - top[j][1];
+                                    const T R1 = R1l + R1r;  // pixel count of the bin in the window
+                                    if (R1 != 0) {
+                                        const T tyc = (T)(yc0 + done_k * h);
+                                        const T R1t = mid1[j] - (top[j][0] + top[j][1]);
+                                        const T R1b = (d1l + d1r) - mid1[j];
+                                        const T Rxl = dxl - top[j][2], Rxr = dxr - top[j][3];
+                                        const T Ryt = midy[j] - top[j][4], Ryb = dyf - midy[j];
+                                        const T sdx = (Rxr - txc * R1r) - (Rxl - txc * R1l);
+                                        const T sdy = (Ryb - tyc * R1b) - (Ryt - tyc * R1t);
+                                        const T U = (T)(p.rx + p.ry) * R1 - sdx - sdy;
+                                        hval = ring_to_float<T>(U) * p.inv_mass;
+                                    }
+                                }
+                                top[j][0] = d1l;
+                                top[j][1] = d1r;
+                                top[j][2] = dxl;
+                                top[j][3] = dxr;
+                                top[j][4] = dyf;
+                            }
+                        } else {  // Euclidean
+                            T d[5] = {0, 0, 0, 0, 0};
+                            if (!zero_row) {
+                                const T *q = st + (size_t)(j * 5) * p.seg;
+#pragma unroll
+                                for (int t = 0; t < 5; ++t) d[t] = q[t * p.seg + i2] - q[t * p.seg + i0];
+                            }
+                            if (done_k >= 0) {
+                                const T R1 = d[0] - top[j][0];
+                                if (R1 != 0) {
+                                    const T tyc = (T)(yc0 + done_k * h);
+                                    const T Rx = d[1] - top[j][1], Ry = d[2] - top[j][2];
+                                    const T Rxx = d[3] - top[j][3], Ryy = d[4] - top[j][4];
+                                    const T sdx2 = Rxx - (T)2 * txc * Rx + txc * txc * R1;
+                                    const T sdy2 = Ryy - (T)2 * tyc * Ry + tyc * tyc * R1;
+                                    const T U = ((T)p.rx * (T)p.rx + (T)p.ry * (T)p.ry) * R1 - sdx2 - sdy2;
+                                    hval = ring_to_float<T>(U) * p.inv_mass;
+                                }
+                            }
+#pragma unroll
+                            for (int t = 0; t < 5; ++t) top[j][t] = d[t];
+                        }
+                        if (done_k >= 0) {
+                            if (p.hist && valid_x) {
+                                const int yc = yc0 + done_k * h;
+                                p.hist[((int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)) * p.B + b] = hval;
+                            }
+                            if (hval != 0.f) {
+                                const float sq = sqrtf(hval);
+                                step_acc += sq * s_sq[b];
+                                for (int t = 1; t < NT; ++t)
+                                    s_acc[(t * KC + done_k) * TX + tid] += sq * s_sq[t * p.B + b];
+                            }
+                        }
+                    }
+                    if (done_k >= 0 && p.target) s_acc[done_k * TX + tid] += step_acc;
+                }
+                // release the stage: every lane of the warp is done reading it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[cs]);
+                if (++cs == NS) {
+                    cs = 0;
+                    cpar ^= 1u;
+                }
+                ++n;
+            }
+            if (stop) break;
+            if constexpr (kGau) {
+                if (s > 0) {  // the window above this lattice row is complete
+                    const int k = s - 1;
+                    const uint32_t yc = (uint32_t)(yc0 + k * h);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int i = 0; i <= DX; ++i) {
+                        if (!occupied) break;
+                        u64 R[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+                        for (int l = 0; l <= KY; ++l) R[l] = E[i][l];
+                        u64 o[3] = {0, 0, 0};
+                        axis_bernstein<DY>(R, yc, (uint32_t)p.ry2, p.ry4, o);
+#pragma unroll
+                        for (int j = 0; j <= DY; ++j) acc = fmaf(p.gamma[i][j], u64_to_float(o[j]), acc);
+                    }
+                    if (p.hist && valid_x)
+                        p.hist[((int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0)) * p.B + b0] = acc;
+                    if (p.target && occupied) {
+                        const float sq = sqrtf(acc);
+                        for (int t = 0; t < NT; ++t) s_acc[(t * KC + k) * TX + tid] += sq * s_sq[t * p.B + b0];
+                    }
+                }
+            }
+        }
+    }
+    if (stop) {
+        if (lane == 0) atomicOr(p.status, kStatusTimeout);
+        return;
+    }
+    if (p.map && valid_x) {
+        for (int t = 0; t < NT; ++t)
+            for (int k = 0; k < K; ++k) {
+                const int yc = yc0 + k * h;
+                const int64_t at = (int64_t)(yc - p.cy0) * p.ncx + (xc - p.cx0);
+                const float v = s_acc[(t * KC + k) * TX + tid];
+                if constexpr (SPLIT)  // this group's share, summed over the groups by gather_reduce_kernel
+                    p.partial[((int64_t)bg * NT + t) * p.ncy * p.ncx + at] = v;
+                else
+                    p.map[t * p.map_stride + at] = v;
+            }
+    }
+}
+
+// A single job: the grid is (column tiles, chains).
+template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SPLIT>
+__global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(const __grid_constant__ GatherParams p)
+{
+    if constexpr (SPLIT)
+        gather_tiled_body<KIND, T, TX, DX, DY, BB, true>(p, blockIdx.x, blockIdx.y / p.nbg, blockIdx.y % p.nbg);
+    else
+        gather_tiled_body<KIND, T, TX, DX, DY, BB, false>(p, blockIdx.x, blockIdx.y, 0);
+}
+
+// A table of jobs sharing one shape: one CTA per work item, items of job j
+// numbered from item_start[j] with the column tiles fastest.
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
+__global__ void __launch_bounds__(TX + 32)
+    gather_table_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs)
+{
+    const int item = blockIdx.x;
+    int lo = 0, hi = n_jobs - 1;  // the last job whose first item is <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const GatherParams &p = jobs[lo];
+    const int li = item - item_start[lo];
+    const int tiles = (p.ncx + TX - 1) / TX;
+    gather_tiled_body<KIND, T, TX, DX, DY, BB, false>(p, li % tiles, li / tiles, 0);
+}
+
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
+int kernel_regs()
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, gather_tiled_kernel<KIND, T, TX, DX, DY, BB, false>) != cudaSuccess) return 255;
+    return fa.numRegs;
+}
+
+template <typename KernelFn>
+cudaError_t set_smem(KernelFn fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int K, typename T, int TX, int DX, int DY, int BB>
+cudaError_t run_op(TiledOp &op)
+{
+    switch (op.what) {
+    case TiledOp::kRegs:
+        op.regs = kernel_regs<K, T, TX, DX, DY, BB>();
+        return cudaSuccess;
+    case TiledOp::kSingle: {
+        const GatherParams &p = *op.p;
+        auto fn = p.nbg > 1 ? gather_tiled_kernel<K, T, TX, DX, DY, BB, true>
+                            : gather_tiled_kernel<K, T, TX, DX, DY, BB, false>;
+        cudaError_t e = set_smem(fn, op.sh->smem);
+        if (e != cudaSuccess) return e;
+        const int h = 2 * p.ry + 1;
+        const dim3 grid((unsigned)((p.ncx + TX - 1) / TX), (unsigned)(h * p.nblk * p.nbg));
+        fn<<<grid, TX + 32, op.sh->smem, op.s>>>(p);
+        return cudaGetLastError();
+    }
+    case TiledOp::kTable: {
+        auto fn = gather_table_kernel<K, T, TX, DX, DY, BB>;
+        cudaError_t e = set_smem(fn, op.sh->smem);
+        if (e != cudaSuccess) return e;
+        fn<<<(unsigned)op.n_items, TX + 32, op.sh->smem, op.s>>>(op.d_jobs, op.d_items, op.n_jobs);
+        return cudaGetLastError();
+    }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// every shape of one kind: element type, tile width, bins per step (and, for
+// the Gaussian, the fitted degrees)
+template <int K>
+cudaError_t dispatch_kind(int elem_bytes, int gdx, int gdy, int tx, int bb, TiledOp &op)
+{
+    using u64 = unsigned long long;
+    if constexpr (K == kGatherGaussian) {
+        if (elem_bytes != 8) return cudaErrorInvalidValue;
+        auto by_tx = [&](auto dx_tag, auto dy_tag) -> cudaError_t {
+            constexpr int DX = decltype(dx_tag)::value, DY = decltype(dy_tag)::value;
+            return tx == 128 ? run_op<K, u64, 128, DX, DY, 1>(op) : run_op<K, u64, 256, DX, DY, 1>(op);
+        };
+        if (gdx == 2 && gdy == 2) return by_tx(int_tag<2>{}, int_tag<2>{});
+        if (gdx == 2 && gdy == 1) return by_tx(int_tag<2>{}, int_tag<1>{});
+        if (gdx == 1 && gdy == 2) return by_tx(int_tag<1>{}, int_tag<2>{});
+        if (gdx == 1 && gdy == 1) return by_tx(int_tag<1>{}, int_tag<1>{});
+        return cudaErrorInvalidValue;
+    } else {
+        auto by_type = [&](auto t_tag) -> cudaError_t {
+            using T = typename decltype(t_tag)::type;
+            if (tx == 128) return bb == 8 ? run_op<K, T, 128, 0, 0, 8>(op) : run_op<K, T, 128, 0, 0, 4>(op);
+            return bb == 8 ? run_op<K, T, 256, 0, 0, 8>(op) : run_op<K, T, 256, 0, 0, 4>(op);
+        };
+        if (elem_bytes == 4) return by_type(template_tag<uint32_t>{});
+        if (elem_bytes == 8) return by_type(template_tag<u64>{});
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+}  // namespace swih

@@ -1,0 +1,11 @@
+// Tiled window gather (K3): the manhattan kernels' instantiations.
+#include "k3_tiled_kernels.cuh"
+
+namespace swih {
+
+cudaError_t tiled_dispatch_manhattan(int elem_bytes, int gdx, int gdy, int tx, int bb, TiledOp &op)
+{
+    return dispatch_kind<kGatherManhattan>(elem_bytes, gdx, gdy, tx, bb, op);
+}
+
+}  // namespace swih

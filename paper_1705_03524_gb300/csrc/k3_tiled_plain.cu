@@ -1,0 +1,11 @@
+// Tiled window gather (K3): the plain kernels' instantiations.
+#include "k3_tiled_kernels.cuh"
+
+namespace swih {
+
+cudaError_t tiled_dispatch_plain(int elem_bytes, int gdx, int gdy, int tx, int bb, TiledOp &op)
+{
+    return dispatch_kind<kGatherPlain>(elem_bytes, gdx, gdy, tx, bb, op);
+}
+
+}  // namespace swih
