@@ -183,6 +183,12 @@ typedef struct swih_plan_info {
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
 
+/* Kernels this library has enqueued in this process so far, counted on the
+ * host at each launch (a CUDA graph's kernels count once, when the graph is
+ * captured; replays do not add to it). For reporting how many launches a
+ * piece of work took. */
+swih_status swih_launch_count(uint64_t *count);
+
 /* ---------------------------------------------------------------- batches
  * Many regions of interest (ROIs) of one frame, each with its own size,
  * kernel, windows (scales) and target histogram, processed by a fixed set of

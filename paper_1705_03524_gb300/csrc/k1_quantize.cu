@@ -109,6 +109,7 @@ cudaError_t launch_quantize(const QuantParams &p, cudaStream_t s)
         quantize_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(p);
     else
         quantize_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(p);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -126,6 +127,7 @@ cudaError_t launch_quantize_table(const QuantRoi *d_table, int n, long long n_ch
         quantize_table_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(d_table, n, n_chunks, B, bitdepth);
     else
         quantize_table_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(d_table, n, n_chunks, B, bitdepth);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -360,6 +360,7 @@ cudaError_t launch_typed(const ScanParams &p, int threads, const ScanRoi *table,
         ih_scan_table_kernel<T, E, NP><<<(unsigned)tiles, threads, 0, s>>>(p, table, n_roi);
     else
         ih_scan_kernel<T, E, NP><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, 0, s>>>(p);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -236,6 +236,7 @@ cudaError_t launch_kind(const GatherParams &p, int kind, cudaStream_t s)
         }
     default: return cudaErrorInvalidValue;
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -172,6 +172,7 @@ cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_byt
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t n = (int64_t)p.ncx * p.ncy;
     const long long blocks = std::min<long long>((n * p.n_targets + 255) / 256, (long long)std::max(1, sms) * 8);
+    count_launches(1);
     gather_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(p.partial, p.map, p.nbg, p.n_targets, n,
                                                           p.n_targets > 1 ? p.map_stride : 0);
     return cudaGetLastError();

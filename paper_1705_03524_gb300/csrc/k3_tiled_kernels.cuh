@@ -590,6 +590,7 @@ cudaError_t run_op(TiledOp &op)
         const int h = 2 * p.ry + 1;
         const dim3 grid((unsigned)((p.ncx + TX - 1) / TX), (unsigned)(h * p.nblk * p.nbg));
         fn<<<grid, TX + 32, op.sh->smem, op.s>>>(p);
+        count_launches(1);
         return cudaGetLastError();
     }
     case TiledOp::kTable: {
@@ -597,6 +598,7 @@ cudaError_t run_op(TiledOp &op)
         cudaError_t e = set_smem(fn, op.sh->smem);
         if (e != cudaSuccess) return e;
         fn<<<(unsigned)op.n_items, TX + 32, op.sh->smem, op.s>>>(op.d_jobs, op.d_items, op.n_jobs);
+        count_launches(1);
         return cudaGetLastError();
     }
     }

@@ -2,6 +2,7 @@
 // argument validation, kernel parameters and launches. No compute happens
 // here; every step of the pipeline runs in the CUDA kernels K1-K3.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -456,6 +457,10 @@ swih_status plan_layout(const swih_plan_desc *d, PlanLayout *out)
 
 void set_thread_error(const char *msg) { g_err = msg; }
 
+std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 }  // namespace swih
 
 extern "C" {
@@ -646,6 +651,13 @@ swih_status swih_destroy(swih_plan_t pl)
     if (pl->d_mem) e = cudaFree(pl->d_mem);
     delete pl;
     if (e != cudaSuccess) return cuda_fail(nullptr, "cudaFree", e);
+    return SWIH_OK;
+}
+
+swih_status swih_launch_count(uint64_t *count)
+{
+    if (!count) return fail(nullptr, SWIH_ERR_INVALID_ARG, "count is NULL");
+    *count = g_launches.load(std::memory_order_relaxed);
     return SWIH_OK;
 }
 

@@ -133,6 +133,9 @@ struct GatherParams {
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
+// kernels this library has enqueued in the process (host count, for reporting)
+void count_launches(unsigned n);
+
 // Tiled gather; returns cudaErrorNotSupported when a window's row segments do
 // not fit in shared memory (the caller then uses launch_gather).
 constexpr int kTiledChainMax = 8;

@@ -227,6 +227,8 @@ def _load() -> ctypes.CDLL:
     lib.swih_debug_inject.restype = S
     lib.swih_plan_get_info.argtypes = [P, ctypes.POINTER(swih_plan_info)]
     lib.swih_plan_get_info.restype = S
+    lib.swih_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.swih_launch_count.restype = S
     BD, RD = ctypes.POINTER(swih_batch_desc), ctypes.POINTER(swih_roi_desc)
     lib.swih_batch_workspace_bytes.argtypes = [BD, RD, I, ctypes.POINTER(ctypes.c_uint64)]
     lib.swih_batch_workspace_bytes.restype = S
@@ -387,6 +389,12 @@ SWIH_INJECT_DIRECT_GATHER = 2
 
 def swih_debug_inject(plan: int, what: int) -> None:
     _check(LIB.swih_debug_inject(plan, int(what)), plan)
+
+
+def swih_launch_count() -> int:
+    out = ctypes.c_uint64(0)
+    _check(LIB.swih_launch_count(ctypes.byref(out)))
+    return int(out.value)
 
 
 def swih_plan_get_info(plan: int) -> swih_plan_info:

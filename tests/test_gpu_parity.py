@@ -359,3 +359,17 @@ def test_wedding_cake_and_plain_are_approximations_swih_is_exact():
     for k in ("plain", "wedding2", "wedding4", "wedding8"):
         assert errs[k][0] > 100 * TOL, k
     assert errs["wedding8"][1] < errs["plain"][1]
+
+
+def test_launch_counter_counts_enqueued_kernels():
+    img = synth.uniform_image(64, 80, 8, seed=5)
+    c0 = S.swih_launch_count()
+    plan, _buf = make_plan(img, 8, 8, ("manhattan",), (9, 9))  # one build: quantise + scan
+    with plan:
+        c1 = S.swih_launch_count()
+        m = torch.empty((56, 72), device=DEV)
+        plan.likelihood("manhattan", 9, 9, torch.full((8,), 0.125, device=DEV), m)
+        plan.sync_status()
+        c2 = S.swih_launch_count()
+    assert c1 - c0 == 2
+    assert c2 - c1 in (1, 2)  # the gather, plus the reduction when the bins were split
