@@ -110,6 +110,15 @@ __device__ __forceinline__ void store_row(T *dst, const T (&v)[E])
     }
 }
 
+// dst[0..E) = src[0..E) (16-byte accesses; src is a row this thread stored)
+template <typename T, int E>
+__device__ __forceinline__ void copy_row(T *dst, const T *src)
+{
+    constexpr int n = E * (int)sizeof(T) / 16;
+#pragma unroll
+    for (int c = 0; c < n; ++c) reinterpret_cast<uint4 *>(dst)[c] = reinterpret_cast<const uint4 *>(src)[c];
+}
+
 template <typename T, int E>
 __device__ __forceinline__ void store_state(T *dst, const T (&v)[E])
 {
@@ -260,6 +269,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     uint8_t vnext[E];
     if (has_cols && y_begin < y_end) load_bins<E>(r.bins + (int64_t)y_begin * r.bins_pitch, x0, vnext);
     for (int y = y_begin; y < y_end; ++y) {
+        bool any = false;  // a pixel of bin b in this thread's columns of row y
         if (has_cols) {
             uint8_t v[E];
 #pragma unroll
@@ -268,7 +278,25 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             const T yq = ring_pow<T>((T)y, q);
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
+                if (v[e] == bb && x0 + e < r.W) {
+                    cs[e] += yq;
+                    any = true;
+                }
+        }
+        // A row without bin b leaves every column sum, hence every term's row,
+        // as in row y-1: copy the row this thread wrote last instead of scanning.
+        // The band's first row is always computed (the row above it belongs to
+        // another tile, which publishes only its column sums).
+        if (!__syncthreads_or(any) && y > y_begin) {
+            if (in_pitch) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    if (k >= n_p) break;
+                    T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane + (int64_t)y * r.ih_pitch;
+                    copy_row<T, E>(row + x0, row - r.ih_pitch + x0);
+                }
+            }
+            continue;
         }
         T cur[E];
 #pragma unroll

@@ -373,3 +373,23 @@ def test_launch_counter_counts_enqueued_kernels():
         c2 = S.swih_launch_count()
     assert c1 - c0 == 2
     assert c2 - c1 in (1, 2)  # the gather, plus the reduction when the bins were split
+
+
+@pytest.mark.parametrize("pattern", ["stripes", "blobs"])
+def test_integral_histograms_with_rows_missing_bins(pattern):
+    """Rows that hold no pixel of a bin are copied from the row above by the
+    scan instead of scanned; check every plane bit for bit where that happens
+    often (horizontal stripes of one value, a smooth scene), across several
+    bands (the first row of a band is always computed)."""
+    if pattern == "stripes":
+        rng = np.random.default_rng(3)
+        vals = rng.integers(0, 256, size=67).astype(np.uint8)
+        img = np.repeat(vals[:, None], 90, axis=1)
+        img[::5, ::7] = 255 - img[::5, ::7]  # a few pixels of other bins
+    else:
+        img = synth.blob_scene(70, 140, 8, seed=4, n_blobs=3, margin=20).image
+    plan, _buf = make_plan(img, 8, 8, ("manhattan", "euclidean", "gaussian"), (9, 9), band_rows=6)
+    with plan:
+        check_ih(plan, img, 8, 8)
+        bins = oracle_bins(img, 8, 8)
+        check_windows(plan, bins, 8, "gaussian", 9, 7)
