@@ -110,15 +110,6 @@ __device__ __forceinline__ void store_row(T *dst, const T (&v)[E])
     }
 }
 
-// dst[0..E) = src[0..E) (16-byte accesses; src is a row this thread stored)
-template <typename T, int E>
-__device__ __forceinline__ void copy_row(T *dst, const T *src)
-{
-    constexpr int n = E * (int)sizeof(T) / 16;
-#pragma unroll
-    for (int c = 0; c < n; ++c) reinterpret_cast<uint4 *>(dst)[c] = reinterpret_cast<const uint4 *>(src)[c];
-}
-
 template <typename T, int E>
 __device__ __forceinline__ void store_state(T *dst, const T (&v)[E])
 {
@@ -163,6 +154,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
 {
     __shared__ int s_flag;
     __shared__ T s_warp[2][32];
+    __shared__ unsigned long long s_rows;  // band rows (first 64) holding a pixel of bin b
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -178,20 +170,29 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     const uint8_t bb = (uint8_t)b;
     if (ticket == p.stall_tile && band == 0) return;  // injected stall: publish nothing
 
-    // ---- 1. band aggregate of [bin == b] * y^q per column
+    // ---- 1. band aggregate of [bin == b] * y^q per column, and which rows hold the bin
+    if (tid == 0) s_rows = 0ull;
     T agg[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) agg[e] = 0;
+    unsigned long long my_rows = 0ull;
     if (has_cols) {
         for (int y = y_begin; y < y_end; ++y) {
             const T yq = ring_pow<T>((T)y, q);
             uint8_t v[E];
             load_bins<E>(r.bins + (int64_t)y * r.bins_pitch, x0, v);
+            bool any = false;
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (v[e] == bb && x0 + e < r.W) agg[e] += yq;
+                if (v[e] == bb && x0 + e < r.W) {
+                    agg[e] += yq;
+                    any = true;
+                }
+            if (any && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
         }
     }
+    __syncthreads();  // s_rows cleared
+    if (my_rows) atomicOr(&s_rows, my_rows);
 
     const int64_t state_row = ((int64_t)chain * r.n_bands + band) * r.ih_pitch;
     int *my_flag = r.flags + (int64_t)chain * r.n_bands + band;
@@ -268,8 +269,13 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     int parity = 0;
     uint8_t vnext[E];
     if (has_cols && y_begin < y_end) load_bins<E>(r.bins + (int64_t)y_begin * r.bins_pitch, x0, vnext);
+    // Rows without a pixel of bin b leave every column sum, hence every term's
+    // row, as in the row above: they are not scanned; each computed row is also
+    // stored into the empty rows that follow it (from registers). The band's
+    // first row is always computed; rows past the first 64 count as holding b.
+    const unsigned long long rows = s_rows;  // read after the barrier of step 1's publication
+    auto holds = [&](int y) { return y - y_begin >= 64 || ((rows >> (y - y_begin)) & 1ull); };
     for (int y = y_begin; y < y_end; ++y) {
-        bool any = false;  // a pixel of bin b in this thread's columns of row y
         if (has_cols) {
             uint8_t v[E];
 #pragma unroll
@@ -278,26 +284,11 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             const T yq = ring_pow<T>((T)y, q);
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (v[e] == bb && x0 + e < r.W) {
-                    cs[e] += yq;
-                    any = true;
-                }
+                if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
         }
-        // A row without bin b leaves every column sum, hence every term's row,
-        // as in row y-1: copy the row this thread wrote last instead of scanning.
-        // The band's first row is always computed (the row above it belongs to
-        // another tile, which publishes only its column sums).
-        if (!__syncthreads_or(any) && y > y_begin) {
-            if (in_pitch) {
-#pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    if (k >= n_p) break;
-                    T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane + (int64_t)y * r.ih_pitch;
-                    copy_row<T, E>(row + x0, row - r.ih_pitch + x0);
-                }
-            }
-            continue;
-        }
+        if (y > y_begin && !holds(y)) continue;  // stored with the last computed row
+        int run = 1;  // this row and the empty rows after it
+        while (y + run < y_end && !holds(y + run)) ++run;
         T cur[E];
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -324,7 +315,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             if (in_pitch) {
                 T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane +
                          (int64_t)y * r.ih_pitch;
-                store_row<T, E>(row + x0, val);
+                for (int i = 0; i < run; ++i) store_row<T, E>(row + (int64_t)i * r.ih_pitch + x0, val);
             }
             parity ^= 1;
         }

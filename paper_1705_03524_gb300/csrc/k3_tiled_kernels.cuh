@@ -227,7 +227,9 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     xc = min(xc, p.cx0 + p.ncx - 1);
     const int yc0 = p.cy0 + phase + slot0 * h;
     const int S = kMan ? 2 * K + 1 : K + 1;  // lattice rows
-    const int steps = (bb1 - bb0) * S * G;
+    // bin blocks this CTA walks: [bb0, bb1), less those without a pixel in the
+    // union of its windows (see below); the list sits just below the carry area
+    int *s_list = reinterpret_cast<int *>(sm + p.dtop_off) - (p.B + 1);
     const int NS = p.nstage;
 
     // row segment [xs-rx-1, xs+TX+rx) of every plane, copied from a 16-byte boundary
@@ -259,7 +261,37 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     if (xlo < 0) {  // column -1 of the integral histogram is 0; copies never land there
         for (int i = tid; i < NS * p.nl; i += TX + 32) stages[(size_t)i * p.seg + (A - 1)] = T(0);
     }
+    // A bin with no pixel anywhere in the union of this CTA's windows adds 0 to
+    // every window's likelihood: its planes are neither copied nor differenced.
+    // Its pixel count over that rectangle is 4 reads of the count plane (x^0
+    // y^0), exact in the ring. Histogram output needs every bin, so then all
+    // bins are kept.
+    const bool sparse = p.hist == nullptr;
+    if (sparse) {
+        const int xa = xs - p.rx - 1;                             // exclusive
+        const int xb = min(xs + TX, p.cx0 + p.ncx) - 1 + p.rx;    // inclusive
+        const int ya = yc0 - p.ry - 1;
+        const int yb = yc0 + (K - 1) * h + p.ry;
+        for (int b = tid; b < p.B; b += TX + 32) {
+            const T *pl = reinterpret_cast<const T *>(p.ih) + ((int64_t)p.t1 * p.B + b) * p.plane;
+            auto at = [&](int x, int y) -> T { return (x >= 0 && y >= 0) ? __ldg(pl + (int64_t)y * p.pitch + x) : T(0); };
+            s_list[b] = (at(xb, yb) - at(xa, yb) - at(xb, ya) + at(xa, ya)) != T(0);
+        }
+    }
     __syncthreads();
+    if (tid == 0) {  // compact in place: flags are read ahead of where block indices are written
+        int n = 0;
+        for (int bb = bb0; bb < bb1; ++bb) {
+            bool any = !sparse;
+            for (int j = 0; j < BB && !any; ++j)
+                if (bb * BB + j < p.B) any = s_list[bb * BB + j] != 0;
+            if (any) s_list[n++] = bb;
+        }
+        s_list[p.B] = n;
+    }
+    __syncthreads();
+    const int nlist = s_list[p.B];
+    const int steps = nlist * S * G;
 
     auto row_of = [&](int s) -> int {
         if constexpr (kMan) {
@@ -273,7 +305,8 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     // consumers have released that stage's previous step
     if (producer) {
         if (lane != 0) return;
-        int g = 0, s = 0, bb = bb0;
+        int g = 0, s = 0, li = 0;
+        int bb = nlist > 0 ? s_list[0] : 0;
         for (int m = 0; m < steps; ++m) {
             const int st_i = m % NS;
             if (m >= NS && !mbar_wait(&empty[st_i], (uint32_t)(((m / NS) - 1) & 1))) {
@@ -311,7 +344,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                 g = 0;
                 if (++s == S) {
                     s = 0;
-                    ++bb;
+                    if (++li < nlist) bb = s_list[li];
                 }
             }
         }
@@ -351,7 +384,8 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     int n = 0;          // step index
     int cs = 0;         // consumer stage
     uint32_t cpar = 0;  // its parity
-    for (int bb = bb0; bb < bb1 && !stop; ++bb) {
+    for (int li = 0; li < nlist && !stop; ++li) {
+        const int bb = s_list[li];
         const int b0 = bb * BB;
         const int nb = min(BB, p.B - b0);
         for (int s = 0; s < S && !stop; ++s) {
