@@ -92,6 +92,38 @@ __device__ __forceinline__ void load_bins(const uint8_t *row, int x0, uint8_t (&
     }
 }
 
+// dst[0..E) = src[0..E) (16-byte accesses; src is a row this thread stored)
+template <typename T, int E>
+__device__ __forceinline__ void copy_row(T *dst, const T *src)
+{
+    constexpr int n = E * (int)sizeof(T) / 16;
+#pragma unroll
+    for (int c = 0; c < n; ++c) reinterpret_cast<uint4 *>(dst)[c] = reinterpret_cast<const uint4 *>(src)[c];
+}
+
+// E bins back into a byte row (the shared-memory copy of the band's bins)
+template <int E>
+__device__ __forceinline__ void put_bins(uint8_t *row, int x0, const uint8_t (&v)[E])
+{
+    if constexpr (E == 4) {
+        uint32_t u = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) u |= (uint32_t)v[i] << (8 * i);
+        *reinterpret_cast<uint32_t *>(row + x0) = u;
+    } else {
+#pragma unroll
+        for (int c = 0; c < E / 8; ++c) {
+            uint2 u = make_uint2(0u, 0u);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                u.x |= (uint32_t)v[8 * c + i] << (8 * i);
+                u.y |= (uint32_t)v[8 * c + 4 + i] << (8 * i);
+            }
+            reinterpret_cast<uint2 *>(row + x0)[c] = u;
+        }
+    }
+}
+
 // store E consecutive ring elements (16-byte aligned) with 16-byte vector stores
 template <typename T, int E>
 __device__ __forceinline__ void store_row(T *dst, const T (&v)[E])
@@ -148,13 +180,15 @@ __device__ __forceinline__ void add_state(const T *src, T (&acc)[E])
 }
 
 // One (chain, band) tile of one image region r; ticket = its ticket number.
-template <typename T, int E, int NP>
+template <typename T, int E, int NP, bool RUNS>
 __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r, const int ticket,
                                           const int band, const int chain)
 {
     __shared__ int s_flag;
     __shared__ T s_warp[2][32];
     __shared__ unsigned long long s_rows;  // band rows (first 64) holding a pixel of bin b
+    extern __shared__ __align__(16) uint8_t s_band_bins[];  // the band's bins when p.sb_rows > 0
+    const int row_bytes = (int)blockDim.x * E;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -181,6 +215,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             const T yq = ring_pow<T>((T)y, q);
             uint8_t v[E];
             load_bins<E>(r.bins + (int64_t)y * r.bins_pitch, x0, v);
+            if (p.sb_rows > 0) put_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
             bool any = false;
 #pragma unroll
             for (int e = 0; e < E; ++e)
@@ -188,7 +223,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
                     agg[e] += yq;
                     any = true;
                 }
-            if (any && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
+            if ((NP <= 3 || RUNS) && any && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
         }
     }
     __syncthreads();  // s_rows cleared
@@ -268,27 +303,53 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     for (int e = 0; e < E; ++e) cs[e] = carry[e];
     int parity = 0;
     uint8_t vnext[E];
-    if (has_cols && y_begin < y_end) load_bins<E>(r.bins + (int64_t)y_begin * r.bins_pitch, x0, vnext);
+    const bool cached = p.sb_rows > 0;  // each thread reads back the bins it stored in step 1
+    if (!cached && has_cols && y_begin < y_end) load_bins<E>(r.bins + (int64_t)y_begin * r.bins_pitch, x0, vnext);
     // Rows without a pixel of bin b leave every column sum, hence every term's
-    // row, as in the row above: they are not scanned; each computed row is also
-    // stored into the empty rows that follow it (from registers). The band's
-    // first row is always computed; rows past the first 64 count as holding b.
+    // row, as in the row above. With up to 3 terms per chain such a row is
+    // copied from the row this thread stored last (still in L2) instead of
+    // scanned. With the Gaussian's 5 terms of 8 bytes the copies' latency costs
+    // more than the scans they save: with RUNS (the table kernel of many
+    // regions, where it measured faster) each computed row is stored again into
+    // the empty rows after it, from registers; otherwise every row is scanned. The band's first row is
+    // always computed; rows past the first 64 count as holding b.
+    constexpr bool kSkip = NP <= 3;
     const unsigned long long rows = s_rows;  // read after the barrier of step 1's publication
-    auto holds = [&](int y) { return y - y_begin >= 64 || ((rows >> (y - y_begin)) & 1ull); };
     for (int y = y_begin; y < y_end; ++y) {
         if (has_cols) {
             uint8_t v[E];
+            if (cached) {
+                load_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
+            } else {
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = vnext[e];
-            if (y + 1 < y_end) load_bins<E>(r.bins + (int64_t)(y + 1) * r.bins_pitch, x0, vnext);
+                for (int e = 0; e < E; ++e) v[e] = vnext[e];
+                if (y + 1 < y_end) load_bins<E>(r.bins + (int64_t)(y + 1) * r.bins_pitch, x0, vnext);
+            }
             const T yq = ring_pow<T>((T)y, q);
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
         }
-        if (y > y_begin && !holds(y)) continue;  // stored with the last computed row
-        int run = 1;  // this row and the empty rows after it
-        while (y + run < y_end && !holds(y + run)) ++run;
+        if constexpr (kSkip) {
+            const bool holds = y - y_begin >= 64 || ((rows >> (y - y_begin)) & 1ull);
+            if (y > y_begin && !holds) {
+                if (in_pitch) {
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        if (k >= n_p) break;
+                        T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane + (int64_t)y * r.ih_pitch;
+                        copy_row<T, E>(row + x0, row - r.ih_pitch + x0);
+                    }
+                }
+                continue;
+            }
+        }
+        int run = 1;  // this row and the empty rows stored with it
+        if constexpr (!kSkip && RUNS) {
+            auto holds = [&](int yy) { return yy - y_begin >= 64 || ((rows >> (yy - y_begin)) & 1ull); };
+            if (y > y_begin && !holds(y)) continue;
+            while (y + run < y_end && !holds(y + run)) ++run;
+        }
         T cur[E];
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -315,7 +376,11 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             if (in_pitch) {
                 T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane +
                          (int64_t)y * r.ih_pitch;
-                for (int i = 0; i < run; ++i) store_row<T, E>(row + (int64_t)i * r.ih_pitch + x0, val);
+                if constexpr (!kSkip && RUNS) {
+                    for (int i = 0; i < run; ++i) store_row<T, E>(row + (int64_t)i * r.ih_pitch + x0, val);
+                } else {
+                    store_row<T, E>(row + x0, val);
+                }
             }
             parity ^= 1;
         }
@@ -344,7 +409,7 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_c
     r.W = p.W;
     r.n_bands = p.n_bands;
     r.ticket0 = 0;
-    scan_tile<T, E, NP>(p, r, ticket, band, ticket - band * n_chains);
+    scan_tile<T, E, NP, false>(p, r, ticket, band, ticket - band * n_chains);
 }
 
 // Several image regions in one launch: region i owns the tickets
@@ -368,17 +433,36 @@ __global__ void __launch_bounds__(kMaxScanThreads)
     const int local = ticket - r.ticket0;
     const int n_chains = p.B * p.n_q;
     const int band = local / n_chains;
-    scan_tile<T, E, NP>(p, r, ticket, band, local - band * n_chains);
+    scan_tile<T, E, NP, true>(p, r, ticket, band, local - band * n_chains);
+}
+
+template <typename KernelFn>
+cudaError_t allow_smem(KernelFn fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T, int E, int NP>
-cudaError_t launch_typed(const ScanParams &p, int threads, const ScanRoi *table, int n_roi, long long tiles,
+cudaError_t launch_typed(const ScanParams &p_in, int threads, const ScanRoi *table, int n_roi, long long tiles,
                          cudaStream_t s)
 {
-    if (table)
-        ih_scan_table_kernel<T, E, NP><<<(unsigned)tiles, threads, 0, s>>>(p, table, n_roi);
-    else
-        ih_scan_kernel<T, E, NP><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, 0, s>>>(p);
+    // the band's bins stay in shared memory between the aggregate pass and the
+    // sweep when the band is at most 64 rows and the copy at most 96 KB
+    ScanParams p = p_in;
+    const size_t per_row = (size_t)threads * E;
+    p.sb_rows = (p.band_rows <= 64 && (size_t)p.band_rows * per_row <= 96 * 1024) ? p.band_rows : 0;
+    const size_t smem = (size_t)p.sb_rows * per_row;
+    cudaError_t e;
+    if (table) {
+        e = allow_smem(ih_scan_table_kernel<T, E, NP>, smem);
+        if (e != cudaSuccess) return e;
+        ih_scan_table_kernel<T, E, NP><<<(unsigned)tiles, threads, smem, s>>>(p, table, n_roi);
+    } else {
+        e = allow_smem(ih_scan_kernel<T, E, NP>, smem);
+        if (e != cudaSuccess) return e;
+        ih_scan_kernel<T, E, NP><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, smem, s>>>(p);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

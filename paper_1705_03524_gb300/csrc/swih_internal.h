@@ -68,6 +68,7 @@ struct ScanParams {
     int p_val[kMaxQ][kMaxP];
     int term[kMaxQ][kMaxP];
     long long spin_limit;
+    int sb_rows;            // band rows whose bins the tile keeps in shared memory (set by the launcher)
     int stall_tile;      // ticket of a tile that never publishes (fault injection), else -1
 };
 // E = columns per thread, threads = ceil(W/E) rounded to a warp multiple
