@@ -230,6 +230,8 @@ def run_swih(args, rank, world, local_rank):
     clocks.start()
     clocks.wait_first()
     wall0 = time.time()
+    for pl in plans:
+        pl.load_bytes(reset=True)  # integral-histogram bytes the gathers request, counted by the kernels
     launches0 = S.swih_launch_count()
     t_start.record(stream)
     for s in range(args.steps):
@@ -244,6 +246,7 @@ def run_swih(args, rank, world, local_rank):
     ms = t_start.elapsed_time(t_end)
     for pl in plans:
         pl.sync_status(stream)
+    loaded_g = plan_g.load_bytes() if plan_g else 0
 
     # per-launch durations inside the timed region
     seg = {"build_me": [], "build_g": []}
@@ -280,7 +283,17 @@ def run_swih(args, rank, world, local_rank):
     dom = max(totals, key=totals.get)
     dom_keys = classes[dom]
     dom_keys = [k for k in dom_keys if k in seg_ms]
-    dom_bytes = float(np.mean([algo[k] for k in dom_keys]))
+    dense_bytes = float(np.mean([algo[k] for k in dom_keys]))
+    dom_bytes = dense_bytes
+    basis = "dense: every integral-histogram element the kernel's terms use, once, plus the map"
+    if dom == "gather Gaussian" and loaded_g:
+        # the gather skips bins and rows absent from its windows: its algorithmic
+        # bytes are the row segments it must load (counted by the kernel) + the map
+        n_g = args.steps * sum(1 for k in jobs if k[0] == "gaussian")
+        maps_b = float(np.mean([4 * (H - w + 1) * (W - w + 1) for w in WINDOWS]))
+        dom_bytes = loaded_g / n_g + maps_b
+        basis = ("integral-histogram row segments the sparse gather loads (rows of windows holding "
+                 "each bin, counted by the kernel over the timed launches) + the map")
     dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
     peak, peak_kind = read_peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -358,6 +371,7 @@ def run_swih(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
+                     "bytes_basis": basis, "dense_bytes_per_launch": dense_bytes,
                      "avg_launch_ms": dom_ms},
         "per_launch_ms": seg_ms,
         "clocks": clk,

@@ -189,6 +189,13 @@ swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
  * piece of work took. */
 swih_status swih_launch_count(uint64_t *count);
 
+/* Bytes of integral histogram the plan's tiled gathers have requested from
+ * device memory since the last reset (each CTA adds the row segments it
+ * copied: rows of windows that hold a bin, for bins present in its windows).
+ * Synchronous; reset = 1 zeroes the count. For reporting how much data the
+ * gathers actually move. */
+swih_status swih_plan_load_bytes(swih_plan_t plan, uint64_t *bytes, int reset);
+
 /* ---------------------------------------------------------------- batches
  * Many regions of interest (ROIs) of one frame, each with its own size,
  * kernel, windows (scales) and target histogram, processed by a fixed set of

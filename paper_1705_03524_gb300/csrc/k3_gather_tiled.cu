@@ -60,8 +60,8 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         sh.kchain_max = gau ? KMAX : KMAX / 2;
         sh.n_targets = std::max(1, std::min(n_targets, kMaxTargets));
         // shared memory: barriers | sqrt(targets) | likelihood sums | bin-block list | [Gaussian carry] | stages
-        // (+ the CTA's list of bin blocks and its length: B + 1 ints)
-        sh.dtop_off = (16 * kMaxStages + 4 * sh.n_targets * B + 4 * sh.n_targets * sh.kchain_max * tx + 4 * (B + 1) +
+        // (+ the CTA's list of bin blocks and of their rows to load: 2 x (B + 1) ints)
+        sh.dtop_off = (16 * kMaxStages + 4 * sh.n_targets * B + 4 * sh.n_targets * sh.kchain_max * tx + 8 * (B + 1) +
                        15) / 16 * 16;
         const int carry = gau ? (2 * gdx + 1) * (2 * gdy + 1) * tx * 8 : 0;
         sh.stage_off = (sh.dtop_off + carry + 127) / 128 * 128;

@@ -229,7 +229,8 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     const int S = kMan ? 2 * K + 1 : K + 1;  // lattice rows
     // bin blocks this CTA walks: [bb0, bb1), less those without a pixel in the
     // union of its windows (see below); the list sits just below the carry area
-    int *s_list = reinterpret_cast<int *>(sm + p.dtop_off) - (p.B + 1);
+    int *s_list = reinterpret_cast<int *>(sm + p.dtop_off) - 2 * (p.B + 1);
+    int *s_rows = s_list + (p.B + 1);  // per listed bin block: the lattice rows to load (bit s)
     const int NS = p.nstage;
 
     // row segment [xs-rx-1, xs+TX+rx) of every plane, copied from a 16-byte boundary
@@ -261,37 +262,54 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     if (xlo < 0) {  // column -1 of the integral histogram is 0; copies never land there
         for (int i = tid; i < NS * p.nl; i += TX + 32) stages[(size_t)i * p.seg + (A - 1)] = T(0);
     }
-    // A bin with no pixel anywhere in the union of this CTA's windows adds 0 to
-    // every window's likelihood: its planes are neither copied nor differenced.
-    // Its pixel count over that rectangle is 4 reads of the count plane (x^0
-    // y^0), exact in the ring. Histogram output needs every bin, so then all
-    // bins are kept.
+    // A window with no pixel of bin b has every moment of b zero, so the
+    // integral histograms' differences at its bottom lattice row equal those at
+    // its top: the row after such a window need not be copied, and a bin absent
+    // from all the CTA's windows needs no row at all. Per bin, the pixel count
+    // of window k over the tile's columns is c(bottom_k) - c(top_k), with
+    // c(y) = I(y, xb) - I(y, xa) on the count plane (x^0 y^0), exact in the
+    // ring: 2 reads per lattice row. The rows to load are those of the present
+    // windows (Manhattan: top, centre and bottom rows). Histogram output needs
+    // every bin and row, so then all are loaded.
     const bool sparse = p.hist == nullptr;
+    const int all_rows = (int)((1u << S) - 1u);
     if (sparse) {
-        const int xa = xs - p.rx - 1;                             // exclusive
-        const int xb = min(xs + TX, p.cx0 + p.ncx) - 1 + p.rx;    // inclusive
-        const int ya = yc0 - p.ry - 1;
-        const int yb = yc0 + (K - 1) * h + p.ry;
+        const int xa = xs - p.rx - 1;                           // exclusive
+        const int xb = min(xs + TX, p.cx0 + p.ncx) - 1 + p.rx;  // inclusive
         for (int b = tid; b < p.B; b += TX + 32) {
             const T *pl = reinterpret_cast<const T *>(p.ih) + ((int64_t)p.t1 * p.B + b) * p.plane;
             auto at = [&](int x, int y) -> T { return (x >= 0 && y >= 0) ? __ldg(pl + (int64_t)y * p.pitch + x) : T(0); };
-            s_list[b] = (at(xb, yb) - at(xa, yb) - at(xb, ya) + at(xa, ya)) != T(0);
+            auto span = [&](int y) -> T { return at(xb, y) - at(xa, y); };
+            unsigned rows_b = 0u;
+            T prev = span(yc0 - p.ry - 1);
+            for (int k = 0; k < K; ++k) {
+                const T next = span(yc0 + k * h + p.ry);
+                if (next != prev) rows_b |= kMan ? (7u << (2 * k)) : (3u << k);
+                prev = next;
+            }
+            s_list[b] = (int)rows_b;
         }
     }
     __syncthreads();
-    if (tid == 0) {  // compact in place: flags are read ahead of where block indices are written
-        int n = 0;
+    if (tid == 0) {  // compact in place: per-bin masks are read ahead of where block entries are written
+        int n = 0, total = 0;
         for (int bb = bb0; bb < bb1; ++bb) {
-            bool any = !sparse;
-            for (int j = 0; j < BB && !any; ++j)
-                if (bb * BB + j < p.B) any = s_list[bb * BB + j] != 0;
-            if (any) s_list[n++] = bb;
+            unsigned m = sparse ? 0u : (unsigned)all_rows;
+            for (int j = 0; j < BB && sparse; ++j)
+                if (bb * BB + j < p.B) m |= (unsigned)s_list[bb * BB + j];
+            if (m) {
+                s_list[n] = bb;
+                s_rows[n] = (int)m;
+                ++n;
+                total += __popc(m);
+            }
         }
         s_list[p.B] = n;
+        s_rows[p.B] = total;
     }
     __syncthreads();
     const int nlist = s_list[p.B];
-    const int steps = nlist * S * G;
+    const int steps = s_rows[p.B] * G;
 
     auto row_of = [&](int s) -> int {
         if constexpr (kMan) {
@@ -307,6 +325,9 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
         if (lane != 0) return;
         int g = 0, s = 0, li = 0;
         int bb = nlist > 0 ? s_list[0] : 0;
+        unsigned rmask = nlist > 0 ? (unsigned)s_rows[0] : 0u;
+        while (s < S && !((rmask >> s) & 1u)) ++s;  // the first row to load
+        unsigned long long loaded = 0;  // bytes of integral histogram requested
         for (int m = 0; m < steps; ++m) {
             const int st_i = m % NS;
             if (m >= NS && !mbar_wait(&empty[st_i], (uint32_t)(((m / NS) - 1) & 1))) {
@@ -332,6 +353,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                 const int nb = min(BB, p.B - b0);
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(br, (uint32_t)(nb * nt) * seg_bytes);
+                loaded += (unsigned long long)(nb * nt) * seg_bytes;
                 T *dst = stages + (size_t)st_i * stage_elems + land;
                 const T *row = reinterpret_cast<const T *>(p.ih) + (int64_t)Y * p.pitch + x_begin;
                 for (int j = 0; j < nb; ++j)
@@ -342,12 +364,18 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
             }
             if (++g == G) {
                 g = 0;
-                if (++s == S) {
+                do {
+                    ++s;
+                } while (s < S && !((rmask >> s) & 1u));
+                if (s == S && ++li < nlist) {
+                    bb = s_list[li];
+                    rmask = (unsigned)s_rows[li];
                     s = 0;
-                    if (++li < nlist) bb = s_list[li];
+                    while (s < S && !((rmask >> s) & 1u)) ++s;
                 }
             }
         }
+        if (p.load_bytes) atomicAdd(p.load_bytes, loaded);
         return;
     }
 
@@ -386,9 +414,12 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     uint32_t cpar = 0;  // its parity
     for (int li = 0; li < nlist && !stop; ++li) {
         const int bb = s_list[li];
+        const unsigned rmask = (unsigned)s_rows[li];
+        bool first = true;  // the first row loaded for this bin completes no window
         const int b0 = bb * BB;
         const int nb = min(BB, p.B - b0);
         for (int s = 0; s < S && !stop; ++s) {
+            if (!((rmask >> s) & 1u)) continue;  // after an absent window: same values as the carried ones
             const bool zero_row = row_of(s) < 0;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -408,7 +439,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                     }
                     // a bin with no pixel in the window has every moment zero: its
                     // translation is skipped (the pixel count is the x^0 y^0 plane)
-                    if (g == 0) occupied = s > 0 && R[0] != 0;
+                    if (g == 0) occupied = !first && R[0] != 0;
                     if (occupied) {
                         u64 ex[3] = {0, 0, 0};
                         axis_bernstein<DX>(R, (uint32_t)xc, (uint32_t)p.rx2, p.rx4, ex);
@@ -418,7 +449,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                 } else {
                     // the window completed by this lattice row (if any); its
                     // likelihood terms for the step's bins are summed in a register
-                    const int done_k = kMan ? ((s & 1) || s == 0 ? -1 : (s >> 1) - 1) : s - 1;
+                    const int done_k = first ? -1 : (kMan ? ((s & 1) ? -1 : (s >> 1) - 1) : s - 1);
                     float step_acc = 0.f;
 #pragma unroll
                     for (int j = 0; j < BB; ++j) {
@@ -522,7 +553,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
             }
             if (stop) break;
             if constexpr (kGau) {
-                if (s > 0) {  // the window above this lattice row is complete
+                if (!first) {  // the window above this lattice row is complete
                     const int k = s - 1;
                     const uint32_t yc = (uint32_t)(yc0 + k * h);
                     float acc = 0.f;
@@ -545,6 +576,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                     }
                 }
             }
+            first = false;
         }
     }
     if (stop) {

@@ -335,6 +335,7 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
     g.target_stride = pl->desc.bins;
     g.map_stride = 0;
     g.nbg = 1;
+    g.load_bytes = reinterpret_cast<unsigned long long *>(pl->d_status + 2);  // 8-byte aligned word of the status block
     g.partial = pl->partial_floats ? reinterpret_cast<float *>(pl->d_mem + pl->off_partial) : nullptr;
     g.partial_cap = (int64_t)pl->partial_floats;
     g.want_tx = pl->cfg_tx[kernel];
@@ -651,6 +652,16 @@ swih_status swih_destroy(swih_plan_t pl)
     if (pl->d_mem) e = cudaFree(pl->d_mem);
     delete pl;
     if (e != cudaSuccess) return cuda_fail(nullptr, "cudaFree", e);
+    return SWIH_OK;
+}
+
+swih_status swih_plan_load_bytes(swih_plan_t pl, uint64_t *bytes, int reset)
+{
+    if (!pl || !bytes) return fail(pl, SWIH_ERR_INVALID_ARG, "plan and bytes are required");
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(pl->d_status + 2);
+    cudaError_t e = cudaMemcpy(bytes, d, sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(d, 0, sizeof(uint64_t));
+    if (e != cudaSuccess) return cuda_fail(pl, "cudaMemcpy(load bytes)", e);
     return SWIH_OK;
 }
 

@@ -131,6 +131,7 @@ struct GatherParams {
     int nbg;                // bin groups: CTAs that split a chain's bins (1: one CTA, writes the map)
     float *partial;         // nbg > 1: per-group likelihoods [nbg][n_targets][ncy][ncx], then summed
     int64_t partial_cap;    // floats available at partial (0: no splitting)
+    unsigned long long *load_bytes;  // optional: integral-histogram bytes the tiled gather requested (added)
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 

@@ -214,6 +214,7 @@ swih_status WorkSet::build_jobs(std::string &err)
         g.map = jb.map;
         g.hist = nullptr;
         g.nbg = 1;  // table launches span many waves already; no split-gather scratch here
+        g.load_bytes = nullptr;
         g.partial = nullptr;
         g.partial_cap = 0;
         g.n_targets = jb.n_targets;

@@ -228,6 +228,8 @@ def _load() -> ctypes.CDLL:
     lib.swih_plan_get_info.argtypes = [P, ctypes.POINTER(swih_plan_info)]
     lib.swih_plan_get_info.restype = S
     lib.swih_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.swih_plan_load_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), I]
+    lib.swih_plan_load_bytes.restype = S
     lib.swih_launch_count.restype = S
     BD, RD = ctypes.POINTER(swih_batch_desc), ctypes.POINTER(swih_roi_desc)
     lib.swih_batch_workspace_bytes.argtypes = [BD, RD, I, ctypes.POINTER(ctypes.c_uint64)]
@@ -391,6 +393,12 @@ def swih_debug_inject(plan: int, what: int) -> None:
     _check(LIB.swih_debug_inject(plan, int(what)), plan)
 
 
+def swih_plan_load_bytes(plan: int, reset: bool = False) -> int:
+    out = ctypes.c_uint64(0)
+    _check(LIB.swih_plan_load_bytes(plan, ctypes.byref(out), 1 if reset else 0), plan)
+    return int(out.value)
+
+
 def swih_launch_count() -> int:
     out = ctypes.c_uint64(0)
     _check(LIB.swih_launch_count(ctypes.byref(out)))
@@ -426,6 +434,9 @@ class Plan:
 
     def info(self) -> swih_plan_info:
         return swih_plan_get_info(self.handle)
+
+    def load_bytes(self, reset=False) -> int:
+        return swih_plan_load_bytes(self.handle, reset)
 
     def close(self):
         if self.handle:

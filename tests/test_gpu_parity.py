@@ -375,16 +375,17 @@ def test_launch_counter_counts_enqueued_kernels():
     assert c2 - c1 in (1, 2)  # the gather, plus the reduction when the bins were split
 
 
-@pytest.mark.parametrize("pattern", ["stripes", "blobs"])
+@pytest.mark.parametrize("pattern", ["stripes", "blobs", "wide_stripes"])
 def test_integral_histograms_with_rows_missing_bins(pattern):
     """Rows that hold no pixel of a bin are copied from the row above by the
     scan instead of scanned; check every plane bit for bit where that happens
     often (horizontal stripes of one value, a smooth scene), across several
     bands (the first row of a band is always computed)."""
-    if pattern == "stripes":
+    if pattern in ("stripes", "wide_stripes"):
         rng = np.random.default_rng(3)
-        vals = rng.integers(0, 256, size=67).astype(np.uint8)
-        img = np.repeat(vals[:, None], 90, axis=1)
+        h, w = (67, 90) if pattern == "stripes" else (40, 4200)  # 4200 columns: 16 per scan thread
+        vals = rng.integers(0, 256, size=h).astype(np.uint8)
+        img = np.repeat(vals[:, None], w, axis=1)
         img[::5, ::7] = 255 - img[::5, ::7]  # a few pixels of other bins
     else:
         img = synth.blob_scene(70, 140, 8, seed=4, n_blobs=3, margin=20).image
@@ -393,3 +394,22 @@ def test_integral_histograms_with_rows_missing_bins(pattern):
         check_ih(plan, img, 8, 8)
         bins = oracle_bins(img, 8, 8)
         check_windows(plan, bins, 8, "gaussian", 9, 7)
+
+
+def test_gather_counts_the_bytes_it_loads():
+    """The tiled gather reports the integral-histogram bytes it requested: on
+    uniform noise (every bin in every window) at least the dense bytes of its
+    planes (it also loads the window halo of each column tile), on a
+    constant image (one bin) far less."""
+    H, W, B, w = 200, 300, 16, 21
+    dense = 5 * B * H * 320 * 4  # Euclidean: 5 planes of 32-bit elements, rows padded to 320
+    for img, lo, hi in [(synth.uniform_image(H, W, 8, seed=3), 0.9, 3.0),
+                        (np.full((H, W), 77, dtype=np.uint8), 0.0, 0.2)]:
+        plan, _buf = make_plan(img, 8, B, ("euclidean",), (w, w))
+        with plan:
+            plan.load_bytes(reset=True)
+            m = torch.empty((H - w + 1, W - w + 1), device=DEV)
+            plan.likelihood("euclidean", w, w, torch.full((B,), 1.0 / B, device=DEV), m)
+            plan.sync_status()
+            got = plan.load_bytes()
+            assert lo * dense <= got <= hi * dense, (got, dense)
