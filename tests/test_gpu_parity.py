@@ -400,11 +400,12 @@ def test_gather_counts_the_bytes_it_loads():
     """The tiled gather reports the integral-histogram bytes it requested: on
     uniform noise (every bin in every window) at least the dense bytes of its
     planes (it also loads the window halo of each column tile), on a
-    constant image (one bin) far less."""
+    constant image (one bin) far less: the one block of 4 bins that a step
+    carries, a quarter of the 16 bins plus the halo."""
     H, W, B, w = 200, 300, 16, 21
     dense = 5 * B * H * 320 * 4  # Euclidean: 5 planes of 32-bit elements, rows padded to 320
     for img, lo, hi in [(synth.uniform_image(H, W, 8, seed=3), 0.9, 3.0),
-                        (np.full((H, W), 77, dtype=np.uint8), 0.0, 0.2)]:
+                        (np.full((H, W), 77, dtype=np.uint8), 0.0, 0.5)]:
         plan, _buf = make_plan(img, 8, B, ("euclidean",), (w, w))
         with plan:
             plan.load_bytes(reset=True)
