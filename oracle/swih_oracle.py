@@ -23,6 +23,11 @@ paper is silent the reading taken is stated in the docstring:
   total weight, scored by the Bhattacharyya coefficient (the paper leaves
   the similarity unnamed).
 
+The exponential kernel's four directional integral histograms
+(``exp_directional_ih``) are Eq. 2 with the weights exp(+-lam x) exp(+-lam y),
+each summed from the side where its weight is smallest and divided by the
+weight at the point (the paper names the kernel without a decomposition).
+
 Parity unpinned: the Gaussian kernel is a polynomial approximant (the paper
 gives no decomposition of it); its distance from the true Gaussian is
 reported by the tests, not pinned to a value printed in the paper.
@@ -41,7 +46,8 @@ _SRC = os.path.join(_HERE, "brute.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD_DIR, "libswih_oracle.so")
 
-KINDS = ("plain", "manhattan", "euclidean", "gaussian")
+KINDS = ("plain", "manhattan", "euclidean", "gaussian", "exponential")
+EXP_LAMBDA = 0.1  # default decay rate of the exponential kernel, per pixel
 
 
 # --------------------------------------------------------------------------
@@ -197,7 +203,7 @@ def wedding_weights(w: int, h: int, rings: int = 4) -> np.ndarray:
 
 
 def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
-                   sigma_frac: float = 0.25, rings: int = 4) -> np.ndarray:
+                   sigma_frac: float = 0.25, rings: int = 4, lam: float = EXP_LAMBDA) -> np.ndarray:
     """Weight table K[dy + ry, dx + rx] (float64, h x w) of one window.
 
     * plain: K = 1 (Porikli's unweighted local histogram).
@@ -215,6 +221,10 @@ def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
       sigma = sigma_frac * (window length along that axis).
     * wedding: the wedding-cake approximation of the Manhattan kernel with
       ``rings`` nested windows (wedding_weights).
+    * exponential: K = exp(-lam (|dx| + |dy|)), the exponential weighting of
+      the city-block distance (Sec. 2 and Fig. 1 name an exponential kernel
+      without a formula). lam is a decay rate per pixel, the same for every
+      window size, so one set of integral histograms serves every scale.
     """
     if w < 3 or h < 3 or w % 2 == 0 or h % 2 == 0:
         raise ValueError("window sides must be odd and >= 3")
@@ -229,6 +239,10 @@ def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
         return (rx * rx - dx * dx) + (ry * ry - dy * dy)
     if kind == "wedding":
         return wedding_weights(w, h, rings)
+    if kind == "exponential":
+        if not lam > 0.0:
+            raise ValueError("the exponential kernel needs a positive decay rate")
+        return np.exp(-lam * (np.abs(dx) + np.abs(dy)))
     if kind == "gaussian":
         gx = gauss_axis(rx, sigma_frac * w, degree)[None, :]
         gy = gauss_axis(ry, sigma_frac * h, degree)[:, None]
@@ -237,6 +251,38 @@ def kernel_weights(kind: str, w: int, h: int, degree: int = 2,
             raise ValueError("Gaussian approximant is negative inside the window")
         return K
     raise ValueError(f"unknown kernel {kind!r}")
+
+
+def exp_directional_ih(bins: np.ndarray, b: int, lam: float) -> np.ndarray:
+    """The four directional integral histograms of the exponential kernel,
+    float64 [4, H, W], direction d = (x side) + 2 (y side):
+
+        J_d(x, y) = sum over x' on the x side, y' on the y side of
+                    [Q(f(x', y')) = b] * exp(-lam (|x - x'| + |y - y'|)),
+
+    x side 0: x' <= x, 1: x' >= x; y side 0: y' <= y, 1: y' >= y. J_0 is
+    Eq. 2 with the weight w(i, j) = exp(lam (i + j)), divided by w(x, y);
+    the other three are the same for the weights exp(-+lam i) exp(-+lam j)
+    with the sums taken from the opposite side (Sec. 2.1: one weighted IH
+    per quadrant, each rising towards the centre). Dividing by the weight at
+    (x, y) keeps the values below 1 / (1 - exp(-lam))^2 on any image size.
+    Written as two triangular matrix products (a library matmul per axis).
+    """
+    H, W = bins.shape
+    c = (bins == b).astype(np.float64)
+
+    def tri(n, side):
+        i = np.arange(n)
+        d = i[:, None] - i[None, :]  # row index minus column index
+        if side == 0:
+            return np.where(d >= 0, np.exp(-lam * np.maximum(d, 0)), 0.0)
+        return np.where(d <= 0, np.exp(-lam * np.maximum(-d, 0)), 0.0)
+
+    out = np.empty((4, H, W), dtype=np.float64)
+    for d in range(4):
+        tx, ty = tri(W, d & 1), tri(H, d >> 1)
+        out[d] = ty @ c @ tx.T
+    return out
 
 
 def true_gaussian(w: int, h: int, sigma_frac: float = 0.25) -> np.ndarray:

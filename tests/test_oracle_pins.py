@@ -398,3 +398,102 @@ def test_wedding_cake_with_one_ring_is_the_plain_histogram():
     hw = O.normalise(O.hist_at(bins, 6, Kw, cx, cy))
     hp = O.normalise(O.hist_at(bins, 6, Kp, cx, cy))
     assert np.abs(hw - hp).max() <= 1e-14
+
+
+# ----------------------------------------------------------------------------
+# the exponential kernel
+# ----------------------------------------------------------------------------
+def geometric_axis_mass(r, lam):
+    """sum_{d=-r..r} exp(-lam |d|) = (1 + q - 2 q^(r+1)) / (1 - q), q = exp(-lam)
+    (two geometric series and the centre)."""
+    import math
+    q = math.exp(-lam)
+    return (1.0 + q - 2.0 * q ** (r + 1)) / (1.0 - q)
+
+
+@pytest.mark.parametrize("w,h,lam", [(3, 3, 0.1), (21, 9, 0.5), (41, 81, 0.02), (7, 5, 3.0)])
+def test_exponential_mass_is_closed_form_everywhere(w, h, lam):
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    M = geometric_axis_mass(rx, lam) * geometric_axis_mass(ry, lam)
+    K = O.kernel_weights("exponential", w, h, lam=lam)
+    assert abs(K.sum() - M) <= 1e-12 * M
+    rng = np.random.default_rng(w * 100 + h)
+    bins = rng.integers(0, 4, size=(h + 6, w + 5)).astype(np.uint8)
+    x0, y0, nx, ny = O.valid_centres(h + 6, w + 5, w, h)
+    U = O.hist_rect(bins, 4, K, x0, y0, nx, ny)
+    np.testing.assert_allclose(U.sum(-1), M, rtol=1e-12)
+
+
+def test_exponential_small_rate_is_the_plain_histogram():
+    rng = np.random.default_rng(31)
+    bins = rng.integers(0, 5, size=(24, 30)).astype(np.uint8)
+    x0, y0, nx, ny = O.valid_centres(24, 30, 9, 7)
+    U = O.hist_rect(bins, 5, O.kernel_weights("exponential", 9, 7, lam=1e-10), x0, y0, nx, ny)
+    C = O.hist_rect(bins, 5, O.kernel_weights("plain", 9, 7), x0, y0, nx, ny)
+    np.testing.assert_allclose(U, C, rtol=1e-8, atol=1e-8)
+
+
+def test_exp_directional_ih_by_brute_force():
+    import math
+    rng = np.random.default_rng(5)
+    bins = rng.integers(0, 2, size=(4, 6)).astype(np.uint8)
+    lam = 0.7
+    J = O.exp_directional_ih(bins, 1, lam)
+    for d in range(4):
+        sx, sy = d & 1, d >> 1
+        for y in range(4):
+            for x in range(6):
+                tot = 0.0
+                for yy in range(4):
+                    for xx in range(6):
+                        on_x = xx <= x if sx == 0 else xx >= x
+                        on_y = yy <= y if sy == 0 else yy >= y
+                        if on_x and on_y and bins[yy, xx] == 1:
+                            tot += math.exp(-lam * (abs(x - xx) + abs(y - yy)))
+                assert abs(J[d, y, x] - tot) <= 1e-12 * max(1.0, tot), (d, x, y)
+
+
+def exp_quadrant_sums(J, lam, w, h, xc, yc):
+    """U(b) of the exponential kernel at (xc, yc) from the four directional IHs
+    J[d] of bin b: each quadrant's sum is a corner difference of its own
+    direction's table, with the decay across the window supplied by powers of
+    q = exp(-lam); the centre row and column belong to the top-left quadrant,
+    the others start one pixel further out (factors q). Reads outside the image
+    are zero."""
+    import math
+    q = math.exp(-lam)
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    Hh, Ww = J.shape[1:]
+
+    def at(d, x, y):
+        return J[d, y, x] if (0 <= x < Ww and 0 <= y < Hh) else 0.0
+
+    xl, xr, yu, yd = xc - rx - 1, xc + rx + 1, yc - ry - 1, yc + ry + 1
+
+    def quad(d, xa, xf, ya, yf, fx, fy):
+        # xa/ya: the corner next to the centre; xf/yf: one past the far edge
+        return at(d, xa, ya) - fx * at(d, xf, ya) - fy * at(d, xa, yf) + fx * fy * at(d, xf, yf)
+
+    tl = quad(0, xc, xl, yc, yu, q ** (rx + 1), q ** (ry + 1))
+    tr = q * quad(1, xc + 1, xr, yc, yu, q ** rx, q ** (ry + 1))
+    bl = q * quad(2, xc, xl, yc + 1, yd, q ** (rx + 1), q ** ry)
+    br = q * q * quad(3, xc + 1, xr, yc + 1, yd, q ** rx, q ** ry)
+    return tl + tr + bl + br
+
+
+@pytest.mark.parametrize("lam", [0.05, 0.3, 1.5])
+def test_exponential_quadrant_decomposition_matches_brute_force(lam):
+    rng = np.random.default_rng(int(lam * 100))
+    H, W, B = 20, 23, 3
+    bins = rng.integers(0, B, size=(H, W)).astype(np.uint8)
+    J = [O.exp_directional_ih(bins, b, lam) for b in range(B)]
+    for (w, h) in [(3, 3), (5, 9), (11, 7), (23, 19), (21, 3)]:
+        K = O.kernel_weights("exponential", w, h, lam=lam)
+        x0, y0, nx, ny = O.valid_centres(H, W, w, h)
+        # every valid centre: includes windows touching each image border
+        cx, cy = np.meshgrid(np.arange(x0, x0 + nx), np.arange(y0, y0 + ny))
+        cx, cy = cx.ravel(), cy.ravel()
+        ref = O.hist_at(bins, B, K, cx, cy)
+        got = np.array([[exp_quadrant_sums(J[b], lam, w, h, x, y) for b in range(B)]
+                        for x, y in zip(cx, cy)])
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11)
