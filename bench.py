@@ -528,6 +528,71 @@ def run_large_frame(args, dev, budget_gb=100):
     }
 
 
+# ----------------------------------------------------------------------------- exponential kernel
+def run_exponential(args, dev, lam=0.1, steps=50):
+    """The exponential kernel exp(-lambda (|dx| + |dy|)), lambda = 0.1 per pixel,
+    on the benchmark frame (1024x1024 u8, B = 32) at windows 21/41/81. One step =
+    quantise + the plain integral histogram (the count gate) + the four
+    directional tables + the 3 likelihood maps, timed with CUDA events; the
+    tables (1.2 GB) exceed L2."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    cfg = synth.config2()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    tx, ty = cfg["target_centre"]
+    d_img = torch.from_numpy(img).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    desc = S.make_desc(H, W, bins=B, kernels=("exponential",), max_win=(81, 81), exp_lambda=lam)
+    maps = {w: torch.empty((H - w + 1, W - w + 1), device=dev) for w in WINDOWS}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 + len(WINDOWS))]
+    with S.Plan(desc) as p:
+        p.build_ih(d_img, stream)
+        tgt = torch.empty((1, 1, B), device=dev)  # set-up: the target is the window at the object
+        p.local_hist("exponential", 41, 41, tx, ty, 1, 1, tgt, stream)
+        q = tgt.reshape(B)
+        for _ in range(3):
+            p.build_ih(d_img, stream)
+            for w in WINDOWS:
+                p.likelihood("exponential", w, w, q, maps[w], stream)
+        t_build, t_map = 0.0, {w: 0.0 for w in WINDOWS}
+        for _ in range(steps):
+            ev[0].record(stream)
+            p.build_ih(d_img, stream)
+            ev[1].record(stream)
+            for i, w in enumerate(WINDOWS):
+                p.likelihood("exponential", w, w, q, maps[w], stream)
+                ev[2 + i].record(stream)
+            torch.cuda.synchronize()
+            t_build += ev[0].elapsed_time(ev[1])
+            prev = ev[1]
+            for i, w in enumerate(WINDOWS):
+                t_map[w] += prev.elapsed_time(ev[2 + i])
+                prev = ev[2 + i]
+        p.sync_status(stream)
+        info = p.info()
+    build = t_build / steps
+    gathers = {w: t / steps for w, t in t_map.items()}
+    step_ms = build + sum(gathers.values())
+    n_win = sum(m.numel() for m in maps.values())
+    pitch = info.ih_pitch
+    written = 4 * B * H * pitch * 8 + B * H * pitch * info.elem_bytes  # tables + count plane
+    peak = read_peaks()[0]
+    return {
+        "workload": ("1024x1024 u8 benchmark frame, B=32, exponential kernel exp(-0.1 (|dx|+|dy|)) "
+                     "x windows 21/41/81, full valid maps"),
+        "windows_per_step": n_win, "ms_per_step": step_ms, "windows_per_s": n_win / (step_ms * 1e-3),
+        "build_ms": build, "gather_ms": {str(w): v for w, v in gathers.items()},
+        "build_bytes_written": written, "build_gbs": written / (build * 1e-3) / 1e9,
+        "build_frac_of_copy_peak": written / (build * 1e-3) / 1e9 / peak,
+        "steps": steps,
+    }
+
+
 # ----------------------------------------------------------------------------- serving
 def run_serving(args, dev, n_queries=400, rate=2000.0):
     """A Poisson stream of tracking queries against 16 resident 2048x2048
@@ -645,7 +710,7 @@ def run_fig6(args):
         img = sc.image
         d_img = torch.from_numpy(img).to(dev)
         bins = O.quantize(img, 8, B)
-        for kind in ("manhattan", "euclidean", "gaussian"):
+        for kind in ("manhattan", "euclidean", "gaussian", "exponential"):
             wins = [w for w in (11, 21, 41, 61, 81, 121, 161, 201, 301, 401) if w < min(H, W)]
             if kind == "gaussian":
                 wins = [w for w in wins if w <= 121]  # exact 64-bit moments: w h rx^4 ry^4 < 2^64
@@ -813,6 +878,7 @@ def main():
         line["batched_regions"] = run_regions(args, dev)
         line["serving"] = run_serving(args, dev, n_queries=args.serve_queries)
         line["large_frame"] = run_large_frame(args, dev)
+        line["exponential"] = run_exponential(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(args.cpu_seconds)
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -70,13 +70,25 @@ typedef enum swih_pixel_type { SWIH_PIXEL_U8 = 0, SWIH_PIXEL_U16 = 1 } swih_pixe
  *              ring between nested windows i-1 and i weighs the mean of the
  *              Manhattan kernel over that ring's pixels. Computed from plain
  *              (unweighted) integral histograms only; n = wedding_rings.
- *              The paper names the scheme without ring sizes or weights.    */
+ *              The paper names the scheme without ring sizes or weights.
+ *   EXPONENTIAL K = exp(-lambda (|dx| + |dy|)), lambda = exp_lambda per pixel
+ *              (the paper names an exponential kernel without a formula).
+ *              The same lambda serves every window size. Built from four
+ *              directional weighted integral histograms (weights exp(+-lambda
+ *              x) exp(+-lambda y), one per quadrant, each summed from the side
+ *              where its weight is smallest and divided by the weight at the
+ *              point), kept in unsigned 64-bit fixed point (see
+ *              swih_plan_info.exp_frac_bits). A bin's window count comes from
+ *              the exact plain integral histogram, so bins absent from a
+ *              window give exactly 0; the others carry a rounding error below
+ *              2^-28 of the window's total weight.                          */
 typedef enum swih_kernel {
     SWIH_KERNEL_PLAIN = 0,
     SWIH_KERNEL_MANHATTAN = 1,
     SWIH_KERNEL_EUCLIDEAN = 2,
     SWIH_KERNEL_GAUSSIAN = 3,
-    SWIH_KERNEL_WEDDING = 4
+    SWIH_KERNEL_WEDDING = 4,
+    SWIH_KERNEL_EXPONENTIAL = 5
 } swih_kernel;
 
 #define SWIH_KERNEL_BIT(k) (1u << (unsigned)(k))
@@ -113,6 +125,7 @@ typedef struct swih_plan_desc {
     int32_t band_rows;         /* rows per scan band (0: automatic) */
     uint64_t hbm_budget_bytes; /* reject plans whose workspace exceeds it (0: no limit) */
     int32_t wedding_rings;     /* nested windows of the WEDDING kernel, 1..16 (0: 4) */
+    double exp_lambda;         /* decay per pixel of the EXPONENTIAL kernel, 2^-10..16 (0: 0.1) */
 } swih_plan_desc;
 
 typedef struct swih_plan_s *swih_plan_t;
@@ -179,6 +192,14 @@ typedef struct swih_plan_info {
     int32_t band_rows;       /* rows per scan band */
     int32_t n_bands;
     uint64_t workspace_bytes;
+    /* EXPONENTIAL kernel (NULL / 0 when the plan does not serve it): the four
+     * directional integral histograms J_d, d = (x side) + 2 (y side), side 0 =
+     * sums over x' <= x (y' <= y), side 1 = over x' >= x (y' >= y), of
+     * [bin = b] exp(-lambda (|x - x'| + |y - y'|)); uint64 plane (d, b) starts
+     * at element (d*B + b) * plane_elems, rows of ih_pitch elements; the value
+     * is element / 2^exp_frac_bits (rounded down at each step of the scan). */
+    const void *d_exp;
+    int32_t exp_frac_bits;
 } swih_plan_info;
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
@@ -292,7 +313,8 @@ swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, 
  * static device array of 8 MiB (8388608 bytes) inside the library, which
  * every GPU that loads the library holds until the process exits. Inputs
  * whose scratch (bins + look-back state, reported nowhere else) exceeds it
- * are rejected with SWIH_ERR_UNSUPPORTED and a message giving the size; when
+ * are rejected with SWIH_ERR_UNSUPPORTED and a message giving the size, and so
+ * is a desc naming the EXPONENTIAL kernel (its tables are not built here); when
  * desc->band_rows is 0 the band height is raised until the state fits.
  *
  * Arguments:

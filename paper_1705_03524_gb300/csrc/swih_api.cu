@@ -156,8 +156,8 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "pitch_bytes of a U16 image must be even");
     if (d->bins < 1 || d->bins > 256)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "bins must be in [1, 256]");
-    if (d->kernel_mask == 0 || (d->kernel_mask & ~0x1Fu))
-        return fail(nullptr, SWIH_ERR_INVALID_ARG, "kernel_mask must name kernels 0..4");
+    if (d->kernel_mask == 0 || (d->kernel_mask & ~0x3Fu))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "kernel_mask must name kernels 0..5");
     if (d->wedding_rings < 0 || d->wedding_rings > kMaxRings)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "wedding_rings must be in [0, 16]");
     if (!odd_window(d->max_win_w) || !odd_window(d->max_win_h))
@@ -172,10 +172,27 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     const double sf = d->gauss_sigma_frac == 0.0 ? 0.25 : d->gauss_sigma_frac;
     if (!(sf > 0.0) || !std::isfinite(sf))
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "gauss_sigma_frac must be positive");
+    const bool want_exp = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_EXPONENTIAL);
+    const double lam = d->exp_lambda == 0.0 ? 0.1 : d->exp_lambda;
+    if (want_exp && !(lam >= 1.0 / 1024.0 && lam <= 16.0))
+        return fail(nullptr, SWIH_ERR_INVALID_ARG, "exp_lambda must be in [2^-10, 16]");
 
     pl->desc = *d;
     pl->gauss_degree = D;
     pl->sigma_frac = sf;
+    pl->has_exp = want_exp;
+    pl->exp_lambda = lam;
+    if (want_exp) {
+        // J_d < 1 / (1 - q)^2 and every window sum < 4 / (1 - q)^2: with
+        // F = 60 - ceil(log2(1 / (1 - q)^2)) fraction bits all stay below 2^62
+        const long double q = expl(-(long double)lam);
+        const long double jmax = 1.0L / ((1.0L - q) * (1.0L - q));
+        pl->exp_F = 60 - (int)ceill(log2l(jmax));
+        // 8 columns per scan thread (16 above 4096 columns): the block-wide scan's
+        // per-thread steps are spread over more pixels than the integer scan's 4
+        pl->exp_E = d->width > 4096 ? 16 : 8;
+        pl->exp_threads = (int)round_up((d->width + pl->exp_E - 1) / pl->exp_E, 32);
+    }
     bool mark[5][5] = {};
     const bool want_man = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_MANHATTAN);
     const bool want_euc = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_EUCLIDEAN);
@@ -219,8 +236,8 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     for (int k = SWIH_KERNEL_PLAIN; k <= SWIH_KERNEL_EUCLIDEAN; ++k)
         if (d->kernel_mask & SWIH_KERNEL_BIT(k))
             need = std::max(need, int_kernel_mass(k, d->max_win_w, d->max_win_h));
-    if (d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_WEDDING))  // rectangle counts
-        need = std::max(need, int_kernel_mass(SWIH_KERNEL_PLAIN, d->max_win_w, d->max_win_h));
+    if (d->kernel_mask & (SWIH_KERNEL_BIT(SWIH_KERNEL_WEDDING) | SWIH_KERNEL_BIT(SWIH_KERNEL_EXPONENTIAL)))
+        need = std::max(need, int_kernel_mass(SWIH_KERNEL_PLAIN, d->max_win_w, d->max_win_h));  // window counts
     const bool fits32 = !want_gau && need < 4294967296.0L;
     if (want_gau && gauss_bound(d->max_win_w, d->max_win_h, D) >= 18446744073709551616.0L)
         return fail(nullptr, SWIH_ERR_UNSUPPORTED,
@@ -260,6 +277,10 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     // largest map, at most 64 MB
     pl->partial_floats = std::min<uint64_t>((uint64_t)8 * H * W, (64ull << 20) / sizeof(float));
     pl->off_partial = take(pl->partial_floats * sizeof(float));
+    if (want_exp) {
+        pl->off_exp = take((uint64_t)4 * d->bins * pl->plane * sizeof(unsigned long long));
+        pl->off_exp_carry = take((uint64_t)2 * d->bins * pl->n_bands * pl->ih_pitch * sizeof(unsigned long long));
+    }
     take(sizeof(uint32_t) * 64);  // status word
     pl->total = off;
     if (d->hbm_budget_bytes && pl->total > d->hbm_budget_bytes) {
@@ -273,7 +294,7 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
 
 swih_status check_window(swih_plan_s *pl, int kernel, int w, int h)
 {
-    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_WEDDING)
+    if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_EXPONENTIAL)
         return fail(pl, SWIH_ERR_INVALID_ARG, "unknown kernel");
     if (!(pl->desc.kernel_mask & SWIH_KERNEL_BIT(kernel)))
         return fail(pl, SWIH_ERR_INVALID_ARG, "kernel not in the plan's kernel_mask");
@@ -407,6 +428,51 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
         g.nl = std::max(g.n_load_even, g.n_load_odd);
     }
     return SWIH_OK;
+}
+
+unsigned long long exp_pow_fixed(long double lambda, long double n)
+{
+    const long double v = ldexpl(expl(-lambda * n), 64);
+    if (v >= 18446744073709551615.0L) return ~0ull;
+    if (!(v >= 1.0L)) return 0ull;
+    return (unsigned long long)v;  // truncation: floor of a positive value
+}
+
+// Exponential-kernel gather over a rectangle of centres (likelihood map and/or
+// histograms). The window's total weight is M = Sx Sy with
+// S = sum_{d=-r..r} q^|d| = 1 + 2 q (1 - q^r) / (1 - q).
+cudaError_t run_exp_gather(swih_plan_s *pl, int w, int h, int cx0, int cy0, int ncx, int ncy,
+                           const float *target, float *map, float *hist, cudaStream_t s)
+{
+    ExpGatherParams g;
+    std::memset(&g, 0, sizeof g);
+    const int B = pl->desc.bins;
+    g.count = pl->d_mem + pl->off_ih + (uint64_t)pl->term_index[0][0] * B * pl->plane * pl->elem_bytes;
+    g.J = reinterpret_cast<const unsigned long long *>(pl->d_mem + pl->off_exp);
+    g.pitch = pl->ih_pitch;
+    g.plane = pl->plane;
+    g.B = B;
+    g.H = pl->desc.height;
+    g.W = pl->desc.width;
+    g.rx = (w - 1) / 2;
+    g.ry = (h - 1) / 2;
+    g.cx0 = cx0;
+    g.cy0 = cy0;
+    g.ncx = ncx;
+    g.ncy = ncy;
+    g.target = target;
+    g.map = map;
+    g.hist = hist;
+    const long double lam = pl->exp_lambda;
+    g.qx1 = exp_pow_fixed(lam, g.rx + 1);
+    g.qx0 = exp_pow_fixed(lam, g.rx);
+    g.qy1 = exp_pow_fixed(lam, g.ry + 1);
+    g.qy0 = exp_pow_fixed(lam, g.ry);
+    g.q1 = exp_pow_fixed(lam, 1);
+    const long double q = expl(-lam);
+    auto axis = [&](int r) { return 1.0L + 2.0L * q * (1.0L - powl(q, r)) / (1.0L - q); };
+    g.scale = (float)(ldexpl(1.0L, -pl->exp_F) / (axis(g.rx) * axis(g.ry)));
+    return launch_exp_gather(g, pl->elem_bytes, s);
 }
 
 // tiled gather when its row segments fit in shared memory, else the direct one
@@ -575,6 +641,31 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
     }
     e = launch_ih_scan(sp, pl->elem_bytes, pl->scan_E, pl->scan_threads, s);
     if (e != cudaSuccess) return cuda_fail(pl, "ih_scan launch", e);
+    if (pl->has_exp) {
+        ExpScanParams xp;
+        std::memset(&xp, 0, sizeof xp);
+        xp.bins = qp.bins;
+        xp.bins_pitch = pl->bins_pitch;
+        xp.J = reinterpret_cast<unsigned long long *>(pl->d_mem + pl->off_exp);
+        xp.pitch = pl->ih_pitch;
+        xp.plane = pl->plane;
+        xp.carry = reinterpret_cast<unsigned long long *>(pl->d_mem + pl->off_exp_carry);
+        xp.H = d.height;
+        xp.W = d.width;
+        xp.B = d.bins;
+        xp.band_rows = pl->band_rows;
+        xp.n_bands = pl->n_bands;
+        xp.E = pl->exp_E;
+        xp.threads = pl->exp_threads;
+        xp.one = 1ull << pl->exp_F;
+        const long double lam = pl->exp_lambda;
+        xp.q1 = exp_pow_fixed(lam, 1);
+        xp.qband = exp_pow_fixed(lam, pl->band_rows);
+        for (int k = 1; k <= 32; ++k) xp.qe[k] = exp_pow_fixed(lam, (long double)xp.E * k);
+        for (int k = 1; k <= 16; ++k) xp.qw[k] = exp_pow_fixed(lam, 32.0L * xp.E * k);
+        e = launch_exp_scan(xp, s);
+        if (e != cudaSuccess) return cuda_fail(pl, "exponential scan launch", e);
+    }
     pl->built = true;
     return SWIH_OK;
 }
@@ -592,6 +683,12 @@ swih_status swih_local_hist(swih_plan_t pl, int kernel, int win_w, int win_h, in
     if (ncx == 0 || ncy == 0) return SWIH_OK;
     if (cx0 < rx || cy0 < ry || (int64_t)cx0 + ncx > W - rx || (int64_t)cy0 + ncy > H - ry)
         return fail(pl, SWIH_ERR_INVALID_ARG, "centre rectangle has windows outside the image");
+    if (kernel == SWIH_KERNEL_EXPONENTIAL) {
+        const cudaError_t e = run_exp_gather(pl, win_w, win_h, cx0, cy0, ncx, ncy, nullptr, nullptr, d_hist,
+                                             static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(pl, "exponential gather launch", e);
+        return SWIH_OK;
+    }
     GatherParams g;
     int kind = 0;
     st = make_gather(pl, kernel, win_w, win_h, g, kind);
@@ -613,6 +710,13 @@ swih_status swih_likelihood(swih_plan_t pl, int kernel, int win_w, int win_h, co
     swih_status st = check_window(pl, kernel, win_w, win_h);
     if (st != SWIH_OK) return st;
     if (!d_target || !d_map) return fail(pl, SWIH_ERR_INVALID_ARG, "d_target or d_map is NULL");
+    if (kernel == SWIH_KERNEL_EXPONENTIAL) {
+        const cudaError_t e = run_exp_gather(pl, win_w, win_h, (win_w - 1) / 2, (win_h - 1) / 2,
+                                             pl->desc.width - win_w + 1, pl->desc.height - win_h + 1, d_target,
+                                             d_map, nullptr, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(pl, "exponential gather launch", e);
+        return SWIH_OK;
+    }
     GatherParams g;
     int kind = 0;
     st = make_gather(pl, kernel, win_w, win_h, g, kind);
@@ -696,6 +800,8 @@ swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, in
                                    int bins_per_step)
 {
     if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    if (kernel == SWIH_KERNEL_EXPONENTIAL)
+        return fail(pl, SWIH_ERR_UNSUPPORTED, "the exponential kernel has no tiled gather to configure");
     if (kernel < SWIH_KERNEL_PLAIN || kernel > SWIH_KERNEL_WEDDING)
         return fail(pl, SWIH_ERR_INVALID_ARG, "unknown kernel");
     if (tile_cols != 0 && tile_cols != 128 && tile_cols != 256)
@@ -731,6 +837,10 @@ swih_status swih_plan_get_info(swih_plan_t pl, swih_plan_info *info)
     info->band_rows = pl->band_rows;
     info->n_bands = pl->n_bands;
     info->workspace_bytes = pl->total;
+    if (pl->has_exp) {
+        info->d_exp = pl->d_mem + pl->off_exp;
+        info->exp_frac_bits = pl->exp_F;
+    }
     return SWIH_OK;
 }
 

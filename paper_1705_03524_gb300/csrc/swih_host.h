@@ -30,6 +30,13 @@ struct swih_plan_s {
     uint64_t off_ih = 0, off_agg = 0, off_incl = 0, off_flags = 0, total = 0;
     uint64_t flags_bytes = 0;
     uint64_t off_partial = 0, partial_floats = 0;  // split-gather scratch
+    // exponential kernel: decay per pixel, fixed-point fraction bits, the four
+    // directional integral histograms and the scan's band carries
+    bool has_exp = false;
+    double exp_lambda = 0.1;
+    int exp_F = 0;
+    int exp_E = 8, exp_threads = 32;  // exponential scan: columns per thread, threads per block
+    uint64_t off_exp = 0, off_exp_carry = 0;
     char *d_mem = nullptr;
     uint32_t *d_status = nullptr;
     int device = 0;
@@ -58,6 +65,8 @@ long double int_kernel_mass(int kernel, int w, int h);
 swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl);
 // gather parameters of one kernel and window over the plan's integral histograms
 swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams &g, int &kind);
+// floor(exp(-lambda n) 2^64): the fixed-point power q^n of the exponential kernel (n >= 1)
+unsigned long long exp_pow_fixed(long double lambda, long double n);
 
 // ---------------------------------------------------------------- work sets
 // Settings shared by every region of a work set.

@@ -91,6 +91,51 @@ struct ScanRoi {
 cudaError_t launch_ih_scan_table(const ScanParams &p, const ScanRoi *d_table, int n_roi, long long tiles,
                                  int elem_bytes, int E, int threads, cudaStream_t s);
 
+// ---------------------------------------------------------------- K2e scan
+// The exponential kernel's four directional integral histograms J_d (Sec. 2.1
+// with the weights exp(+-lambda x) exp(+-lambda y), divided by the weight at
+// the point), in unsigned 64-bit fixed point with `one` = 2^F. A chain is
+// (bin b, y side s): its column-filtered values C(x, y) = [bin = b] one +
+// q C(x, y -+ 1) are shared by both x sides, whose rows are prefix scans of C
+// with the decay q = exp(-lambda). Three launches: band aggregates of C,
+// carries into each band (a sequential pass over the bands per column), and
+// the scan that writes J. q^n is kept as floor(q^n 2^64) and applied as the
+// high half of a 64 x 64-bit product.
+constexpr int kExpMaxE = 16;
+struct ExpScanParams {
+    const uint8_t *bins;
+    int64_t bins_pitch;        // bytes
+    unsigned long long *J;     // planes [d][b][H][pitch], d = x side + 2 y side
+    int64_t pitch, plane;      // elements
+    unsigned long long *carry; // [s][b][band][pitch]: band aggregates, then carries into bands
+    int H, W, B;
+    int band_rows, n_bands;
+    int E, threads;            // columns per scan thread, threads per block
+    unsigned long long one;    // 2^F
+    unsigned long long q1;     // q
+    unsigned long long qband;  // q^band_rows
+    unsigned long long qe[33];  // q^(E d), d = 1..32
+    unsigned long long qw[17];  // q^(32 E d), d = 1..16
+};
+cudaError_t launch_exp_scan(const ExpScanParams &p, cudaStream_t s);
+
+// One exponential-kernel gather: a thread per centre; per bin, the exact
+// window count from the plain integral histogram (ring element type T) gates
+// the 16 corner reads of the four J_d.
+struct ExpGatherParams {
+    const void *count;           // plain IH plane of bin b at count + b * plane (ring elements)
+    const unsigned long long *J; // as ExpScanParams::J
+    int64_t pitch, plane;        // elements (shared by both)
+    int B, H, W, rx, ry;
+    int cx0, cy0, ncx, ncy;
+    const float *target;         // [B] or NULL
+    float *map;                  // [ncy][ncx] or NULL
+    float *hist;                 // [ncy][ncx][B] or NULL
+    unsigned long long qx1, qx0, qy1, qy0, q1;  // q^(rx+1), q^rx, q^(ry+1), q^ry, q
+    float scale;                 // 2^-F / M
+};
+cudaError_t launch_exp_gather(const ExpGatherParams &p, int elem_bytes, cudaStream_t s);
+
 // ---------------------------------------------------------------- K3 gather
 enum GatherKind { kGatherPlain = 0, kGatherManhattan = 1, kGatherEuclidean = 2, kGatherGaussian = 3, kGatherWedding = 4 };
 constexpr int kMaxRings = 16;

@@ -105,6 +105,9 @@ extern "C" swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const v
                                              swih_plan_info *layout, void *stream)
 {
     if (!desc) return fail_na(SWIH_ERR_INVALID_ARG, "desc is NULL");
+    if (desc->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_EXPONENTIAL))
+        return fail_na(SWIH_ERR_UNSUPPORTED, "the allocation-free build serves the integer integral histograms only "
+                                             "(no exponential kernel)");
     swih_plan_desc d = *desc;
     PlanLayout L;
     swih_status st = plan_layout(&d, &L);

@@ -34,6 +34,7 @@ SWIH_KERNEL_MANHATTAN = 1
 SWIH_KERNEL_EUCLIDEAN = 2
 SWIH_KERNEL_GAUSSIAN = 3
 SWIH_KERNEL_WEDDING = 4
+SWIH_KERNEL_EXPONENTIAL = 5
 
 SWIH_PREC_AUTO = 0
 SWIH_PREC_RING32 = 1
@@ -41,7 +42,7 @@ SWIH_PREC_RING64 = 2
 
 KERNELS = {"plain": SWIH_KERNEL_PLAIN, "manhattan": SWIH_KERNEL_MANHATTAN,
            "euclidean": SWIH_KERNEL_EUCLIDEAN, "gaussian": SWIH_KERNEL_GAUSSIAN,
-           "wedding": SWIH_KERNEL_WEDDING}
+           "wedding": SWIH_KERNEL_WEDDING, "exponential": SWIH_KERNEL_EXPONENTIAL}
 
 
 def kernel_bit(k: int) -> int:
@@ -71,6 +72,7 @@ class swih_plan_desc(ctypes.Structure):
         ("band_rows", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_uint64),
         ("wedding_rings", ctypes.c_int32),
+        ("exp_lambda", ctypes.c_double),
     ]
 
 
@@ -91,6 +93,8 @@ class swih_plan_info(ctypes.Structure):
         ("band_rows", ctypes.c_int32),
         ("n_bands", ctypes.c_int32),
         ("workspace_bytes", ctypes.c_uint64),
+        ("d_exp", ctypes.c_void_p),
+        ("exp_frac_bits", ctypes.c_int32),
     ]
 
 
@@ -307,7 +311,7 @@ def _check(status: int, plan=None):
 def make_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8, bitdepth=None,
               bins=16, kernels=("manhattan",), gauss_degree=2, gauss_sigma_frac=0.25,
               max_win=(3, 3), precision=SWIH_PREC_AUTO, band_rows=0, hbm_budget_bytes=0,
-              wedding_rings=0):
+              wedding_rings=0, exp_lambda=0.0):
     pb = 1 if pixel_type == SWIH_PIXEL_U8 else 2
     mask = 0
     for k in kernels:
@@ -326,6 +330,7 @@ def make_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8, bitd
     d.band_rows = int(band_rows)
     d.hbm_budget_bytes = int(hbm_budget_bytes)
     d.wedding_rings = int(wedding_rings)
+    d.exp_lambda = float(exp_lambda)
     return d
 
 

@@ -32,9 +32,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "swih.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(swih_plan_desc), offsetof(swih_plan_desc, gauss_sigma_frac),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(swih_plan_desc), offsetof(swih_plan_desc, gauss_sigma_frac),
          offsetof(swih_plan_desc, hbm_budget_bytes), sizeof(swih_plan_info),
-         offsetof(swih_plan_info, workspace_bytes));
+         offsetof(swih_plan_info, workspace_bytes), offsetof(swih_plan_desc, exp_lambda),
+         offsetof(swih_plan_info, d_exp), offsetof(swih_plan_info, exp_frac_bits));
   return 0;
 }
 '''
@@ -47,7 +48,8 @@ int main(void) {
                                                check=True).stdout.split()]
     assert vals == [ctypes.sizeof(S.swih_plan_desc), S.swih_plan_desc.gauss_sigma_frac.offset,
                     S.swih_plan_desc.hbm_budget_bytes.offset, ctypes.sizeof(S.swih_plan_info),
-                    S.swih_plan_info.workspace_bytes.offset]
+                    S.swih_plan_info.workspace_bytes.offset, S.swih_plan_desc.exp_lambda.offset,
+                    S.swih_plan_info.d_exp.offset, S.swih_plan_info.exp_frac_bits.offset]
 
 
 def _desc(**kw):
@@ -73,6 +75,9 @@ def _desc(**kw):
     (dict(precision=S.SWIH_PREC_RING32, kernels=("gaussian",)), S.SWIH_ERR_UNSUPPORTED),
     (dict(height=1024, width=1024, kernels=("gaussian",), max_win=(255, 255)), S.SWIH_ERR_UNSUPPORTED),
     (dict(hbm_budget_bytes=1000), S.SWIH_ERR_BUDGET),
+    (dict(kernels=("exponential",), exp_lambda=20.0), S.SWIH_ERR_INVALID_ARG),
+    (dict(kernels=("exponential",), exp_lambda=1e-4), S.SWIH_ERR_INVALID_ARG),
+    (dict(kernels=("exponential",), exp_lambda=-0.5), S.SWIH_ERR_INVALID_ARG),
 ])
 def test_plan_validation(kw, status):
     with pytest.raises(S.SwihError) as ei:
@@ -96,6 +101,31 @@ def test_workspace_bytes_layout():
     # width not a multiple of 32: rows are padded to 32 elements
     n3 = S.swih_plan_workspace_bytes(_desc(width=100, max_win=(31, 31)))
     assert n3 >= 3 * 16 * 128 * 128 * 4
+
+
+def test_exponential_workspace_layout():
+    # four directional 8-byte planes per bin, plus band carries for two y sides;
+    # the count gate keeps a plain 32-bit integral histogram (term x^0 y^0)
+    n = S.swih_plan_workspace_bytes(_desc(kernels=("exponential",)))
+    planes = 4 * 16 * 128 * 128 * 8
+    count = 16 * 128 * 128 * 4
+    assert planes + count < n < planes + count + 4 * 1024 * 1024
+    # the exponential kernel alone adds nothing to the integer term set
+    both = S.swih_plan_workspace_bytes(_desc(kernels=("manhattan", "exponential")))
+    man = S.swih_plan_workspace_bytes(_desc())
+    assert both - man >= planes
+
+
+def test_noalloc_build_refuses_the_exponential_kernel():
+    # refused on the host, before any device memory is touched
+    d = _desc(kernels=("exponential",))
+    assert S.LIB.swih_build_ih_noalloc(ctypes.byref(d), None, None, 0, None, None, None) == S.SWIH_ERR_UNSUPPORTED
+    assert "exponential" in S.swih_last_error()
+
+
+def test_exponential_has_no_tiled_gather_config():
+    # host-only: the configuration call is refused before anything touches a plan's memory
+    assert S.LIB.swih_set_gather_config(None, S.SWIH_KERNEL_EXPONENTIAL, 0, 0, 0) == S.SWIH_ERR_INVALID_ARG
 
 
 def test_null_plan_calls_fail_cleanly():
