@@ -593,6 +593,29 @@ def run_exponential(args, dev, lam=0.1, steps=50):
     }
 
 
+def run_exp_profile():
+    """A small exponential-kernel run to capture under ncu: the benchmark frame
+    with B = 8 (268 MB of tables, above L2), two builds and two w = 41 maps."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    img = synth.config2()["image"]
+    H, W = img.shape
+    B = 8
+    d_img = torch.from_numpy(img).to(dev)
+    q = torch.full((B,), 1.0 / B, device=dev)
+    m = torch.empty((H - 40, W - 40), device=dev)
+    with S.Plan(S.make_desc(H, W, bins=B, kernels=("exponential",), max_win=(81, 81), exp_lambda=0.1)) as p:
+        for _ in range(2):
+            p.build_ih(d_img)
+            p.likelihood("exponential", 41, 41, q, m)
+        p.sync_status()
+    print(json.dumps({"exp_profile": "ok", "bins": B}), flush=True)
+
+
 # ----------------------------------------------------------------------------- serving
 def run_serving(args, dev, n_queries=400, rate=2000.0):
     """A Poisson stream of tracking queries against 16 resident 2048x2048
@@ -843,6 +866,8 @@ def main():
     ap.add_argument("--serve-queries", type=int, default=400)
     ap.add_argument("--fig6", action="store_true",
                     help="time per map against window size (SWIH on the GPU vs the brute-force oracle)")
+    ap.add_argument("--exp-profile", action="store_true",
+                    help="small exponential-kernel run for ncu captures: B = 8, two builds and two w = 41 maps")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "swih":
         args.warmup = 3
@@ -852,6 +877,9 @@ def main():
 
     if args.fig6:
         print(json.dumps(run_fig6(args)), flush=True)
+        return
+    if args.exp_profile:
+        run_exp_profile()
         return
 
     if args.impl == "reference":

@@ -367,6 +367,21 @@ def test_gauss_approximant_distance_from_true_gaussian():
         assert err < 0.05, (w, err)
 
 
+@pytest.mark.parametrize("r", [7, 10, 20, 40, 63])
+def test_gauss_fit_residual_falls_with_the_degree(r):
+    # the fits of degree 2, 3, 4 minimise the squared error over nested spaces
+    # of polynomials, so their residuals on the samples cannot grow with the degree
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    sigma = 0.25 * (2 * r + 1)
+    y = np.exp(-d * d / (2 * sigma * sigma))
+    t = d * d / float(r * r)
+    res = []
+    for D in (2, 3, 4):
+        c = O.gauss_fit(r, sigma, D)
+        res.append(float(np.sum((sum(ci * t ** i for i, ci in enumerate(c)) - y) ** 2)))
+    assert res[0] >= res[1] - 1e-15 and res[1] >= res[2] - 1e-15, res
+
+
 # --------------------------------------------------------------------------- wedding cake
 def test_wedding_cake_hand_case():
     """5 x 5 window, 2 nested windows (half-sides 1 and 2). Manhattan weights
