@@ -200,6 +200,15 @@ typedef struct swih_plan_info {
      * is element / 2^exp_frac_bits (rounded down at each step of the scan). */
     const void *d_exp;
     int32_t exp_frac_bits;
+    /* Rows a plan does not store (bands of at most 64 rows, the default 32,
+     * and at most 32767 rows):
+     * a row holding no pixel of bin b equals the row above it in every plane
+     * of b, so the scan neither computes nor writes it. d_row_map (int32
+     * [bins][height]) gives for row y of bin b the row whose stored values
+     * hold it (-1: the row is all zero); row y of plane (t, b) is read at row
+     * d_row_map[b * height + y]. NULL: every row is stored (band_rows > 64,
+     * or more than 32767 rows). */
+    const int32_t *d_row_map;
 } swih_plan_info;
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);

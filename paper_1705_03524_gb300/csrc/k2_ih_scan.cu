@@ -180,7 +180,7 @@ __device__ __forceinline__ void add_state(const T *src, T (&acc)[E])
 }
 
 // One (chain, band) tile of one image region r; ticket = its ticket number.
-template <typename T, int E, int NP, bool RUNS>
+template <typename T, int E, int NP, bool RUNS, bool SPARSE>
 __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r, const int ticket,
                                           const int band, const int chain)
 {
@@ -223,7 +223,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
                     agg[e] += yq;
                     any = true;
                 }
-            if ((NP <= 3 || RUNS) && any && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
+            if ((NP <= 3 || RUNS || SPARSE) && any && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
         }
     }
     __syncthreads();  // s_rows cleared
@@ -237,6 +237,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     if (tid == 0) {
         __threadfence();
         st_release(my_flag, band == 0 ? kFlagInclusive : kFlagAggregate);
+        if (SPARSE && qi == 0) p.occ[(int64_t)b * r.n_bands + band] = s_rows;  // the rows this bin stores
     }
 
     // ---- 2. look back over the bands above for the column carry
@@ -312,8 +313,10 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     // more than the scans they save: with RUNS (the table kernel of many
     // regions, where it measured faster) each computed row is stored again into
     // the empty rows after it, from registers; otherwise every row is scanned. The band's first row is
-    // always computed; rows past the first 64 count as holding b.
-    constexpr bool kSkip = NP <= 3;
+    // always computed; rows past the first 64 count as holding b. With SPARSE
+    // (bands of at most 64 rows) an empty row is neither scanned nor stored:
+    // readers take the last stored row through the plan's row map.
+    constexpr bool kSkip = NP <= 3 && !SPARSE;
     const unsigned long long rows = s_rows;  // read after the barrier of step 1's publication
     for (int y = y_begin; y < y_end; ++y) {
         if (has_cols) {
@@ -330,6 +333,9 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             for (int e = 0; e < E; ++e)
                 if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
         }
+        if constexpr (SPARSE) {
+            if (!((rows >> (y - y_begin)) & 1ull)) continue;  // uniform over the block
+        }
         if constexpr (kSkip) {
             const bool holds = y - y_begin >= 64 || ((rows >> (y - y_begin)) & 1ull);
             if (y > y_begin && !holds) {
@@ -345,7 +351,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             }
         }
         int run = 1;  // this row and the empty rows stored with it
-        if constexpr (!kSkip && RUNS) {
+        if constexpr (!kSkip && !SPARSE && RUNS) {
             auto holds = [&](int yy) { return yy - y_begin >= 64 || ((rows >> (yy - y_begin)) & 1ull); };
             if (y > y_begin && !holds(y)) continue;
             while (y + run < y_end && !holds(y + run)) ++run;
@@ -376,7 +382,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             if (in_pitch) {
                 T *row = (T *)r.ih + ((int64_t)p.term[qi][k] * p.B + b) * r.plane +
                          (int64_t)y * r.ih_pitch;
-                if constexpr (!kSkip && RUNS) {
+                if constexpr (!kSkip && !SPARSE && RUNS) {
                     for (int i = 0; i < run; ++i) store_row<T, E>(row + (int64_t)i * r.ih_pitch + x0, val);
                 } else {
                     store_row<T, E>(row + x0, val);
@@ -387,7 +393,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     }
 }
 
-template <typename T, int E, int NP>
+template <typename T, int E, int NP, bool SPARSE>
 __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_constant__ ScanParams p)
 {
     __shared__ int s_ticket;
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_c
     r.W = p.W;
     r.n_bands = p.n_bands;
     r.ticket0 = 0;
-    scan_tile<T, E, NP, false>(p, r, ticket, band, ticket - band * n_chains);
+    scan_tile<T, E, NP, false, SPARSE>(p, r, ticket, band, ticket - band * n_chains);
 }
 
 // Several image regions in one launch: region i owns the tickets
@@ -433,7 +439,7 @@ __global__ void __launch_bounds__(kMaxScanThreads)
     const int local = ticket - r.ticket0;
     const int n_chains = p.B * p.n_q;
     const int band = local / n_chains;
-    scan_tile<T, E, NP, true>(p, r, ticket, band, local - band * n_chains);
+    scan_tile<T, E, NP, true, false>(p, r, ticket, band, local - band * n_chains);
 }
 
 template <typename KernelFn>
@@ -458,10 +464,15 @@ cudaError_t launch_typed(const ScanParams &p_in, int threads, const ScanRoi *tab
         e = allow_smem(ih_scan_table_kernel<T, E, NP>, smem);
         if (e != cudaSuccess) return e;
         ih_scan_table_kernel<T, E, NP><<<(unsigned)tiles, threads, smem, s>>>(p, table, n_roi);
-    } else {
-        e = allow_smem(ih_scan_kernel<T, E, NP>, smem);
+    } else if (p.occ) {
+        if (p.band_rows > 64) return cudaErrorInvalidValue;  // the occupancy word covers 64 rows
+        e = allow_smem(ih_scan_kernel<T, E, NP, true>, smem);
         if (e != cudaSuccess) return e;
-        ih_scan_kernel<T, E, NP><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, smem, s>>>(p);
+        ih_scan_kernel<T, E, NP, true><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, smem, s>>>(p);
+    } else {
+        e = allow_smem(ih_scan_kernel<T, E, NP, false>, smem);
+        if (e != cudaSuccess) return e;
+        ih_scan_kernel<T, E, NP, false><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, smem, s>>>(p);
     }
     count_launches(1);
     return cudaGetLastError();
@@ -493,7 +504,47 @@ cudaError_t launch_e(const ScanParams &p, int E, int threads, const ScanRoi *tab
     return cudaErrorInvalidValue;
 }
 
+// One warp per bin: the bands' last stored rows, a running maximum across the
+// bands (warp prefix max, 32 bands at a time), then every row's last stored row.
+__global__ void __launch_bounds__(32) row_map_kernel(const unsigned long long *__restrict__ occ,
+                                                     int *__restrict__ row_map, int H, int band_rows, int n_bands)
+{
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x;
+    int carry = -1;  // last stored row of the bands before this group of 32
+    for (int k0 = 0; k0 < n_bands; k0 += 32) {
+        const int k = k0 + lane;
+        const unsigned long long w = k < n_bands ? occ[(int64_t)b * n_bands + k] : 0ull;
+        int last = w ? k * band_rows + 63 - __clzll((long long)w) : -1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, last, d);
+            if (lane >= d) last = max(last, o);
+        }
+        int before = __shfl_up_sync(0xffffffffu, last, 1);
+        before = max(lane == 0 ? -1 : before, carry);
+        if (k < n_bands) {
+            const int y0 = k * band_rows, y1 = min(y0 + band_rows, H);
+            int cur = before;
+            for (int y = y0; y < y1; ++y) {
+                if ((w >> (y - y0)) & 1ull) cur = y;
+                row_map[(int64_t)b * H + y] = cur;
+            }
+        }
+        carry = max(carry, __shfl_sync(0xffffffffu, last, 31));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_row_map(const unsigned long long *occ, int *row_map, int B, int H, int band_rows, int n_bands,
+                           cudaStream_t s)
+{
+    if (band_rows < 1 || band_rows > 64) return cudaErrorInvalidValue;
+    row_map_kernel<<<(unsigned)B, 32, 0, s>>>(occ, row_map, H, band_rows, n_bands);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads, cudaStream_t s)
 {

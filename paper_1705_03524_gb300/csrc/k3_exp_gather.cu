@@ -60,14 +60,20 @@ __global__ void __launch_bounds__(256) exp_gather_kernel(const ExpGatherParams p
         const bool in_l = xl >= 0, in_r = xr < p.W, in_u = yu >= 0, in_d = yd < p.H;
         const int64_t oc = (int64_t)yc * p.pitch, ou = (int64_t)yu * p.pitch;
         const int64_t oc1 = (int64_t)(yc + 1) * p.pitch, od = (int64_t)yd * p.pitch;
-        const int64_t o2 = (int64_t)y2 * p.pitch;
         float acc = 0.f;
         for (int b = 0; b < p.B; ++b) {
             const T *cnt = reinterpret_cast<const T *>(p.count) + (int64_t)b * p.plane;
-            const T c22 = cnt[o2 + x2];
-            const T c02 = in_l ? cnt[o2 + xl] : T(0);
-            const T c20 = in_u ? cnt[ou + x2] : T(0);
-            const T c00 = (in_l && in_u) ? cnt[ou + xl] : T(0);
+            // rows of the count plane without a pixel of the bin are read at the stored row holding them
+            int r2 = y2, ru = yu;
+            if (p.row_map) {
+                r2 = __ldg(p.row_map + (int64_t)b * p.H + y2);
+                ru = in_u ? __ldg(p.row_map + (int64_t)b * p.H + yu) : -1;
+            }
+            const int64_t q2 = (int64_t)r2 * p.pitch, qu = (int64_t)ru * p.pitch;
+            const T c22 = r2 >= 0 ? cnt[q2 + x2] : T(0);
+            const T c02 = (in_l && r2 >= 0) ? cnt[q2 + xl] : T(0);
+            const T c20 = ru >= 0 ? cnt[qu + x2] : T(0);
+            const T c00 = (in_l && ru >= 0) ? cnt[qu + xl] : T(0);
             float h = 0.f;
             if ((T)(c22 - c02 - c20 + c00) != T(0)) {
                 const u64 *J0 = p.J + (int64_t)b * p.plane;

@@ -5,7 +5,9 @@
 // centres of a row, so every integral-histogram read is a coalesced row
 // segment of one (term, bin) plane. Corner lattice of a window:
 //   X0 = xc-rx-1, X1 = xc, X2 = xc+rx,   Y0 = yc-ry-1, Y1 = yc, Y2 = yc+ry
-// (IH at a -1 coordinate is 0). Rectangle sums over half-open lattice cells
+// (IH at a -1 coordinate is 0). Rows of a bin that the scan did not store
+// (no pixel of the bin) are read at the stored row that holds them, through
+// the plan's row map. Rectangle sums over half-open lattice cells
 // give the sums of [bin = b] * x^k y^l over each quadrant / half / window.
 //
 // All integer work happens in the ring T (uint32 or uint64, wrapping):
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
     iy = min(iy, p.ncy - 1);
     const int xc = p.cx0 + ix, yc = p.cy0 + iy;
     const int X0 = xc - p.rx - 1, X1 = xc, X2 = xc + p.rx;
-    const int Y0 = yc - p.ry - 1, Y1 = yc, Y2 = yc + p.ry;
+    const int yT = yc - p.ry - 1, yC = yc, yB = yc + p.ry;  // lattice rows (image)
     const T txc = (T)xc, tyc = (T)yc;
 
     float acc[kMaxTargets];
@@ -118,6 +120,9 @@ __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
     for (int t = 0; t < kMaxTargets; ++t) acc[t] = 0.f;
     float *hist = p.hist ? p.hist + ((int64_t)iy * p.ncx + ix) * p.B : nullptr;
     for (int b = 0; b < p.B; ++b) {
+        // the stored row holding image row y of bin b's planes (-1: zero)
+        auto row = [&](int y) -> int { return (y < 0 || !p.row_map) ? y : __ldg(p.row_map + (int64_t)b * p.H + y); };
+        const int Y0 = row(yT), Y1 = row(yC), Y2 = row(yB);
         float h;
         if constexpr (KIND == kGatherPlain) {
             const T U = plane_of<T>(p, p.t1, b).rect(X0, X2, Y0, Y2);
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(128) gather_kernel(GatherParams p)
             float u = 0.f;
             for (int i = 0; i < p.n_rings; ++i) {
                 const int a = p.ring_rx[i], c = p.ring_ry[i];
-                const T n = P1.rect(xc - a - 1, xc + a, yc - c - 1, yc + c);
+                const T n = P1.rect(xc - a - 1, xc + a, row(yc - c - 1), row(yc + c));
                 u = fmaf(p.ring_c[i], to_float(n), u);
             }
             h = u * p.inv_mass;

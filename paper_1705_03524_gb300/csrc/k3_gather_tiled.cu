@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256)
 }  // namespace
 
 cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, int B, int nl_per_bin,
-                        int n_targets, int want_tx, int want_stages, int want_bb, GatherShape *shape)
+                        int n_targets, int want_tx, int want_stages, int want_bb, bool row_map, GatherShape *shape)
 {
     const bool gau = kind == kGatherGaussian;
     const int A = 16 / elem_bytes;
@@ -60,9 +60,10 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         sh.kchain_max = gau ? KMAX : KMAX / 2;
         sh.n_targets = std::max(1, std::min(n_targets, kMaxTargets));
         // shared memory: barriers | sqrt(targets) | likelihood sums | bin-block list | [Gaussian carry] | stages
-        // (+ the CTA's list of bin blocks and of their rows to load: 2 x (B + 1) ints)
+        // (+ the CTA's list of bin blocks and of their rows to load: 2 x (B + 1) ints, and, when
+        // rows are read through a row map, each bin's stored row per lattice row: B x kTiledRowSlots int16)
         sh.dtop_off = (16 * kMaxStages + 4 * sh.n_targets * B + 4 * sh.n_targets * sh.kchain_max * tx + 8 * (B + 1) +
-                       15) / 16 * 16;
+                       (row_map ? 2 * B * kTiledRowSlots : 0) + 15) / 16 * 16;
         const int carry = gau ? (2 * gdx + 1) * (2 * gdy + 1) * tx * 8 : 0;
         sh.stage_off = (sh.dtop_off + carry + 127) / 128 * 128;
         const size_t stage = (size_t)sh.nl * sh.seg * elem_bytes;
@@ -154,7 +155,7 @@ cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_byt
     if (p_in.ncx <= 0 || p_in.ncy <= 0) return cudaSuccess;
     GatherShape sh;
     cudaError_t e = tiled_shape(kind, elem_bytes, p_in.gdx, p_in.gdy, 2 * p_in.rx + 1, p_in.B, p_in.nl,
-                                p_in.n_targets, p_in.want_tx, p_in.want_stages, p_in.want_bb, &sh);
+                                p_in.n_targets, p_in.want_tx, p_in.want_stages, p_in.want_bb, true, &sh);
     if (e != cudaSuccess) return e;
     GatherParams p = p_in;
     p.nbg = 1;

@@ -45,6 +45,8 @@ namespace {
 
 
 constexpr int KMAX = kTiledChainMax;
+constexpr int kRowSlots = kTiledRowSlots;  // lattice rows per chain: K + 1, or 2 K + 1 with K <= KMAX / 2 (Manhattan)
+static_assert(2 * (KMAX / 2) + 1 <= kRowSlots, "row slots");
 constexpr int kMaxStages = kTiledMaxStages;
 
 template <typename T>
@@ -184,7 +186,7 @@ __device__ __forceinline__ void axis_bernstein(const unsigned long long (&R)[5],
 }
 
 // One work item: column tile `tile` and chain `cy` (phase-major) of job p.
-template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SPLIT>
+template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SPLIT, bool ROWMAP>
 __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const int tile, const int cy, const int bg)
 {
     using u64 = unsigned long long;
@@ -231,6 +233,10 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     // union of its windows (see below); the list sits just below the carry area
     int *s_list = reinterpret_cast<int *>(sm + p.dtop_off) - 2 * (p.B + 1);
     int *s_rows = s_list + (p.B + 1);  // per listed bin block: the lattice rows to load (bit s)
+    // per bin and lattice row: the stored row that holds it (-1: the zero row),
+    // through the plan's row map when empty rows are not stored (plans use a row
+    // map only below 32768 rows, so int16 holds it)
+    int16_t *s_rmap = reinterpret_cast<int16_t *>(s_list) - p.B * kRowSlots;
     const int NS = p.nstage;
 
     // row segment [xs-rx-1, xs+TX+rx) of every plane, copied from a 16-byte boundary
@@ -271,19 +277,46 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     // ring: 2 reads per lattice row. The rows to load are those of the present
     // windows (Manhattan: top, centre and bottom rows). Histogram output needs
     // every bin and row, so then all are loaded.
+    auto row_of = [&](int s) -> int {
+        if constexpr (kMan) {
+            const int k = s >> 1;
+            return (s & 1) ? yc0 + k * h : yc0 + k * h - p.ry - 1;
+        } else {
+            return yc0 + s * h - p.ry - 1;
+        }
+    };
     const bool sparse = p.hist == nullptr;
     const int all_rows = (int)((1u << S) - 1u);
-    if (sparse) {
+    // the CTA's bins: all of them, or bin group bg's share of a split launch
+    const int bin0 = bb0 * BB, bin1 = min(p.B, bb1 * BB);
+    if constexpr (ROWMAP) {  // all threads: the row map reads overlap
+        for (int i = tid; i < (bin1 - bin0) * S; i += TX + 32) {
+            const int b = bin0 + i / S, s = i % S;
+            const int Y = row_of(s);
+            s_rmap[b * kRowSlots + s] = (int16_t)((Y < 0 || !p.row_map) ? Y : __ldg(p.row_map + (int64_t)b * p.H + Y));
+        }
+        __syncthreads();
+    }
+    // image row s of bin b's planes is stored at this row (-1: zero); without a
+    // row map every row is stored
+    auto stored_row = [&](int b, int s) -> int {
+        if constexpr (ROWMAP)
+            return s_rmap[b * kRowSlots + s];
+        else
+            return row_of(s);
+    };
+    {
         const int xa = xs - p.rx - 1;                           // exclusive
         const int xb = min(xs + TX, p.cx0 + p.ncx) - 1 + p.rx;  // inclusive
-        for (int b = tid; b < p.B; b += TX + 32) {
+        for (int b = bin0 + tid; b < bin1; b += TX + 32) {
+            if (!sparse) continue;
             const T *pl = reinterpret_cast<const T *>(p.ih) + ((int64_t)p.t1 * p.B + b) * p.plane;
             auto at = [&](int x, int y) -> T { return (x >= 0 && y >= 0) ? __ldg(pl + (int64_t)y * p.pitch + x) : T(0); };
-            auto span = [&](int y) -> T { return at(xb, y) - at(xa, y); };
+            auto span = [&](int s) -> T { return at(xb, stored_row(b, s)) - at(xa, stored_row(b, s)); };  // lattice row s
             unsigned rows_b = 0u;
-            T prev = span(yc0 - p.ry - 1);
+            T prev = span(0);
             for (int k = 0; k < K; ++k) {
-                const T next = span(yc0 + k * h + p.ry);
+                const T next = span(kMan ? 2 * k + 2 : k + 1);  // window k's bottom row
                 if (next != prev) rows_b |= kMan ? (7u << (2 * k)) : (3u << k);
                 prev = next;
             }
@@ -311,14 +344,6 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     const int nlist = s_list[p.B];
     const int steps = s_rows[p.B] * G;
 
-    auto row_of = [&](int s) -> int {
-        if constexpr (kMan) {
-            const int k = s >> 1;
-            return (s & 1) ? yc0 + k * h : yc0 + k * h - p.ry - 1;
-        } else {
-            return yc0 + s * h - p.ry - 1;
-        }
-    };
     // producer warp, lane 0: steps in order, each into stage m % NS once the
     // consumers have released that stage's previous step
     if (producer) {
@@ -334,9 +359,12 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                 atomicOr(p.status, kStatusTimeout);
                 return;
             }
-            const int Y = row_of(s);
             uint64_t *br = &full[st_i];
-            if (Y < 0) {  // the zero row above the image: nothing to copy
+            const int b0 = bb * BB;
+            const int nb = min(BB, p.B - b0);
+            int n_rows = 0;  // bins of the block whose row is stored (the others read as zero)
+            for (int j = 0; j < nb; ++j) n_rows += stored_row(b0 + j, s) >= 0;
+            if (n_rows == 0) {  // zero rows only (above the image, or before the bin's first pixel)
                 mbar_arrive(br);
             } else {
                 int nt;
@@ -349,18 +377,19 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                     nt = odd ? p.n_load_odd : p.n_load_even;
                     list = odd ? p.load_odd : p.load_even;
                 }
-                const int b0 = bb * BB;
-                const int nb = min(BB, p.B - b0);
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(br, (uint32_t)(nb * nt) * seg_bytes);
-                loaded += (unsigned long long)(nb * nt) * seg_bytes;
+                mbar_arrive_expect_tx(br, (uint32_t)(n_rows * nt) * seg_bytes);
+                loaded += (unsigned long long)(n_rows * nt) * seg_bytes;
                 T *dst = stages + (size_t)st_i * stage_elems + land;
-                const T *row = reinterpret_cast<const T *>(p.ih) + (int64_t)Y * p.pitch + x_begin;
-                for (int j = 0; j < nb; ++j)
+                for (int j = 0; j < nb; ++j) {
+                    const int Y = stored_row(b0 + j, s);
+                    if (Y < 0) continue;
+                    const T *row = reinterpret_cast<const T *>(p.ih) + (int64_t)Y * p.pitch + x_begin;
                     for (int t = 0; t < nt; ++t) {
                         const T *src = row + ((int64_t)list[t] * p.B + b0 + j) * p.plane;
                         bulk_copy_g2s(dst + (size_t)(j * nt + t) * p.seg, src, seg_bytes, br);
                     }
+                }
             }
             if (++g == G) {
                 g = 0;
@@ -420,7 +449,9 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
         const int nb = min(BB, p.B - b0);
         for (int s = 0; s < S && !stop; ++s) {
             if (!((rmask >> s) & 1u)) continue;  // after an absent window: same values as the carried ones
-            const bool zero_row = row_of(s) < 0;
+            // bin b0's row s reads as zero (above the image, or before the bin's
+            // first pixel); the Gaussian carries one bin, the others test each bin
+            const bool zero_row = stored_row(b0, s) < 0;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (!mbar_wait(&full[cs], cpar)) stop = true;
@@ -455,12 +486,13 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                     for (int j = 0; j < BB; ++j) {
                         if (j >= nb) break;
                         const int b = b0 + j;
+                        const bool zr = stored_row(b, s) < 0;
                         // h stays 0 for a bin with no pixel in the window: the
                         // combination, conversion and square root are skipped
                         float hval = 0.f;
                         if constexpr (KIND == kGatherPlain) {
                             const T *q = st + (size_t)j * p.seg;
-                            const T d = zero_row ? T(0) : (T)(q[i2] - q[i0]);
+                            const T d = zr ? T(0) : (T)(q[i2] - q[i0]);
                             if (done_k >= 0) {
                                 const T U = d - top[j][0];
                                 if (U != 0) hval = ring_to_float<T>(U) * p.inv_mass;
@@ -469,11 +501,11 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                         } else if constexpr (kMan) {
                             if (s & 1) {  // centre row: full-width sums of IH_1 and IH_y
                                 const T *q = st + (size_t)(j * 2) * p.seg;
-                                mid1[j] = q[i2] - q[i0];
-                                midy[j] = q[p.seg + i2] - q[p.seg + i0];
+                                mid1[j] = zr ? T(0) : (T)(q[i2] - q[i0]);
+                                midy[j] = zr ? T(0) : (T)(q[p.seg + i2] - q[p.seg + i0]);
                             } else {
                                 T d1l = 0, d1r = 0, dxl = 0, dxr = 0, dyf = 0;
-                                if (!zero_row) {
+                                if (!zr) {
                                     const T *q = st + (size_t)(j * 3) * p.seg;
                                     const T a0 = q[i0], a1 = q[i1], a2 = q[i2];
                                     const T *sx = q + p.seg;
@@ -507,7 +539,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                             }
                         } else {  // Euclidean
                             T d[5] = {0, 0, 0, 0, 0};
-                            if (!zero_row) {
+                            if (!zr) {
                                 const T *q = st + (size_t)(j * 5) * p.seg;
 #pragma unroll
                                 for (int t = 0; t < 5; ++t) d[t] = q[t * p.seg + i2] - q[t * p.seg + i0];
@@ -602,9 +634,34 @@ template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SPLIT>
 __global__ void __launch_bounds__(TX + 32) gather_tiled_kernel(const __grid_constant__ GatherParams p)
 {
     if constexpr (SPLIT)
-        gather_tiled_body<KIND, T, TX, DX, DY, BB, true>(p, blockIdx.x, blockIdx.y / p.nbg, blockIdx.y % p.nbg);
+        gather_tiled_body<KIND, T, TX, DX, DY, BB, true, true>(p, blockIdx.x, blockIdx.y / p.nbg, blockIdx.y % p.nbg);
     else
-        gather_tiled_body<KIND, T, TX, DX, DY, BB, false>(p, blockIdx.x, blockIdx.y, 0);
+        gather_tiled_body<KIND, T, TX, DX, DY, BB, false, true>(p, blockIdx.x, blockIdx.y, 0);
+}
+
+// The same for the 128-column Gaussian, compiled for 5 resident CTAs: 72
+// registers instead of 86 and no spills. Its 3-stage ring fits 4 CTAs in shared
+// memory; the leaner code measured 2-5% faster at w = 21 and 81 and 1% slower
+// at 41. (A minimum of one CTA written out for the other kernels changed their
+// register allocation and slowed them, hence a kernel of its own.)
+template <typename T, int DX, int DY, bool SPLIT>
+__global__ void __launch_bounds__(128 + 32, 5) gather_gauss128_kernel(const __grid_constant__ GatherParams p)
+{
+    if constexpr (SPLIT)
+        gather_tiled_body<kGatherGaussian, T, 128, DX, DY, 1, true, true>(p, blockIdx.x, blockIdx.y / p.nbg,
+                                                                           blockIdx.y % p.nbg);
+    else
+        gather_tiled_body<kGatherGaussian, T, 128, DX, DY, 1, false, true>(p, blockIdx.x, blockIdx.y, 0);
+}
+
+// the single-job kernel of an instantiation
+template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SPLIT>
+constexpr auto single_kernel()
+{
+    if constexpr (KIND == kGatherGaussian && TX == 128 && BB == 1)
+        return gather_gauss128_kernel<T, DX, DY, SPLIT>;
+    else
+        return gather_tiled_kernel<KIND, T, TX, DX, DY, BB, SPLIT>;
 }
 
 // A table of jobs sharing one shape: one CTA per work item, items of job j
@@ -622,14 +679,14 @@ __global__ void __launch_bounds__(TX + 32)
     const GatherParams &p = jobs[lo];
     const int li = item - item_start[lo];
     const int tiles = (p.ncx + TX - 1) / TX;
-    gather_tiled_body<KIND, T, TX, DX, DY, BB, false>(p, li % tiles, li / tiles, 0);
+    gather_tiled_body<KIND, T, TX, DX, DY, BB, false, false>(p, li % tiles, li / tiles, 0);  // work sets store every row
 }
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
 int kernel_regs()
 {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, gather_tiled_kernel<KIND, T, TX, DX, DY, BB, false>) != cudaSuccess) return 255;
+    if (cudaFuncGetAttributes(&fa, single_kernel<KIND, T, TX, DX, DY, BB, false>()) != cudaSuccess) return 255;
     return fa.numRegs;
 }
 
@@ -649,8 +706,8 @@ cudaError_t run_op(TiledOp &op)
         return cudaSuccess;
     case TiledOp::kSingle: {
         const GatherParams &p = *op.p;
-        auto fn = p.nbg > 1 ? gather_tiled_kernel<K, T, TX, DX, DY, BB, true>
-                            : gather_tiled_kernel<K, T, TX, DX, DY, BB, false>;
+        auto fn = p.nbg > 1 ? single_kernel<K, T, TX, DX, DY, BB, true>()
+                            : single_kernel<K, T, TX, DX, DY, BB, false>();
         cudaError_t e = set_smem(fn, op.sh->smem);
         if (e != cudaSuccess) return e;
         const int h = 2 * p.ry + 1;

@@ -277,6 +277,11 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     // largest map, at most 64 MB
     pl->partial_floats = std::min<uint64_t>((uint64_t)8 * H * W, (64ull << 20) / sizeof(float));
     pl->off_partial = take(pl->partial_floats * sizeof(float));
+    pl->sparse_rows = pl->band_rows <= 64 && H <= 32767;  // the gather keeps stored rows as int16
+    if (pl->sparse_rows) {
+        pl->off_occ = take((uint64_t)d->bins * pl->n_bands * sizeof(unsigned long long));
+        pl->off_row_map = take((uint64_t)d->bins * H * sizeof(int));
+    }
     if (want_exp) {
         pl->off_exp = take((uint64_t)4 * d->bins * pl->plane * sizeof(unsigned long long));
         pl->off_exp_carry = take((uint64_t)2 * d->bins * pl->n_bands * pl->ih_pitch * sizeof(unsigned long long));
@@ -337,6 +342,7 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
 {
     std::memset(&g, 0, sizeof g);
     g.ih = pl->d_mem + pl->off_ih;
+    g.row_map = (pl->sparse_rows && pl->d_mem) ? reinterpret_cast<const int *>(pl->d_mem + pl->off_row_map) : nullptr;
     g.plane = pl->plane;
     g.pitch = pl->ih_pitch;
     g.B = pl->desc.bins;
@@ -448,6 +454,7 @@ cudaError_t run_exp_gather(swih_plan_s *pl, int w, int h, int cx0, int cy0, int 
     std::memset(&g, 0, sizeof g);
     const int B = pl->desc.bins;
     g.count = pl->d_mem + pl->off_ih + (uint64_t)pl->term_index[0][0] * B * pl->plane * pl->elem_bytes;
+    g.row_map = pl->sparse_rows ? reinterpret_cast<const int *>(pl->d_mem + pl->off_row_map) : nullptr;
     g.J = reinterpret_cast<const unsigned long long *>(pl->d_mem + pl->off_exp);
     g.pitch = pl->ih_pitch;
     g.plane = pl->plane;
@@ -634,6 +641,7 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
     }
     sp.spin_limit = 1LL << 22;  // with 64 ns sleeps: well under a few seconds
     sp.stall_tile = -1;
+    sp.occ = pl->sparse_rows ? reinterpret_cast<unsigned long long *>(pl->d_mem + pl->off_occ) : nullptr;
     if (pl->inject == SWIH_INJECT_STALL_SCAN_TILE) {
         sp.stall_tile = 0;        // chain 0, band 0 never publishes
         sp.spin_limit = 1LL << 12;
@@ -641,6 +649,11 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
     }
     e = launch_ih_scan(sp, pl->elem_bytes, pl->scan_E, pl->scan_threads, s);
     if (e != cudaSuccess) return cuda_fail(pl, "ih_scan launch", e);
+    if (pl->sparse_rows) {
+        e = launch_row_map(sp.occ, reinterpret_cast<int *>(pl->d_mem + pl->off_row_map), d.bins, d.height,
+                           pl->band_rows, pl->n_bands, s);
+        if (e != cudaSuccess) return cuda_fail(pl, "row map launch", e);
+    }
     if (pl->has_exp) {
         ExpScanParams xp;
         std::memset(&xp, 0, sizeof xp);
@@ -841,6 +854,7 @@ swih_status swih_plan_get_info(swih_plan_t pl, swih_plan_info *info)
         info->d_exp = pl->d_mem + pl->off_exp;
         info->exp_frac_bits = pl->exp_F;
     }
+    if (pl->sparse_rows && pl->d_mem) info->d_row_map = reinterpret_cast<const int32_t *>(pl->d_mem + pl->off_row_map);
     return SWIH_OK;
 }
 

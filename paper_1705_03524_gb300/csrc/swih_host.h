@@ -30,6 +30,11 @@ struct swih_plan_s {
     uint64_t off_ih = 0, off_agg = 0, off_incl = 0, off_flags = 0, total = 0;
     uint64_t flags_bytes = 0;
     uint64_t off_partial = 0, partial_floats = 0;  // split-gather scratch
+    // sparse rows (bands of at most 64 rows): rows without a pixel of a bin are
+    // not stored; occ holds each (bin, band)'s stored-row mask, row_map each
+    // (bin, row)'s last stored row
+    bool sparse_rows = false;
+    uint64_t off_occ = 0, off_row_map = 0;
     // exponential kernel: decay per pixel, fixed-point fraction bits, the four
     // directional integral histograms and the scan's band carries
     bool has_exp = false;

@@ -70,7 +70,16 @@ struct ScanParams {
     long long spin_limit;
     int sb_rows;            // band rows whose bins the tile keeps in shared memory (set by the launcher)
     int stall_tile;      // ticket of a tile that never publishes (fault injection), else -1
+    // Sparse rows (single-plan scan, band_rows <= 64): a row without a pixel of
+    // bin b equals the row above in every plane of b, so it is neither computed
+    // nor stored; occ[b * n_bands + band] receives the band's mask of stored rows
+    // (bit r: band row r holds bin b). NULL: every row is stored.
+    unsigned long long *occ;
 };
+// row_map[b * H + y] = the last stored row <= y of bin b's planes (-1: none, the
+// row is all zero), from the occupancy words of a sparse-row scan
+cudaError_t launch_row_map(const unsigned long long *occ, int *row_map, int B, int H, int band_rows, int n_bands,
+                           cudaStream_t s);
 // E = columns per thread, threads = ceil(W/E) rounded to a warp multiple
 cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads,
                            cudaStream_t s);
@@ -124,6 +133,7 @@ cudaError_t launch_exp_scan(const ExpScanParams &p, cudaStream_t s);
 // the 16 corner reads of the four J_d.
 struct ExpGatherParams {
     const void *count;           // plain IH plane of bin b at count + b * plane (ring elements)
+    const int *row_map;          // [b][H] stored row holding row y of the count plane (-1: zero); NULL: identity
     const unsigned long long *J; // as ExpScanParams::J
     int64_t pitch, plane;        // elements (shared by both)
     int B, H, W, rx, ry;
@@ -142,6 +152,7 @@ constexpr int kMaxRings = 16;
 
 struct GatherParams {
     const void *ih;
+    const int *row_map;     // [b][H]: row whose stored values hold row y of bin b (-1: zero); NULL: identity
     int64_t plane, pitch;   // elements
     int B, H, W;
     int rx, ry;
@@ -186,6 +197,7 @@ void count_launches(unsigned n);
 // Tiled gather; returns cudaErrorNotSupported when a window's row segments do
 // not fit in shared memory (the caller then uses launch_gather).
 constexpr int kTiledChainMax = 8;
+constexpr int kTiledRowSlots = kTiledChainMax + 1;  // lattice rows of a chain (K + 1, or 2 K + 1 with K <= 4)
 constexpr int kMaxTargets = 8;
 cudaError_t launch_gather_tiled(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
@@ -202,9 +214,11 @@ struct GatherShape {
     size_t smem;     // dynamic shared memory bytes
 };
 // Shape for jobs of one kind with the given fitted degrees, largest window
-// width and bin count; cudaErrorNotSupported when nothing fits.
+// width and bin count; cudaErrorNotSupported when nothing fits. row_map: the
+// launch reads rows through a row map (single-plan launches), which takes a
+// table of B x kTiledRowSlots int16 in shared memory.
 cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, int B, int nl_per_bin,
-                        int n_targets, int want_tx, int want_stages, int want_bb, GatherShape *shape);
+                        int n_targets, int want_tx, int want_stages, int want_bb, bool row_map, GatherShape *shape);
 // Fill a job's shape fields and chain split; returns its number of work items
 // (column tiles x chains).
 int tiled_items(GatherParams *job, const GatherShape &shape);

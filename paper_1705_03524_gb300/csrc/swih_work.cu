@@ -213,6 +213,7 @@ swih_status WorkSet::build_jobs(std::string &err)
         g.target = jb.target;
         g.map = jb.map;
         g.hist = nullptr;
+        g.row_map = nullptr;  // the table scan stores every row
         g.nbg = 1;  // table launches span many waves already; no split-gather scratch here
         g.load_bytes = nullptr;
         g.partial = nullptr;
@@ -261,7 +262,7 @@ swih_status WorkSet::build_jobs(std::string &err)
         }
         const GatherParams &g0 = jobs_[G.job_begin];
         G.tiled = tiled_shape(G.kind, tmpl_.elem_bytes, G.gdx, G.gdy, max_w, spec_.bins, g0.nl, max_t, G.want_tx,
-                              G.want_stages, G.want_bb, &G.shape) == cudaSuccess;
+                              G.want_stages, G.want_bb, false, &G.shape) == cudaSuccess;
         G.items_off = (int)items_.size();
         long long items = 0;
         for (int j = G.job_begin; j < G.job_end; ++j) {

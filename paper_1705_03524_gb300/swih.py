@@ -95,6 +95,7 @@ class swih_plan_info(ctypes.Structure):
         ("workspace_bytes", ctypes.c_uint64),
         ("d_exp", ctypes.c_void_p),
         ("exp_frac_bits", ctypes.c_int32),
+        ("d_row_map", ctypes.c_void_p),
     ]
 
 

@@ -75,11 +75,21 @@ def check_ih(plan, img, bitdepth, B):
     bits = 8 * info.elem_bytes
     ts = "<i4" if info.elem_bytes == 4 else "<i8"
     udt = np.uint32 if info.elem_bytes == 4 else np.uint64
+    # rows of a bin the scan did not store (no pixel of the bin) are read at the
+    # stored row the plan's row map gives (-1: zero)
+    rmap = device_rows(info.d_row_map, B, H, "<i4") if info.d_row_map else None
+    if rmap is not None:
+        for b in range(B):
+            holds = (bins == b).any(axis=1)
+            last = np.maximum.accumulate(np.where(holds, np.arange(H), -1))
+            assert np.array_equal(rmap[b], last), f"row map of bin {b}"
     for t in range(info.n_terms):
         p, q = info.term_p[t], info.term_q[t]
         for b in range(B):
             ptr = info.d_ih + (t * B + b) * info.plane_elems * info.elem_bytes
             got = device_rows(ptr, H, info.ih_pitch, ts)[:, :W].view(udt)
+            if rmap is not None:
+                got = np.where((rmap[b] >= 0)[:, None], got[np.maximum(rmap[b], 0)], 0).astype(udt)
             ref = O.weighted_ih(bins, b, p, q, bits)
             if not np.array_equal(got, ref):
                 bad = np.argwhere(got != ref)[0]
@@ -364,21 +374,21 @@ def test_wedding_cake_and_plain_are_approximations_swih_is_exact():
 def test_launch_counter_counts_enqueued_kernels():
     img = synth.uniform_image(64, 80, 8, seed=5)
     c0 = S.swih_launch_count()
-    plan, _buf = make_plan(img, 8, 8, ("manhattan",), (9, 9))  # one build: quantise + scan
+    plan, _buf = make_plan(img, 8, 8, ("manhattan",), (9, 9))  # one build: quantise + scan + row map
     with plan:
         c1 = S.swih_launch_count()
         m = torch.empty((56, 72), device=DEV)
         plan.likelihood("manhattan", 9, 9, torch.full((8,), 0.125, device=DEV), m)
         plan.sync_status()
         c2 = S.swih_launch_count()
-    assert c1 - c0 == 2
+    assert c1 - c0 == 3
     assert c2 - c1 in (1, 2)  # the gather, plus the reduction when the bins were split
 
 
 @pytest.mark.parametrize("pattern", ["stripes", "blobs", "wide_stripes"])
 def test_integral_histograms_with_rows_missing_bins(pattern):
-    """Rows that hold no pixel of a bin are copied from the row above by the
-    scan instead of scanned; check every plane bit for bit where that happens
+    """Rows that hold no pixel of a bin are not stored by the scan (they are read
+    through the plan's row map); check every plane bit for bit where that happens
     often (horizontal stripes of one value, a smooth scene), across several
     bands (the first row of a band is always computed)."""
     if pattern in ("stripes", "wide_stripes"):
@@ -394,6 +404,34 @@ def test_integral_histograms_with_rows_missing_bins(pattern):
         check_ih(plan, img, 8, 8)
         bins = oracle_bins(img, 8, 8)
         check_windows(plan, bins, 8, "gaussian", 9, 7)
+
+
+def test_rows_left_from_an_earlier_build_are_never_read():
+    """A plan stores only the rows that hold each bin; the rows it skips keep
+    whatever an earlier build wrote there. Build uniform noise first (every row
+    of every bin stored), then stripes on the same plan: every plane through
+    the row map, and maps of every tiled and direct kernel, must match the
+    oracle for the second image."""
+    H, W, B = 90, 150, 8
+    noise = synth.uniform_image(H, W, 8, seed=11)
+    rng = np.random.default_rng(12)
+    stripes = np.repeat(rng.integers(0, 256, size=H).astype(np.uint8)[:, None], W, axis=1)
+    stripes[::9, ::11] = 7
+    kinds = ("plain", "manhattan", "euclidean", "gaussian", "wedding")
+    plan, buf = make_plan(noise, 8, B, kinds, (21, 21))
+    with plan:
+        info = plan.info()
+        assert info.d_row_map
+        buf2, ptr2, _ = upload(stripes)
+        plan.build_ih(ptr2)
+        plan.sync_status()
+        bins = check_ih(plan, stripes, 8, B)
+        for kind in kinds:
+            check_windows(plan, bins, B, kind, 21, 15)
+        S.swih_debug_inject(plan.handle, S.SWIH_INJECT_DIRECT_GATHER)
+        for kind in ("manhattan", "gaussian"):
+            check_windows(plan, bins, B, kind, 9, 9)
+        S.swih_debug_inject(plan.handle, 0)
 
 
 def test_gather_counts_the_bytes_it_loads():

@@ -29,12 +29,19 @@ class _View:
 
 
 def planes(ptr, info):
-    """All integral-histogram planes as host uint arrays [T*B, H, W]."""
+    """All integral-histogram planes as host uint arrays [T*B, H, W]; a plan's rows
+    that were not stored (no pixel of the bin) are read through its row map."""
     ts = "<i4" if info.elem_bytes == 4 else "<i8"
     udt = np.uint32 if info.elem_bytes == 4 else np.uint64
     n = info.n_terms * info.bins
     t = torch.as_tensor(_View(ptr, (n, info.height, info.ih_pitch), ts), device=DEV)
-    return t.cpu().numpy()[:, :, : info.width].view(udt)
+    out = t.cpu().numpy()[:, :, : info.width].view(udt)
+    if info.d_row_map:
+        rm = torch.as_tensor(_View(info.d_row_map, (info.bins, info.height), "<i4"), device=DEV).cpu().numpy()
+        for i in range(n):
+            r = rm[i % info.bins]
+            out[i] = np.where((r >= 0)[:, None], out[i][np.maximum(r, 0)], 0)
+    return out
 
 
 @pytest.mark.parametrize("kernels,shape,B", [(("manhattan", "euclidean"), (300, 500), 16),
