@@ -237,7 +237,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     if (tid == 0) {
         __threadfence();
         st_release(my_flag, band == 0 ? kFlagInclusive : kFlagAggregate);
-        if (SPARSE && qi == 0) p.occ[(int64_t)b * r.n_bands + band] = s_rows;  // the rows this bin stores
+        if (SPARSE && qi == 0) r.occ[(int64_t)b * r.n_bands + band] = s_rows;  // the rows this bin stores
     }
 
     // ---- 2. look back over the bands above for the column carry
@@ -415,6 +415,8 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_c
     r.W = p.W;
     r.n_bands = p.n_bands;
     r.ticket0 = 0;
+    r.occ = p.occ;
+    r.row_map = nullptr;
     scan_tile<T, E, NP, false, SPARSE>(p, r, ticket, band, ticket - band * n_chains);
 }
 
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_c
 // [table[i].ticket0, table[i + 1].ticket0), band-major, so every tile a tile
 // may wait for (the same chain, an earlier band, the same region) holds a
 // smaller ticket and has already started.
-template <typename T, int E, int NP>
+template <typename T, int E, int NP, bool SPARSE>
 __global__ void __launch_bounds__(kMaxScanThreads)
     ih_scan_table_kernel(const __grid_constant__ ScanParams p, const ScanRoi *__restrict__ table, int n)
 {
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(kMaxScanThreads)
     const int local = ticket - r.ticket0;
     const int n_chains = p.B * p.n_q;
     const int band = local / n_chains;
-    scan_tile<T, E, NP, true, false>(p, r, ticket, band, local - band * n_chains);
+    scan_tile<T, E, NP, !SPARSE, SPARSE>(p, r, ticket, band, local - band * n_chains);
 }
 
 template <typename KernelFn>
@@ -460,10 +462,15 @@ cudaError_t launch_typed(const ScanParams &p_in, int threads, const ScanRoi *tab
     p.sb_rows = (p.band_rows <= 64 && (size_t)p.band_rows * per_row <= 96 * 1024) ? p.band_rows : 0;
     const size_t smem = (size_t)p.sb_rows * per_row;
     cudaError_t e;
-    if (table) {
-        e = allow_smem(ih_scan_table_kernel<T, E, NP>, smem);
+    if (table && p.occ) {
+        if (p.band_rows > 64) return cudaErrorInvalidValue;  // the occupancy word covers 64 rows
+        e = allow_smem(ih_scan_table_kernel<T, E, NP, true>, smem);
         if (e != cudaSuccess) return e;
-        ih_scan_table_kernel<T, E, NP><<<(unsigned)tiles, threads, smem, s>>>(p, table, n_roi);
+        ih_scan_table_kernel<T, E, NP, true><<<(unsigned)tiles, threads, smem, s>>>(p, table, n_roi);
+    } else if (table) {
+        e = allow_smem(ih_scan_table_kernel<T, E, NP, false>, smem);
+        if (e != cudaSuccess) return e;
+        ih_scan_table_kernel<T, E, NP, false><<<(unsigned)tiles, threads, smem, s>>>(p, table, n_roi);
     } else if (p.occ) {
         if (p.band_rows > 64) return cudaErrorInvalidValue;  // the occupancy word covers 64 rows
         e = allow_smem(ih_scan_kernel<T, E, NP, true>, smem);
@@ -506,15 +513,14 @@ cudaError_t launch_e(const ScanParams &p, int E, int threads, const ScanRoi *tab
 
 // One warp per bin: the bands' last stored rows, a running maximum across the
 // bands (warp prefix max, 32 bands at a time), then every row's last stored row.
-__global__ void __launch_bounds__(32) row_map_kernel(const unsigned long long *__restrict__ occ,
-                                                     int *__restrict__ row_map, int H, int band_rows, int n_bands)
+__device__ __forceinline__ void row_map_body(const unsigned long long *__restrict__ occ, int *__restrict__ row_map,
+                                             int H, int band_rows, int n_bands)
 {
-    const int b = blockIdx.x;
     const int lane = threadIdx.x;
     int carry = -1;  // last stored row of the bands before this group of 32
     for (int k0 = 0; k0 < n_bands; k0 += 32) {
         const int k = k0 + lane;
-        const unsigned long long w = k < n_bands ? occ[(int64_t)b * n_bands + k] : 0ull;
+        const unsigned long long w = k < n_bands ? occ[k] : 0ull;
         int last = w ? k * band_rows + 63 - __clzll((long long)w) : -1;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -528,11 +534,26 @@ __global__ void __launch_bounds__(32) row_map_kernel(const unsigned long long *_
             int cur = before;
             for (int y = y0; y < y1; ++y) {
                 if ((w >> (y - y0)) & 1ull) cur = y;
-                row_map[(int64_t)b * H + y] = cur;
+                row_map[y] = cur;
             }
         }
         carry = max(carry, __shfl_sync(0xffffffffu, last, 31));
     }
+}
+
+__global__ void __launch_bounds__(32) row_map_kernel(const unsigned long long *__restrict__ occ,
+                                                     int *__restrict__ row_map, int H, int band_rows, int n_bands)
+{
+    const int b = blockIdx.x;
+    row_map_body(occ + (int64_t)b * n_bands, row_map + (int64_t)b * H, H, band_rows, n_bands);
+}
+
+// block (region i, bin b) = blockIdx.x = i * B + b
+__global__ void __launch_bounds__(32) row_map_table_kernel(const ScanRoi *__restrict__ table, int B, int band_rows)
+{
+    const int i = blockIdx.x / B, b = blockIdx.x - i * B;
+    const ScanRoi &r = table[i];
+    row_map_body(r.occ + (int64_t)b * r.n_bands, r.row_map + (int64_t)b * r.H, r.H, band_rows, r.n_bands);
 }
 
 }  // namespace
@@ -542,6 +563,16 @@ cudaError_t launch_row_map(const unsigned long long *occ, int *row_map, int B, i
 {
     if (band_rows < 1 || band_rows > 64) return cudaErrorInvalidValue;
     row_map_kernel<<<(unsigned)B, 32, 0, s>>>(occ, row_map, H, band_rows, n_bands);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_map_table(const ScanRoi *d_table, int n_roi, int B, int band_rows, cudaStream_t s)
+{
+    if (band_rows < 1 || band_rows > 64) return cudaErrorInvalidValue;
+    if ((long long)n_roi * B > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (n_roi <= 0) return cudaSuccess;
+    row_map_table_kernel<<<(unsigned)(n_roi * B), 32, 0, s>>>(d_table, B, band_rows);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(TX + 32)
     const GatherParams &p = jobs[lo];
     const int li = item - item_start[lo];
     const int tiles = (p.ncx + TX - 1) / TX;
-    gather_tiled_body<KIND, T, TX, DX, DY, BB, false, false>(p, li % tiles, li / tiles, 0);  // work sets store every row
+    gather_tiled_body<KIND, T, TX, DX, DY, BB, false, true>(p, li % tiles, li / tiles, 0);
 }
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>

@@ -150,6 +150,7 @@ class WorkSet {
         int n_bands = 0;
         int64_t bins_pitch = 0, ih_pitch = 0, plane = 0;
         uint64_t off_bins = 0, off_ih = 0, off_agg = 0, off_incl = 0, off_flags = 0;
+        uint64_t off_occ = 0, off_row_map = 0;  // sparse rows
         int ticket0 = 0;
         long long chunk0 = 0;
     };
@@ -174,6 +175,7 @@ class WorkSet {
     std::vector<Group> groups_;
     std::vector<unsigned char> blob_;
     int scan_E_ = 4, scan_threads_ = 32, band_rows_ = 32;
+    bool sparse_ = false;  // the scan stores only the rows that hold each bin; gathers read through row maps
     long long scan_tiles_ = 0, quant_chunks_ = 0;
     uint64_t flags_ints_ = 0, n_centres_ = 0;
     uint64_t off_status_ = 0, off_flags_ = 0, off_tables_ = 0, total_ = 0;

@@ -94,11 +94,19 @@ struct ScanRoi {
     int *flags;
     int H, W, n_bands;
     int ticket0;  // first ticket of the region; regions are in ticket order
+    // sparse rows (when the launch's p.occ is non-NULL): the region's
+    // occupancy words [b][band] and row map [b][H]
+    unsigned long long *occ;
+    int *row_map;
 };
 // One launch over several regions sharing B, terms, ring and band height;
-// p carries those plus ticket/status/spin_limit; tiles = total tiles.
+// p carries those plus ticket/status/spin_limit; tiles = total tiles. A
+// non-NULL p.occ selects sparse rows (each region's own occ is used).
 cudaError_t launch_ih_scan_table(const ScanParams &p, const ScanRoi *d_table, int n_roi, long long tiles,
                                  int elem_bytes, int E, int threads, cudaStream_t s);
+// The row maps of every region of a sparse table scan (table[i].occ ->
+// table[i].row_map), one launch.
+cudaError_t launch_row_map_table(const ScanRoi *d_table, int n_roi, int B, int band_rows, cudaStream_t s);
 
 // ---------------------------------------------------------------- K2e scan
 // The exponential kernel's four directional integral histograms J_d (Sec. 2.1

@@ -135,6 +135,10 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
     off_flags_ = kStatusBytes;  // directly after the status word: one memset clears both
     off_tables_ = align256(off_flags_ + flags_ints_ * sizeof(int));
     uint64_t off = off_tables_ + tables;
+    // rows that hold no pixel of a bin are not stored (bands of at most 64 rows,
+    // regions below 32768 rows: the gathers keep stored rows as int16)
+    sparse_ = band_rows_ <= 64;
+    for (const auto &R : regions_) sparse_ = sparse_ && R.in.H <= 32767;
     for (auto &R : regions_) {
         R.off_bins = off;
         off = align256(off + (uint64_t)R.in.H * R.bins_pitch);
@@ -144,6 +148,12 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
         off = align256(off + n_chains * R.n_bands * R.ih_pitch * es);
         R.off_incl = off;
         off = align256(off + n_chains * R.n_bands * R.ih_pitch * es);
+        if (sparse_) {
+            R.off_occ = off;
+            off = align256(off + (uint64_t)spec.bins * R.n_bands * sizeof(unsigned long long));
+            R.off_row_map = off;
+            off = align256(off + (uint64_t)spec.bins * R.in.H * sizeof(int));
+        }
     }
     total_ = off;
     d_mem_ = nullptr;
@@ -213,7 +223,7 @@ swih_status WorkSet::build_jobs(std::string &err)
         g.target = jb.target;
         g.map = jb.map;
         g.hist = nullptr;
-        g.row_map = nullptr;  // the table scan stores every row
+        g.row_map = sparse_ ? reinterpret_cast<const int *>(d_mem_ + R.off_row_map) : nullptr;
         g.nbg = 1;  // table launches span many waves already; no split-gather scratch here
         g.load_bytes = nullptr;
         g.partial = nullptr;
@@ -262,7 +272,7 @@ swih_status WorkSet::build_jobs(std::string &err)
         }
         const GatherParams &g0 = jobs_[G.job_begin];
         G.tiled = tiled_shape(G.kind, tmpl_.elem_bytes, G.gdx, G.gdy, max_w, spec_.bins, g0.nl, max_t, G.want_tx,
-                              G.want_stages, G.want_bb, false, &G.shape) == cudaSuccess;
+                              G.want_stages, G.want_bb, true, &G.shape) == cudaSuccess;
         G.items_off = (int)items_.size();
         long long items = 0;
         for (int j = G.job_begin; j < G.job_end; ++j) {
@@ -308,6 +318,8 @@ void WorkSet::build_blob()
         stt[i].W = R.in.W;
         stt[i].n_bands = R.n_bands;
         stt[i].ticket0 = R.ticket0;
+        stt[i].occ = sparse_ ? reinterpret_cast<unsigned long long *>(d_mem_ + R.off_occ) : nullptr;
+        stt[i].row_map = sparse_ ? reinterpret_cast<int *>(d_mem_ + R.off_row_map) : nullptr;
     }
     if (!jobs_.empty()) std::memcpy(blob_.data() + tab_jobs_, jobs_.data(), sizeof(GatherParams) * jobs_.size());
     if (!items_.empty()) std::memcpy(blob_.data() + tab_items_, items_.data(), sizeof(int) * items_.size());
@@ -355,9 +367,17 @@ cudaError_t WorkSet::enqueue(cudaStream_t s, bool zero_status) const
     sp.status = status_device();
     sp.spin_limit = 1LL << 22;  // with 64 ns sleeps: well under a few seconds
     sp.stall_tile = -1;
-    e = launch_ih_scan_table(sp, reinterpret_cast<const ScanRoi *>(tables_device() + tab_scan_), (int)regions_.size(),
-                             scan_tiles_, tmpl_.elem_bytes, scan_E_, scan_threads_, s);
+    // a table launch only tests occ for non-NULL; each region writes its own
+    sp.occ = sparse_ && !regions_.empty() ? reinterpret_cast<unsigned long long *>(d_mem_ + regions_[0].off_occ)
+                                          : nullptr;
+    const ScanRoi *d_scan = reinterpret_cast<const ScanRoi *>(tables_device() + tab_scan_);
+    e = launch_ih_scan_table(sp, d_scan, (int)regions_.size(), scan_tiles_, tmpl_.elem_bytes, scan_E_, scan_threads_,
+                             s);
     if (e != cudaSuccess) return e;
+    if (sparse_) {
+        e = launch_row_map_table(d_scan, (int)regions_.size(), spec_.bins, band_rows_, s);
+        if (e != cudaSuccess) return e;
+    }
     for (int g = 0; g < (int)groups_.size(); ++g) {
         e = enqueue_group(g, s);
         if (e != cudaSuccess) return e;
