@@ -152,6 +152,7 @@ int choose_bin_groups(const GatherParams &p, const GatherShape &sh, long long ba
 cudaError_t launch_gather_tiled(const GatherParams &p_in, int kind, int elem_bytes, cudaStream_t s)
 {
     if (kind == kGatherWedding) return cudaErrorNotSupported;  // nested windows: the direct gather
+    if (p_in.H > kTiledMaxRows) return cudaErrorNotSupported;  // rows beyond int16: the direct gather
     if (p_in.ncx <= 0 || p_in.ncy <= 0) return cudaSuccess;
     GatherShape sh;
     cudaError_t e = tiled_shape(kind, elem_bytes, p_in.gdx, p_in.gdy, 2 * p_in.rx + 1, p_in.B, p_in.nl,

@@ -206,6 +206,7 @@ void count_launches(unsigned n);
 // not fit in shared memory (the caller then uses launch_gather).
 constexpr int kTiledChainMax = 8;
 constexpr int kTiledRowSlots = kTiledChainMax + 1;  // lattice rows of a chain (K + 1, or 2 K + 1 with K <= 4)
+constexpr int kTiledMaxRows = 32767;  // the tiled gather keeps rows as int16; taller images use the direct one
 constexpr int kMaxTargets = 8;
 cudaError_t launch_gather_tiled(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 

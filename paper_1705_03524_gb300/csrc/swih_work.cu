@@ -265,13 +265,16 @@ swih_status WorkSet::build_jobs(std::string &err)
     // launch shape and work items per group
     items_.clear();
     for (Group &G : groups_) {
-        int max_w = 3, max_t = 1;
+        int max_w = 3, max_t = 1, max_h = 3;
         for (int j = G.job_begin; j < G.job_end; ++j) {
             max_w = std::max(max_w, 2 * jobs_[j].rx + 1);
             max_t = std::max(max_t, jobs_[j].n_targets);
+            max_h = std::max(max_h, jobs_[j].H);
         }
         const GatherParams &g0 = jobs_[G.job_begin];
-        G.tiled = tiled_shape(G.kind, tmpl_.elem_bytes, G.gdx, G.gdy, max_w, spec_.bins, g0.nl, max_t, G.want_tx,
+        // regions taller than the tiled gather's row range take the direct gather
+        G.tiled = max_h <= kTiledMaxRows &&
+                  tiled_shape(G.kind, tmpl_.elem_bytes, G.gdx, G.gdy, max_w, spec_.bins, g0.nl, max_t, G.want_tx,
                               G.want_stages, G.want_bb, true, &G.shape) == cudaSuccess;
         G.items_off = (int)items_.size();
         long long items = 0;

@@ -115,6 +115,22 @@ def test_mixed_regions_match_oracle(layout):
         check_against_oracle(img, 12, 24, specs)
 
 
+def test_bands_taller_than_64_rows_store_every_row():
+    """Work sets store only the rows that hold each bin when bands are at most
+    64 rows; with 65-row bands they store every row (no row maps). Both paths
+    match the oracle on the same regions."""
+    img = synth.blob_scene(200, 400, 8, seed=9, n_blobs=6, margin=10).image
+    for band_rows in (65, 16):
+        specs = [Spec(*r) for r in MIXED]
+        batch, buf, _ptr = make_batch(img, 8, 16, ("plain", "manhattan", "euclidean", "gaussian"), specs,
+                                      band_rows=band_rows)
+        with batch:
+            batch.run()
+            batch.sync_status()
+        torch.cuda.synchronize()
+        check_against_oracle(img, 8, 16, specs)
+
+
 def test_batch_equals_single_region_plans():
     img = synth.blob_scene(300, 500, 8, seed=5, n_blobs=5, margin=40).image
     specs = [Spec(0, 0, 200, 150, "manhattan", [(21, 21), (41, 41)]),

@@ -434,6 +434,19 @@ def test_rows_left_from_an_earlier_build_are_never_read():
         S.swih_debug_inject(plan.handle, 0)
 
 
+def test_plans_taller_than_32767_rows_store_every_row():
+    """The gathers keep stored rows as int16, so a plan of more than 32767 rows
+    stores every row and has no row map; it still matches the oracle."""
+    img = synth.blob_scene(32800, 24, 8, seed=13, n_blobs=40, axes=(3, 9), margin=4).image
+    plan, _buf = make_plan(img, 8, 4, ("manhattan", "gaussian"), (5, 9))
+    with plan:
+        info = plan.info()
+        assert not info.d_row_map
+        bins = check_ih(plan, img, 8, 4)
+        check_windows(plan, bins, 4, "manhattan", 5, 9)
+        check_windows(plan, bins, 4, "gaussian", 5, 5)
+
+
 def test_gather_counts_the_bytes_it_loads():
     """The tiled gather reports the integral-histogram bytes it requested: on
     uniform noise (every bin in every window) at least the dense bytes of its
