@@ -19,7 +19,8 @@
 //
 // A chain is (bin b, y side s); both x sides share its C. Three launches:
 //  1. exp_band_agg_kernel: per (chain, band, column), C at the band's last row
-//     (scan order) with nothing carried in.
+//     (scan order) with nothing carried in, as a sum of table powers q^d over the
+//     rows that hold the bin; and the band's mask of such rows.
 //  2. exp_band_carry_kernel: per (chain, column), the value carried into each
 //     band, sequentially over the bands: c_{k+1} = agg_k + q^band_rows c_k,
 //     written over the aggregates.
@@ -27,7 +28,7 @@
 //     the carry, then for each x side a block-wide scan of the linear
 //     recurrence (thread-serial over E columns, warp shuffles with q^(E d),
 //     warp totals through shared memory with q^(32 E d)); each row of J leaves
-//     as 16-byte stores.
+//     as 16-byte stores. A row without the bin is q times the row above.
 // No block waits on another.
 #include "swih_internal.h"
 
@@ -81,23 +82,45 @@ __device__ __forceinline__ unsigned match_bits(const uint8_t *row, int x0, int W
 
 __global__ void __launch_bounds__(256) exp_band_agg_kernel(const ExpScanParams p)
 {
+    // the band's C at its last row is a sum of powers q^d over the rows holding
+    // the bin (d = rows after it); bands of up to 64 rows read them from a table
+    __shared__ unsigned long long s_qrow[65];
+    __shared__ unsigned long long s_rows;
     const int nchain = 2 * p.B;
     const int chain = blockIdx.x % nchain, band = blockIdx.x / nchain;
     const int side = chain / p.B, b = chain - side * p.B;
     const int r0 = band * p.band_rows, r1 = min(r0 + p.band_rows, p.H);
+    const bool table = p.band_rows <= 64;
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) s_qrow[i] = p.qrow[i];
+    if (threadIdx.x == 0) s_rows = 0ull;
+    __syncthreads();
+    unsigned long long mine = 0ull;  // rows (first 64 of the band) where the thread's columns hold the bin
     u64 *out = p.carry + ((int64_t)chain * p.n_bands + band) * p.pitch;
     for (int x0 = 4 * threadIdx.x; x0 < p.W; x0 += 4 * blockDim.x) {
         u64 a[4] = {0, 0, 0, 0};
         for (int r = r0; r < r1; ++r) {
             const int y = side ? p.H - 1 - r : r;
             const unsigned m = match_bits<4>(p.bins + (int64_t)y * p.bins_pitch, x0, p.W, b);
+            if (table) {
+                if (m) {
+                    mine |= 1ull << (r - r0);
+                    const u64 w = s_qrow[r1 - 1 - r];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = mulq(a[i], p.q1) + (((m >> i) & 1u) ? p.one : 0ull);
+                    for (int i = 0; i < 4; ++i)
+                        if ((m >> i) & 1u) a[i] += w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = mulq(a[i], p.q1) + (((m >> i) & 1u) ? p.one : 0ull);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (x0 + i < p.W) out[x0 + i] = a[i];
     }
+    if (mine) atomicOr(&s_rows, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) p.rows[(int64_t)chain * p.n_bands + band] = table ? s_rows : ~0ull;
 }
 
 __global__ void __launch_bounds__(256) exp_band_carry_kernel(const ExpScanParams p)
@@ -129,7 +152,7 @@ __device__ __forceinline__ void store_row(u64 *dst, int x0, int64_t pitch, int W
 }
 
 template <int E>
-__global__ void __launch_bounds__(512) exp_scan_kernel(const ExpScanParams p)
+__global__ void __launch_bounds__(512, 1) exp_scan_kernel(const ExpScanParams p)
 {
     // [row parity][x side][warp]: warp totals, then their scan across warps
     __shared__ u64 s_warp[2][2][16];
@@ -149,9 +172,32 @@ __global__ void __launch_bounds__(512) exp_scan_kernel(const ExpScanParams p)
     u64 *Jf = p.J + ((int64_t)(2 * side) * p.B + b) * p.plane;      // x side 0 (x' <= x)
     u64 *Jr = p.J + ((int64_t)(2 * side + 1) * p.B + b) * p.plane;  // x side 1 (x' >= x)
 
+    // A row without the bin has C = q C(row above), hence both rows of J are q
+    // times the rows above: with up to 8 columns per thread they are formed from
+    // the previous row's outputs, kept in registers, with no scan and no barrier
+    // (uniform over the block: the band's row mask comes from the aggregate pass).
+    constexpr bool kDecay = E <= 8;
+    const unsigned long long rmask = p.rows[(int64_t)chain * p.n_bands + band];
+    u64 outf[E], outr[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) outf[i] = outr[i] = 0;
+
     for (int r = r0; r < r1; ++r) {
         const int y = side ? p.H - 1 - r : r;
         const int par = (r - r0) & 1;
+        if constexpr (kDecay) {
+            if (r > r0 && r - r0 < 64 && !((rmask >> (r - r0)) & 1ull)) {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    C[i] = mulq(C[i], p.q1);
+                    outf[i] = mulq(outf[i], p.q1);
+                    outr[i] = mulq(outr[i], p.q1);
+                }
+                store_row<E>(Jf + (int64_t)y * p.pitch, x0, p.pitch, p.W, outf);
+                store_row<E>(Jr + (int64_t)y * p.pitch, x0, p.pitch, p.W, outr);
+                continue;
+            }
+        }
         const unsigned m = match_bits<E>(p.bins + (int64_t)y * p.bins_pitch, x0, p.W, b);
 #pragma unroll
         for (int i = 0; i < E; ++i) C[i] = mulq(C[i], p.q1) + (((m >> i) & 1u) ? p.one : 0ull);
@@ -199,21 +245,20 @@ __global__ void __launch_bounds__(512) exp_scan_kernel(const ExpScanParams p)
         const u64 Xf = lane == 0 ? Pf : pf + mulq(Pf, p.qe[lane]);
         const u64 Xr = lane == 31 ? Pr : pr + mulq(Pr, p.qe[31 - lane]);
 
-        u64 out[E];
         u64 s = Xf;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             s = C[i] + mulq(s, p.q1);
-            out[i] = s;
+            outf[i] = s;
         }
-        store_row<E>(Jf + (int64_t)y * p.pitch, x0, p.pitch, p.W, out);
+        store_row<E>(Jf + (int64_t)y * p.pitch, x0, p.pitch, p.W, outf);
         s = Xr;
 #pragma unroll
         for (int i = E - 1; i >= 0; --i) {
             s = C[i] + mulq(s, p.q1);
-            out[i] = s;
+            outr[i] = s;
         }
-        store_row<E>(Jr + (int64_t)y * p.pitch, x0, p.pitch, p.W, out);
+        store_row<E>(Jr + (int64_t)y * p.pitch, x0, p.pitch, p.W, outr);
     }
 }
 

@@ -285,6 +285,7 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     if (want_exp) {
         pl->off_exp = take((uint64_t)4 * d->bins * pl->plane * sizeof(unsigned long long));
         pl->off_exp_carry = take((uint64_t)2 * d->bins * pl->n_bands * pl->ih_pitch * sizeof(unsigned long long));
+        pl->off_exp_rows = take((uint64_t)2 * d->bins * pl->n_bands * sizeof(unsigned long long));
     }
     take(sizeof(uint32_t) * 64);  // status word
     pl->total = off;
@@ -674,6 +675,9 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
         const long double lam = pl->exp_lambda;
         xp.q1 = exp_pow_fixed(lam, 1);
         xp.qband = exp_pow_fixed(lam, pl->band_rows);
+        xp.rows = reinterpret_cast<unsigned long long *>(pl->d_mem + pl->off_exp_rows);
+        xp.qrow[0] = xp.one;
+        for (int k = 1; k <= 64; ++k) xp.qrow[k] = exp_pow_fixed(lam, k) >> (64 - pl->exp_F);
         for (int k = 1; k <= 32; ++k) xp.qe[k] = exp_pow_fixed(lam, (long double)xp.E * k);
         for (int k = 1; k <= 16; ++k) xp.qw[k] = exp_pow_fixed(lam, 32.0L * xp.E * k);
         e = launch_exp_scan(xp, s);

@@ -41,7 +41,7 @@ struct swih_plan_s {
     double exp_lambda = 0.1;
     int exp_F = 0;
     int exp_E = 8, exp_threads = 32;  // exponential scan: columns per thread, threads per block
-    uint64_t off_exp = 0, off_exp_carry = 0;
+    uint64_t off_exp = 0, off_exp_carry = 0, off_exp_rows = 0;
     char *d_mem = nullptr;
     uint32_t *d_status = nullptr;
     int device = 0;

@@ -125,6 +125,8 @@ struct ExpScanParams {
     unsigned long long *J;     // planes [d][b][H][pitch], d = x side + 2 y side
     int64_t pitch, plane;      // elements
     unsigned long long *carry; // [s][b][band][pitch]: band aggregates, then carries into bands
+    unsigned long long *rows;  // [s][b][band]: bit r = the band's r-th row in scan order holds bin b
+    unsigned long long qrow[65]; // floor(q^d 2^F) = one * q^d, d = 0..64 (band aggregates)
     int H, W, B;
     int band_rows, n_bands;
     int E, threads;            // columns per scan thread, threads per block
