@@ -186,6 +186,7 @@ def run_swih(args, rank, world, local_rank):
     info_g = plan_g.info() if plan_g else None
 
     jobs = [(k, w) for k in kernels for w in WINDOWS]
+    job_of = {k: [j for j, (kk, _) in enumerate(jobs) if kk == k] for k in kernels}
     # targets: the window of each kernel and size centred on object 0 (untimed set-up)
     for pl in plans:
         pl.build_ih(d_img, stream)
@@ -207,12 +208,14 @@ def run_swih(args, rank, world, local_rank):
             plan_g.build_ih(d_img, stream)
         if ev is not None:
             ev[2].record(stream)
-        for j, (k, w) in enumerate(jobs):
-            plan_of[k].likelihood(k, w, w, targets[j], maps[j], stream)
+        for ki, k in enumerate(kernels):  # the kernel's windows in one launch (multi-scale search)
+            js = job_of[k]
+            plan_of[k].likelihood_scales(k, [(jobs[j][1], jobs[j][1]) for j in js], [targets[j] for j in js],
+                                         [maps[j] for j in js], stream)
             if ev is not None:
-                ev[3 + j].record(stream)
+                ev[3 + ki].record(stream)
 
-    n_ev = 3 + len(jobs)
+    n_ev = 3 + len(kernels)
     for _ in range(args.warmup):
         step()
     for pl in plans:
@@ -251,14 +254,14 @@ def run_swih(args, rank, world, local_rank):
 
     # per-launch durations inside the timed region
     seg = {"build_me": [], "build_g": []}
-    for j in range(len(jobs)):
-        seg[f"gather_{jobs[j][0]}_{jobs[j][1]}"] = []
+    for k in kernels:
+        seg[f"gather_{k}"] = []  # one launch: the kernel's three windows
     for s in range(args.steps):
         ev = events[s]
         seg["build_me"].append(ev[0].elapsed_time(ev[1]))
         seg["build_g"].append(ev[1].elapsed_time(ev[2]))
-        for j in range(len(jobs)):
-            seg[f"gather_{jobs[j][0]}_{jobs[j][1]}"].append(ev[2 + j].elapsed_time(ev[3 + j]))
+        for ki, k in enumerate(kernels):
+            seg[f"gather_{k}"].append(ev[2 + ki].elapsed_time(ev[3 + ki]))
     seg_ms = {k: float(np.mean(v)) for k, v in seg.items()}
 
     # algorithmic bytes per launch
@@ -271,15 +274,15 @@ def run_swih(args, rank, world, local_rank):
         "build_g": 2 * H * W + ih_bytes(info_g, info_g.n_terms) if info_g else 0,
     }
     used_terms = {"manhattan": 3, "euclidean": 5, "gaussian": info_g.n_terms if info_g else 0}
-    for (k, w) in jobs:
-        algo[f"gather_{k}_{w}"] = (ih_bytes(info_g if k == "gaussian" else info_me, used_terms[k])
-                                   + 4 * (H - w + 1) * (W - w + 1))
+    for k in kernels:  # each window reads the kernel's planes once, and writes its map
+        algo[f"gather_{k}"] = sum(ih_bytes(info_g if k == "gaussian" else info_me, used_terms[k])
+                                  + 4 * (H - w + 1) * (W - w + 1) for w in WINDOWS)
     # dominant kernel class by total time per step
     classes = {"ih_scan (Gaussian plan, 64-bit ring)": ["build_g"],
                "ih_scan (Manhattan+Euclidean plan, 32-bit ring)": ["build_me"],
-               "gather Gaussian": [f"gather_gaussian_{w}" for w in WINDOWS],
-               "gather Euclidean": [f"gather_euclidean_{w}" for w in WINDOWS],
-               "gather Manhattan": [f"gather_manhattan_{w}" for w in WINDOWS]}
+               "gather Gaussian": ["gather_gaussian"],
+               "gather Euclidean": ["gather_euclidean"],
+               "gather Manhattan": ["gather_manhattan"]}
     totals = {c: sum(seg_ms.get(k, 0.0) for k in ks) for c, ks in classes.items()}
     dom = max(totals, key=totals.get)
     dom_keys = classes[dom]
@@ -290,9 +293,8 @@ def run_swih(args, rank, world, local_rank):
     if dom == "gather Gaussian" and loaded_g:
         # the gather skips bins and rows absent from its windows: its algorithmic
         # bytes are the row segments it must load (counted by the kernel) + the map
-        n_g = args.steps * sum(1 for k in jobs if k[0] == "gaussian")
-        maps_b = float(np.mean([4 * (H - w + 1) * (W - w + 1) for w in WINDOWS]))
-        dom_bytes = loaded_g / n_g + maps_b
+        maps_b = float(sum(4 * (H - w + 1) * (W - w + 1) for w in WINDOWS))
+        dom_bytes = loaded_g / args.steps + maps_b  # one launch per step: the three windows
         basis = ("integral-histogram row segments the sparse gather loads (rows of windows holding "
                  "each bin, counted by the kernel over the timed launches) + the map")
     dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
@@ -321,7 +323,7 @@ def run_swih(args, rank, world, local_rank):
     d_maps = [maps, [torch.empty_like(m) for m in maps]]
     ev_in = [torch.cuda.Event() for _ in range(2)]      # set i uploaded
     ev_used = [torch.cuda.Event() for _ in range(2)]    # kernels done reading set i's inputs
-    ev_map = [[torch.cuda.Event() for _ in jobs] for _ in range(2)]  # map j of set i written
+    ev_map = [[torch.cuda.Event() for _ in jobs] for _ in range(2)]  # map j of set i written (its kernel's launch)
     ev_out = [[torch.cuda.Event() for _ in jobs] for _ in range(2)]  # map j of set i downloaded
     for i in range(2):  # nothing pending yet
         ev_used[i].record(stream)
@@ -339,10 +341,14 @@ def run_swih(args, rank, world, local_rank):
         stream.wait_event(ev_in[i])
         for pl in plans:
             pl.build_ih(d_imgs[i], stream)
-        for j, (k, w) in enumerate(jobs):
-            stream.wait_event(ev_out[i][j])
-            plan_of[k].likelihood(k, w, w, d_tgts[i][j], d_maps[i][j], stream)
-            ev_map[i][j].record(stream)
+        for k in kernels:
+            js = job_of[k]
+            for j in js:
+                stream.wait_event(ev_out[i][j])
+            plan_of[k].likelihood_scales(k, [(jobs[j][1], jobs[j][1]) for j in js], [d_tgts[i][j] for j in js],
+                                         [d_maps[i][j] for j in js], stream)
+            for j in js:
+                ev_map[i][j].record(stream)
         ev_used[i].record(stream)
         with torch.cuda.stream(copy):
             for j in range(len(jobs)):

@@ -166,6 +166,24 @@ swih_status swih_local_hist(swih_plan_t plan, int kernel, int win_w, int win_h, 
 swih_status swih_likelihood(swih_plan_t plan, int kernel, int win_w, int win_h,
                             const float *d_target, float *d_map, void *stream);
 
+/* Multi-scale search: swih_likelihood for n_windows windows of one kernel
+ * (1..SWIH_MAX_SCALES), map i for window win_w[i] x win_h[i] against target
+ * d_targets[i] (float32 [B]) into d_maps[i] (float32 [H-win_h[i]+1][W-win_w[i]+1]).
+ * win_w, win_h, d_targets and d_maps are host arrays (of device pointers for
+ * the last two). The windows of the tiled kernels run as one launch over a job
+ * table in the plan (the launch's last wave is a small part of it), which is
+ * uploaded with cudaMemcpyAsync on the stream from host memory, so this call
+ * cannot be captured into a CUDA graph; the wedding cake, the exponential
+ * kernel and Gaussian windows of different fitted degrees run one launch per
+ * window. Results equal those of n_windows calls of swih_likelihood up to
+ * float rounding (a single-window call may split its bins over CTA groups and
+ * add their partial sums in another order). Calls on one plan must not overlap
+ * on the GPU (the job table is shared). */
+#define SWIH_MAX_SCALES 8
+swih_status swih_likelihood_scales(swih_plan_t plan, int kernel, int n_windows, const int *win_w,
+                                   const int *win_h, const float *const *d_targets, float *const *d_maps,
+                                   void *stream);
+
 /* Wait for the stream, then report the first device-side error the plan
  * recorded since the last call (SWIH_ERR_TIMEOUT) and clear it. */
 swih_status swih_sync_status(swih_plan_t plan, void *stream);
@@ -236,8 +254,6 @@ swih_status swih_plan_load_bytes(swih_plan_t plan, uint64_t *bytes, int reset);
  * search problem (Sec. 1, Sec. 4: likelihood maps for many candidate regions)
  * run for many targets at once; the paper itself processes one region at a
  * time. */
-#define SWIH_MAX_SCALES 8
-
 typedef struct swih_batch_desc {
     int32_t height;            /* frame rows */
     int32_t width;             /* frame columns */

@@ -684,8 +684,22 @@ constexpr auto single_kernel()
 // A table of jobs sharing one shape: one CTA per work item, items of job j
 // numbered from item_start[j] with the column tiles fastest.
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
+__device__ __forceinline__ void gather_table_body(const GatherParams *__restrict__ jobs,
+                                                  const int *__restrict__ item_start, int n_jobs);
+
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
 __global__ void __launch_bounds__(TX + 32)
     gather_table_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs)
+{
+    gather_table_body<KIND, T, TX, DX, DY, BB>(jobs, item_start, n_jobs);
+}
+
+// The table kernel's body, and its instantiations with the same register
+// bounds as the single-job kernels (the 128-column Gaussian for 5 resident CTAs,
+// the 256-column 32-bit Manhattan and Euclidean for 4).
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
+__device__ __forceinline__ void gather_table_body(const GatherParams *__restrict__ jobs,
+                                                  const int *__restrict__ item_start, int n_jobs)
 {
     const int item = blockIdx.x;
     int lo = 0, hi = n_jobs - 1;  // the last job whose first item is <= item
@@ -697,6 +711,32 @@ __global__ void __launch_bounds__(TX + 32)
     const int li = item - item_start[lo];
     const int tiles = (p.ncx + TX - 1) / TX;
     gather_tiled_body<KIND, T, TX, DX, DY, BB, false, true>(p, li % tiles, li / tiles, 0);
+}
+
+template <typename T, int DX, int DY>
+__global__ void __launch_bounds__(128 + 32, 5)
+    gather_table_gauss128_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs)
+{
+    gather_table_body<kGatherGaussian, T, 128, DX, DY, 1>(jobs, item_start, n_jobs);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256 + 32, 4)
+    gather_table_me256_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs)
+{
+    gather_table_body<KIND, uint32_t, 256, 0, 0, 4>(jobs, item_start, n_jobs);
+}
+
+template <int KIND, typename T, int TX, int DX, int DY, int BB>
+constexpr auto table_kernel()
+{
+    if constexpr (KIND == kGatherGaussian && TX == 128 && BB == 1)
+        return gather_table_gauss128_kernel<T, DX, DY>;
+    else if constexpr ((KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && BB == 4 &&
+                       sizeof(T) == 4)
+        return gather_table_me256_kernel<KIND>;
+    else
+        return gather_table_kernel<KIND, T, TX, DX, DY, BB>;
 }
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
@@ -734,7 +774,7 @@ cudaError_t run_op(TiledOp &op)
         return cudaGetLastError();
     }
     case TiledOp::kTable: {
-        auto fn = gather_table_kernel<K, T, TX, DX, DY, BB>;
+        auto fn = table_kernel<K, T, TX, DX, DY, BB>();
         cudaError_t e = set_smem(fn, op.sh->smem);
         if (e != cudaSuccess) return e;
         fn<<<(unsigned)op.n_items, TX + 32, op.sh->smem, op.s>>>(op.d_jobs, op.d_items, op.n_jobs);

@@ -287,6 +287,7 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         pl->off_exp_carry = take((uint64_t)2 * d->bins * pl->n_bands * pl->ih_pitch * sizeof(unsigned long long));
         pl->off_exp_rows = take((uint64_t)2 * d->bins * pl->n_bands * sizeof(unsigned long long));
     }
+    pl->off_jobs = take(sizeof(GatherParams) * SWIH_MAX_SCALES + sizeof(int) * (SWIH_MAX_SCALES + 1));
     take(sizeof(uint32_t) * 64);  // status word
     pl->total = off;
     if (d->hbm_budget_bytes && pl->total > d->hbm_budget_bytes) {
@@ -745,6 +746,76 @@ swih_status swih_likelihood(swih_plan_t pl, int kernel, int win_w, int win_h, co
     g.target = d_target;
     g.map = d_map;
     const cudaError_t e = run_gather(pl, g, kind, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(pl, "gather launch", e);
+    return SWIH_OK;
+}
+
+swih_status swih_likelihood_scales(swih_plan_t pl, int kernel, int n_windows, const int *win_w, const int *win_h,
+                                   const float *const *d_targets, float *const *d_maps, void *stream)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    if (n_windows < 1 || n_windows > SWIH_MAX_SCALES)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "n_windows must be in [1, SWIH_MAX_SCALES]");
+    if (!win_w || !win_h || !d_targets || !d_maps)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "win_w, win_h, d_targets and d_maps are required");
+    for (int i = 0; i < n_windows; ++i) {
+        const swih_status st = check_window(pl, kernel, win_w[i], win_h[i]);
+        if (st != SWIH_OK) return st;
+        if (!d_targets[i] || !d_maps[i]) return fail(pl, SWIH_ERR_INVALID_ARG, "a target or map is NULL");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto one_by_one = [&]() -> swih_status {
+        for (int i = 0; i < n_windows; ++i) {
+            const swih_status st = swih_likelihood(pl, kernel, win_w[i], win_h[i], d_targets[i], d_maps[i], stream);
+            if (st != SWIH_OK) return st;
+        }
+        return SWIH_OK;
+    };
+    const bool tiled_kind = kernel == SWIH_KERNEL_PLAIN || kernel == SWIH_KERNEL_MANHATTAN ||
+                            kernel == SWIH_KERNEL_EUCLIDEAN || kernel == SWIH_KERNEL_GAUSSIAN;
+    if (n_windows == 1 || !tiled_kind || pl->gather_path == 1 || pl->desc.height > kTiledMaxRows)
+        return one_by_one();
+    GatherParams jobs[SWIH_MAX_SCALES];
+    int kind = 0, max_w = 3;
+    for (int i = 0; i < n_windows; ++i) {
+        int k = 0;
+        const swih_status st = make_gather(pl, kernel, win_w[i], win_h[i], jobs[i], k);
+        if (st != SWIH_OK) return st;
+        if (i > 0 && (jobs[i].gdx != jobs[0].gdx || jobs[i].gdy != jobs[0].gdy)) return one_by_one();
+        kind = k;
+        jobs[i].cx0 = (win_w[i] - 1) / 2;
+        jobs[i].cy0 = (win_h[i] - 1) / 2;
+        jobs[i].ncx = pl->desc.width - win_w[i] + 1;
+        jobs[i].ncy = pl->desc.height - win_h[i] + 1;
+        jobs[i].target = d_targets[i];
+        jobs[i].map = d_maps[i];
+        jobs[i].nbg = 1;
+        max_w = std::max(max_w, win_w[i]);
+    }
+    GatherShape sh;
+    if (tiled_shape(kind, pl->elem_bytes, jobs[0].gdx, jobs[0].gdy, max_w, pl->desc.bins, jobs[0].nl, 1,
+                    jobs[0].want_tx, jobs[0].want_stages, jobs[0].want_bb, true, &sh) != cudaSuccess) {
+        cudaGetLastError();
+        return one_by_one();
+    }
+    int start[SWIH_MAX_SCALES + 1];
+    long long total = 0;
+    for (int i = 0; i < n_windows; ++i) {
+        start[i] = (int)total;
+        total += tiled_items(&jobs[i], sh);
+        if (total > 0x7fffffffLL) return one_by_one();
+    }
+    start[n_windows] = (int)total;
+    // job table, then the item starts, uploaded on the stream (stream-ordered)
+    unsigned char host[sizeof(GatherParams) * SWIH_MAX_SCALES + sizeof(int) * (SWIH_MAX_SCALES + 1)];
+    std::memcpy(host, jobs, sizeof(GatherParams) * n_windows);
+    std::memcpy(host + sizeof(GatherParams) * SWIH_MAX_SCALES, start, sizeof(int) * (n_windows + 1));
+    char *d_tab = pl->d_mem + pl->off_jobs;
+    cudaError_t e = cudaMemcpyAsync(d_tab, host, sizeof host, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(pl, "cudaMemcpyAsync(job table)", e);
+    e = launch_gather_table(reinterpret_cast<const GatherParams *>(d_tab),
+                            reinterpret_cast<const int *>(d_tab + sizeof(GatherParams) * SWIH_MAX_SCALES), n_windows,
+                            (int)total, jobs[0], kind, pl->elem_bytes, jobs[0].gdx, jobs[0].gdy, sh, s);
     if (e != cudaSuccess) return cuda_fail(pl, "gather launch", e);
     return SWIH_OK;
 }

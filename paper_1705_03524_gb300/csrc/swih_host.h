@@ -35,6 +35,7 @@ struct swih_plan_s {
     // (bin, row)'s last stored row
     bool sparse_rows = false;
     uint64_t off_occ = 0, off_row_map = 0;
+    uint64_t off_jobs = 0;  // job table of swih_likelihood_scales (SWIH_MAX_SCALES jobs + item starts)
     // exponential kernel: decay per pixel, fixed-point fraction bits, the four
     // directional integral histograms and the scan's band carries
     bool has_exp = false;

@@ -217,6 +217,9 @@ def _load() -> ctypes.CDLL:
     lib.swih_local_hist.restype = S
     lib.swih_likelihood.argtypes = [P, I, I, I, P, P, P]
     lib.swih_likelihood.restype = S
+    lib.swih_likelihood_scales.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(P),
+                                           ctypes.POINTER(P), P]
+    lib.swih_likelihood_scales.restype = S
     lib.swih_sync_status.argtypes = [P, P]
     lib.swih_sync_status.restype = S
     lib.swih_destroy.argtypes = [P]
@@ -363,6 +366,16 @@ def swih_likelihood(plan: int, kernel: int, win_w: int, win_h: int, target, out_
                                _stream(stream)), plan)
 
 
+def swih_likelihood_scales(plan: int, kernel: int, windows, targets, maps, stream=None) -> None:
+    """windows: [(w, h), ...]; targets, maps: device tensors or pointers, one per window."""
+    n = len(windows)
+    ww = (ctypes.c_int * n)(*[int(w) for w, _ in windows])
+    wh = (ctypes.c_int * n)(*[int(h) for _, h in windows])
+    tg = (ctypes.c_void_p * n)(*[_ptr(t) for t in targets])
+    mp = (ctypes.c_void_p * n)(*[_ptr(m) for m in maps])
+    _check(LIB.swih_likelihood_scales(plan, int(kernel), n, ww, wh, tg, mp, _stream(stream)), plan)
+
+
 def swih_sync_status(plan: int, stream=None) -> None:
     _check(LIB.swih_sync_status(plan, _stream(stream)), plan)
 
@@ -434,6 +447,10 @@ class Plan:
     def likelihood(self, kernel, win_w, win_h, target, out_map, stream=None):
         k = KERNELS[kernel] if isinstance(kernel, str) else kernel
         swih_likelihood(self.handle, k, win_w, win_h, target, out_map, stream)
+
+    def likelihood_scales(self, kernel, windows, targets, maps, stream=None):
+        k = KERNELS[kernel] if isinstance(kernel, str) else kernel
+        swih_likelihood_scales(self.handle, k, windows, targets, maps, stream)
 
     def sync_status(self, stream=None):
         swih_sync_status(self.handle, stream)

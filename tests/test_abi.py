@@ -116,6 +116,10 @@ def test_exponential_workspace_layout():
     assert both - man >= planes
 
 
+def test_scales_call_validates_on_the_host():
+    assert S.LIB.swih_likelihood_scales(None, 1, 1, None, None, None, None, None) == S.SWIH_ERR_INVALID_ARG
+
+
 def test_noalloc_build_refuses_the_exponential_kernel():
     # refused on the host, before any device memory is touched
     d = _desc(kernels=("exponential",))

@@ -447,6 +447,38 @@ def test_plans_taller_than_32767_rows_store_every_row():
         check_windows(plan, bins, 4, "gaussian", 5, 5)
 
 
+def test_scales_in_one_launch_equal_single_windows():
+    """swih_likelihood_scales runs the windows of a tiled kernel as one table
+    launch (and the others one window at a time); every map equals the
+    single-window call up to float rounding, and matches the oracle."""
+    img = synth.blob_scene(160, 230, 8, seed=17, n_blobs=5, margin=20).image
+    B = 16
+    kinds = ("plain", "manhattan", "euclidean", "gaussian", "wedding", "exponential")
+    plan, _buf = make_plan(img, 8, B, kinds, (81, 81))
+    bins = oracle_bins(img, 8, B)
+    windows = [(21, 21), (41, 31), (81, 81), (9, 15), (3, 3)]  # 3 x 3: the Gaussian's fitted degree drops
+    with plan:
+        for kind in kinds:
+            targets, singles, multis = [], [], []
+            for i, (w, h) in enumerate(windows):
+                K = O.kernel_weights(kind, w, h)
+                x0, y0, nx, ny = O.valid_centres(160, 230, w, h)
+                q = O.target_hist(bins, B, K, x0 + (7 * i) % nx, y0 + (5 * i) % ny)
+                targets.append(torch.tensor(q, dtype=torch.float32, device=DEV))
+                singles.append(torch.empty((ny, nx), device=DEV))
+                multis.append(torch.full((ny, nx), -1.0, device=DEV))
+                plan.likelihood(kind, w, h, targets[i], singles[i])
+            plan.likelihood_scales(kind, windows, targets, multis)
+            plan.sync_status()
+            for (w, h), a, b in zip(windows, singles, multis):
+                assert (a - b).abs().max().item() <= 1e-6, (kind, w, h)
+            K = O.kernel_weights(kind, 41, 31)
+            err = np.abs(multis[1].cpu().numpy() - O.likelihood_map(bins, B, K, targets[1].cpu().numpy())).max()
+            assert err <= TOL, (kind, err)
+        with pytest.raises(S.SwihError):
+            plan.likelihood_scales("manhattan", [(21, 21)] * 9, [targets[0]] * 9, [multis[0]] * 9)
+
+
 def test_gather_counts_the_bytes_it_loads():
     """The tiled gather reports the integral-histogram bytes it requested: on
     uniform noise (every bin in every window) at least the dense bytes of its
