@@ -152,7 +152,7 @@ __device__ __forceinline__ void store_row(u64 *dst, int x0, int64_t pitch, int W
 }
 
 template <int E>
-__global__ void __launch_bounds__(512, 1) exp_scan_kernel(const ExpScanParams p)
+__global__ void __launch_bounds__(512) exp_scan_kernel(const ExpScanParams p)
 {
     // [row parity][x side][warp]: warp totals, then their scan across warps
     __shared__ u64 s_warp[2][2][16];

@@ -188,9 +188,9 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         const long double q = expl(-(long double)lam);
         const long double jmax = 1.0L / ((1.0L - q) * (1.0L - q));
         pl->exp_F = 60 - (int)ceill(log2l(jmax));
-        // 8 columns per scan thread (16 above 4096 columns): the block-wide scan's
-        // per-thread steps are spread over more pixels than the integer scan's 4
-        pl->exp_E = d->width > 4096 ? 16 : 8;
+        // columns per scan thread: 4 up to 2048 columns (more warps per CTA hide
+        // the latency of the rows that are scanned), 8 up to 4096, 16 above
+        pl->exp_E = d->width > 4096 ? 16 : (d->width > 2048 ? 8 : 4);
         pl->exp_threads = (int)round_up((d->width + pl->exp_E - 1) / pl->exp_E, 32);
     }
     bool mark[5][5] = {};

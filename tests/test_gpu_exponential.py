@@ -42,6 +42,7 @@ CASES = [
     (64, 200, False, 64, 4.0, [(3, 3), (25, 25)], 1, True),
     (50, 96, True, 32, 1.0 / 1024, [(7, 7), (95, 49)], 0, False),
     (37, 160, False, 12, 16.0, [(3, 5), (31, 31)], 0, True),
+    (11, 3000, True, 8, 0.2, [(3, 3), (13, 11)], 0, False),
     (9, 4100, False, 16, 0.3, [(3, 3), (9, 9)], 0, False),
     (7, 8192, True, 8, 0.05, [(5, 7), (61, 5)], 0, False),
 ]
