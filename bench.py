@@ -428,12 +428,13 @@ def run_swih(args, rank, world, local_rank):
 
 
 # ----------------------------------------------------------------------------- batches
-def run_regions(args, dev):
+def run_regions(args, dev, per_region=True):
     """64 search regions of 96-768 px from a 4096x4096 u16 frame (B = 64,
     Gaussian, 3 scales): one batch (CUDA graph: one quantise, one scan, one
     gather launch per job group) against one plan per region (its own
     quantise, scan and three gathers), each timed with CUDA events over
-    whole steps."""
+    whole steps. per_region = False leaves out the per-region plans (a short
+    run that profiles the batch alone)."""
     import torch
 
     from paper_1705_03524_gb300 import swih as S
@@ -456,6 +457,9 @@ def run_regions(args, dev):
     # one plan per region; targets = each region's object window at scale 1 (set-up)
     plans = []
     for i, ((x0, y0, w, h), ks, (ox, oy)) in enumerate(zip(rois, wins, cfg["object_centres"])):
+        if not per_region:
+            targets[i].fill_(1.0 / B)
+            continue
         p = S.Plan(S.make_desc(h, w, pitch_bytes=pitch, pixel_type=S.SWIH_PIXEL_U16, bitdepth=16, bins=B,
                                kernels=("gaussian",), max_win=(max(ks), max(ks))))
         p.build_ih(ptr + y0 * pitch + x0 * 2, stream)
@@ -470,15 +474,17 @@ def run_regions(args, dev):
             for k, m in zip(ks, ms):
                 p.likelihood("gaussian", k, k, targets[i], m, stream)
 
-    for _ in range(2):
-        per_roi_step()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        per_roi_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    per_roi_ms = e0.elapsed_time(e1) / steps
+    per_roi_ms = float("nan")
+    if per_region:
+        for _ in range(2):
+            per_roi_step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            per_roi_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_roi_ms = e0.elapsed_time(e1) / steps
     for p in plans:
         p.sync_status(stream)
         p.close()
@@ -503,7 +509,8 @@ def run_regions(args, dev):
         torch.cuda.synchronize()
         b.sync_status(stream)
         batch_ms = e0.elapsed_time(e1) / steps
-    diff = max((m - r).abs().max().item() for ms, rs in zip(maps, ref) for m, r in zip(ms, rs))
+    diff = (max((m - r).abs().max().item() for ms, rs in zip(maps, ref) for m, r in zip(ms, rs))
+            if per_region else None)
     del maps, ref
     torch.cuda.empty_cache()
     return {
@@ -513,9 +520,9 @@ def run_regions(args, dev):
         "batch": {"ms_per_step": batch_ms, "windows_per_s": wps / (batch_ms * 1e-3),
                   "launches_per_step": "1 quantise + 1 scan + 1 gather per job group (graph replay)",
                   "workspace_gb": ws_bytes / 1e9},
-        "per_region_plans": {"ms_per_step": per_roi_ms, "windows_per_s": wps / (per_roi_ms * 1e-3),
+        "per_region_plans": {"ms_per_step": per_roi_ms, "windows_per_s": wps / (per_roi_ms * 1e-3) if per_region else None,
                              "launches_per_step": 6 * len(rois)},
-        "speedup": per_roi_ms / batch_ms,
+        "speedup": per_roi_ms / batch_ms if per_region else None,
         "max_abs_diff_batch_vs_per_region": diff,
     }
 
@@ -914,6 +921,8 @@ def main():
                     help="time per map against window size (SWIH on the GPU vs the brute-force oracle)")
     ap.add_argument("--exp-profile", action="store_true",
                     help="small exponential-kernel run for ncu captures: B = 8, two builds and two w = 41 maps")
+    ap.add_argument("--regions-only", action="store_true",
+                    help="only the batched search-regions measurement (for launch lists of the batch)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "swih":
         args.warmup = 3
@@ -926,6 +935,11 @@ def main():
         return
     if args.exp_profile:
         run_exp_profile()
+        return
+    if args.regions_only:
+        import torch
+        print(json.dumps({"batched_regions": run_regions(args, torch.device("cuda", 0), per_region=False)}),
+              flush=True)
         return
 
     if args.impl == "reference":
