@@ -325,9 +325,10 @@ swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, 
 
 /* Integral-histogram build for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface for hosts whose memory
- * rules forbid cudaMalloc at call time -- code running while a stream is
- * being captured into a CUDA graph, pipelines that give all device memory to a
- * fixed pool at start-up, or allocators that refuse driver allocations later.
+ * rules forbid cudaMalloc at call time -- pipelines that give all device
+ * memory to a fixed pool at start-up, real-time loops that may not take the
+ * device-wide synchronisation a driver allocation can cause, or allocators
+ * that refuse driver allocations after start-up.
  * Such callers cannot create a plan (swih_plan allocates a workspace).
  *
  * Computes exactly what swih_build_ih computes for a plan made from *desc,

@@ -1,10 +1,11 @@
 // swih_build_ih_noalloc: the integral-histogram build for callers that cannot
 // allocate device memory.
 //
-// Some callers may not call cudaMalloc at all: code that runs while a stream is
-// being captured into a CUDA graph, processes that hand all device memory to a
-// fixed pool up front (embedded and real-time tracking pipelines), or hosts
-// whose allocator policy forbids driver allocations after start-up. They can
+// Some callers may not call cudaMalloc at all: processes that hand all device
+// memory to a fixed pool up front (embedded tracking pipelines), real-time loops
+// that may not take the device-wide synchronisation a driver allocation can
+// cause, or hosts whose allocator policy forbids driver allocations after
+// start-up. They can
 // own the input frame and the output integral histograms, but not a plan (which
 // allocates its own workspace). For them this entry point runs the same
 // quantisation and scan kernels with the scan's intermediate data -- the bin

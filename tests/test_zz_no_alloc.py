@@ -1,7 +1,7 @@
 """The allocation-free build (swih_build_ih_noalloc) against the plan build.
 
 swih_build_ih_noalloc serves callers that may not allocate device memory
-(work recorded during CUDA-graph capture, fixed memory pools): it keeps the
+(fixed memory pools, real-time loops that may not synchronise): it keeps the
 scan's scratch in a static device array inside the library and writes the
 integral histograms into memory the caller owns. This test calls it through
 the C ABI twice in a row on two different frames and checks that each result
