@@ -212,18 +212,22 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     unsigned long long my_rows = 0ull;
     if (has_cols) {
         for (int y = y_begin; y < y_end; ++y) {
-            const T yq = ring_pow<T>((T)y, q);
             uint8_t v[E];
             load_bins<E>(r.bins + (int64_t)y * r.bins_pitch, x0, v);
             if (p.sb_rows > 0) put_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
+            bool hit[E];
             bool any = false;
 #pragma unroll
+            for (int e = 0; e < E; ++e) {
+                hit[e] = v[e] == bb && x0 + e < r.W;
+                any |= hit[e];
+            }
+            if (!any) continue;  // y^q only for rows where this thread's columns hold the bin
+            const T yq = ring_pow<T>((T)y, q);
+#pragma unroll
             for (int e = 0; e < E; ++e)
-                if (v[e] == bb && x0 + e < r.W) {
-                    agg[e] += yq;
-                    any = true;
-                }
-            if ((NP <= 3 || RUNS || SPARSE) && any && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
+                if (hit[e]) agg[e] += yq;
+            if ((NP <= 3 || RUNS || SPARSE) && y - y_begin < 64) my_rows |= 1ull << (y - y_begin);
         }
     }
     __syncthreads();  // s_rows cleared
@@ -303,9 +307,23 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
 #pragma unroll
     for (int e = 0; e < E; ++e) cs[e] = carry[e];
     int parity = 0;
+    const unsigned long long rows = s_rows;  // read after the barrier of step 1's publication
+    // the next row the sweep visits: with SPARSE only rows holding a pixel of bin
+    // b (any other row changes no column sum and is not stored; bands are at most
+    // 64 rows, all in the mask), otherwise every row
+    auto next_row = [&](int y) -> int {
+        if constexpr (SPARSE) {
+            const int o = y - y_begin;
+            const unsigned long long m = o < 64 ? rows >> o : 0ull;
+            return m ? y + __ffsll((long long)m) - 1 : y_end;
+        } else {
+            return y;
+        }
+    };
+    const int y_first = next_row(y_begin);
     uint8_t vnext[E];
     const bool cached = p.sb_rows > 0;  // each thread reads back the bins it stored in step 1
-    if (!cached && has_cols && y_begin < y_end) load_bins<E>(r.bins + (int64_t)y_begin * r.bins_pitch, x0, vnext);
+    if (!cached && has_cols && y_first < y_end) load_bins<E>(r.bins + (int64_t)y_first * r.bins_pitch, x0, vnext);
     // Rows without a pixel of bin b leave every column sum, hence every term's
     // row, as in the row above. With up to 3 terms per chain such a row is
     // copied from the row this thread stored last (still in L2) instead of
@@ -317,8 +335,8 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     // (bands of at most 64 rows) an empty row is neither scanned nor stored:
     // readers take the last stored row through the plan's row map.
     constexpr bool kSkip = NP <= 3 && !SPARSE;
-    const unsigned long long rows = s_rows;  // read after the barrier of step 1's publication
-    for (int y = y_begin; y < y_end; ++y) {
+    for (int y = y_first, yn; y < y_end; y = yn) {
+        yn = next_row(y + 1);  // uniform over the block
         if (has_cols) {
             uint8_t v[E];
             if (cached) {
@@ -326,15 +344,12 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = vnext[e];
-                if (y + 1 < y_end) load_bins<E>(r.bins + (int64_t)(y + 1) * r.bins_pitch, x0, vnext);
+                if (yn < y_end) load_bins<E>(r.bins + (int64_t)yn * r.bins_pitch, x0, vnext);
             }
             const T yq = ring_pow<T>((T)y, q);
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (v[e] == bb && x0 + e < r.W) cs[e] += yq;
-        }
-        if constexpr (SPARSE) {
-            if (!((rows >> (y - y_begin)) & 1ull)) continue;  // uniform over the block
         }
         if constexpr (kSkip) {
             const bool holds = y - y_begin >= 64 || ((rows >> (y - y_begin)) & 1ull);
