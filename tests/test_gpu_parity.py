@@ -385,21 +385,27 @@ def test_launch_counter_counts_enqueued_kernels():
     assert c2 - c1 in (1, 2)  # the gather, plus the reduction when the bins were split
 
 
-@pytest.mark.parametrize("pattern", ["stripes", "blobs", "wide_stripes"])
+@pytest.mark.parametrize("pattern", ["stripes", "blobs", "wide_stripes", "uncached_stripes"])
 def test_integral_histograms_with_rows_missing_bins(pattern):
     """Rows that hold no pixel of a bin are not stored by the scan (they are read
     through the plan's row map); check every plane bit for bit where that happens
     often (horizontal stripes of one value, a smooth scene), across several
-    bands (the first row of a band is always computed)."""
-    if pattern in ("stripes", "wide_stripes"):
+    bands (the first row of a band is always computed). With 3000 columns and
+    64-row bands the band's bins do not fit the scan's shared-memory copy, so its
+    sweep prefetches the next row holding the bin from global memory."""
+    band_rows = 6
+    if pattern in ("stripes", "wide_stripes", "uncached_stripes"):
         rng = np.random.default_rng(3)
-        h, w = (67, 90) if pattern == "stripes" else (40, 4200)  # 4200 columns: 16 per scan thread
+        # 4200 columns: 16 per scan thread; 3000: 8 per thread, 64 rows x 3 KB of bins
+        h, w = {"stripes": (67, 90), "wide_stripes": (40, 4200), "uncached_stripes": (150, 3000)}[pattern]
         vals = rng.integers(0, 256, size=h).astype(np.uint8)
         img = np.repeat(vals[:, None], w, axis=1)
         img[::5, ::7] = 255 - img[::5, ::7]  # a few pixels of other bins
+        if pattern == "uncached_stripes":
+            band_rows = 64
     else:
         img = synth.blob_scene(70, 140, 8, seed=4, n_blobs=3, margin=20).image
-    plan, _buf = make_plan(img, 8, 8, ("manhattan", "euclidean", "gaussian"), (9, 9), band_rows=6)
+    plan, _buf = make_plan(img, 8, 8, ("manhattan", "euclidean", "gaussian"), (9, 9), band_rows=band_rows)
     with plan:
         check_ih(plan, img, 8, 8)
         bins = oracle_bins(img, 8, 8)
