@@ -415,13 +415,13 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     const T txc = (T)xc;
 
     // carried values of the previous lattice row, per bin of the block
-    T top[BB][5];
+    T top[BB][4];
     T mid1[BB], midy[BB];
 #pragma unroll
     for (int j = 0; j < BB; ++j) {
         mid1[j] = midy[j] = 0;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) top[j][i] = 0;
+        for (int i = 0; i < 4; ++i) top[j][i] = 0;
     }
     // Gaussian: raw row differences of the previous lattice row (shared memory,
     // one column per thread), and the current window's x-translated Bernstein
@@ -505,60 +505,67 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                                 mid1[j] = zr ? T(0) : (T)(q[i2] - q[i0]);
                                 midy[j] = zr ? T(0) : (T)(q[p.seg + i2] - q[p.seg + i0]);
                             } else {
-                                T d1l = 0, d1r = 0, dxl = 0, dxr = 0, dyf = 0;
+                                // per lattice row, of the left (dx <= 0) and right (dx > 0)
+                                // halves of the window's columns: the count of both (d1),
+                                // right minus left of the count (dd1) and of IH_x (ddx), and
+                                // the full-width IH_y difference (dyf)
+                                T d1 = 0, dd1 = 0, ddx = 0, dyf = 0;
                                 if (!zr) {
                                     const T *q = st + (size_t)(j * 3) * p.seg;
                                     const T a0 = q[i0], a1 = q[i1], a2 = q[i2];
                                     const T *sx = q + p.seg;
                                     const T *sy = q + 2 * p.seg;
-                                    d1l = a1 - a0;
-                                    d1r = a2 - a1;
-                                    dxl = sx[i1] - sx[i0];
-                                    dxr = sx[i2] - sx[i1];
+                                    d1 = a2 - a0;
+                                    dd1 = (a2 + a0) - (a1 + a1);
+                                    ddx = (sx[i2] + sx[i0]) - (sx[i1] + sx[i1]);
                                     dyf = sy[i2] - sy[i0];
                                 }
                                 if (done_k >= 0) {
-                                    const T R1l = d1l - top[j][0], R1r = d1r - top[j][1];
-                                    const T R1 = R1l + R1r;  // pixel count of the bin in the window
+                                    const T R1 = d1 - top[j][0];  // pixel count of the bin in the window
                                     if (R1 != 0) {
                                         const T tyc = (T)(yc0 + done_k * h);
-                                        const T R1t = mid1[j] - (top[j][0] + top[j][1]);
-                                        const T R1b = (d1l + d1r) - mid1[j];
-                                        const T Rxl = dxl - top[j][2], Rxr = dxr - top[j][3];
-                                        const T Ryt = midy[j] - top[j][4], Ryb = dyf - midy[j];
-                                        const T sdx = (Rxr - txc * R1r) - (Rxl - txc * R1l);
+                                        const T R1t = mid1[j] - top[j][0];
+                                        const T R1b = d1 - mid1[j];
+                                        const T Ryt = midy[j] - top[j][3], Ryb = dyf - midy[j];
+                                        // sum over the window of |dx|: right half minus left half of
+                                        // (x - xc); likewise |dy| with the centre row
+                                        const T sdx = (ddx - top[j][2]) - txc * (dd1 - top[j][1]);
                                         const T sdy = (Ryb - tyc * R1b) - (Ryt - tyc * R1t);
                                         const T U = (T)(p.rx + p.ry) * R1 - sdx - sdy;
                                         hval = ring_to_float<T>(U) * p.inv_mass;
                                     }
                                 }
-                                top[j][0] = d1l;
-                                top[j][1] = d1r;
-                                top[j][2] = dxl;
-                                top[j][3] = dxr;
-                                top[j][4] = dyf;
+                                top[j][0] = d1;
+                                top[j][1] = dd1;
+                                top[j][2] = ddx;
+                                top[j][3] = dyf;
                             }
                         } else {  // Euclidean
-                            T d[5] = {0, 0, 0, 0, 0};
+                            // full-width differences of the planes 1, y, y^2 and of
+                            // x^2 - 2 xc x + xc^2 (centred on this thread's column, a
+                            // linear map, so it commutes with the vertical difference)
+                            T d[4] = {0, 0, 0, 0};
                             if (!zr) {
                                 const T *q = st + (size_t)(j * 5) * p.seg;
-#pragma unroll
-                                for (int t = 0; t < 5; ++t) d[t] = q[t * p.seg + i2] - q[t * p.seg + i0];
+                                auto dif = [&](int t) -> T { return q[t * p.seg + i2] - q[t * p.seg + i0]; };
+                                d[0] = dif(0);
+                                d[1] = dif(3) - (T)2 * txc * dif(1) + txc * txc * d[0];
+                                d[2] = dif(2);
+                                d[3] = dif(4);
                             }
                             if (done_k >= 0) {
                                 const T R1 = d[0] - top[j][0];
                                 if (R1 != 0) {
                                     const T tyc = (T)(yc0 + done_k * h);
-                                    const T Rx = d[1] - top[j][1], Ry = d[2] - top[j][2];
-                                    const T Rxx = d[3] - top[j][3], Ryy = d[4] - top[j][4];
-                                    const T sdx2 = Rxx - (T)2 * txc * Rx + txc * txc * R1;
+                                    const T sdx2 = d[1] - top[j][1];
+                                    const T Ry = d[2] - top[j][2], Ryy = d[3] - top[j][3];
                                     const T sdy2 = Ryy - (T)2 * tyc * Ry + tyc * tyc * R1;
                                     const T U = ((T)p.rx * (T)p.rx + (T)p.ry * (T)p.ry) * R1 - sdx2 - sdy2;
                                     hval = ring_to_float<T>(U) * p.inv_mass;
                                 }
                             }
 #pragma unroll
-                            for (int t = 0; t < 5; ++t) top[j][t] = d[t];
+                            for (int t = 0; t < 4; ++t) top[j][t] = d[t];
                         }
                         if (done_k >= 0) {
                             if (p.hist && valid_x) {
