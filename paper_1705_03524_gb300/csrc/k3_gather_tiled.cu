@@ -78,10 +78,13 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         // the Gaussian's long steps want at least three stages (one consumed,
         // two in flight) more than one more resident CTA; the cheap kernels
         // want resident CTAs. Settle for two stages when nothing deeper fits.
+        // the 256-column 32-bit Manhattan/Euclidean table kernel keeps a copy of
+        // its job's parameters past the layout
+        const size_t extra = (!gau && tx == 256 && bb == 4 && elem_bytes == 4) ? sizeof(GatherParams) : 0;
         int ns = 0;
         for (int min_ns = std::min(gau ? 3 : 2, want); min_ns >= 2 && ns < 2; --min_ns) {
             for (int c = ctas; c >= 1; --c) {
-                const size_t budget = (size_t)227 * 1024 / c - 1024;
+                const size_t budget = (size_t)227 * 1024 / c - 1024 - extra;
                 if (budget < sh.stage_off + (size_t)min_ns * stage) continue;
                 ns = (int)std::min<size_t>(want, (budget - sh.stage_off) / stage);
                 break;
@@ -90,7 +93,7 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         if (ns < 2) continue;
         sh.nstage = ns;
         sh.smem = sh.stage_off + ns * stage;
-        sh.ctas_per_sm = std::max(1, std::min(ctas, (int)((size_t)227 * 1024 / (sh.smem + 1024))));
+        sh.ctas_per_sm = std::max(1, std::min(ctas, (int)((size_t)227 * 1024 / (sh.smem + extra + 1024))));
         *shape = sh;
         return cudaSuccess;
     }

@@ -690,9 +690,9 @@ constexpr auto single_kernel()
 
 // A table of jobs sharing one shape: one CTA per work item, items of job j
 // numbered from item_start[j] with the column tiles fastest.
-template <int KIND, typename T, int TX, int DX, int DY, int BB>
+template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SMEM_P = false>
 __device__ __forceinline__ void gather_table_body(const GatherParams *__restrict__ jobs,
-                                                  const int *__restrict__ item_start, int n_jobs);
+                                                  const int *__restrict__ item_start, int n_jobs, int p_off = 0);
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
 __global__ void __launch_bounds__(TX + 32)
@@ -703,10 +703,12 @@ __global__ void __launch_bounds__(TX + 32)
 
 // The table kernel's body, and its instantiations with the same register
 // bounds as the single-job kernels (the 128-column Gaussian for 5 resident CTAs,
-// the 256-column 32-bit Manhattan and Euclidean for 4).
-template <int KIND, typename T, int TX, int DX, int DY, int BB>
+// the 256-column 32-bit Manhattan and Euclidean for 4). With SMEM_P the job's
+// parameters are first copied to shared memory at byte p_off (past the shape's
+// layout), so that fields the loop reloads come from shared memory, not L1.
+template <int KIND, typename T, int TX, int DX, int DY, int BB, bool SMEM_P>
 __device__ __forceinline__ void gather_table_body(const GatherParams *__restrict__ jobs,
-                                                  const int *__restrict__ item_start, int n_jobs)
+                                                  const int *__restrict__ item_start, int n_jobs, int p_off)
 {
     const int item = blockIdx.x;
     int lo = 0, hi = n_jobs - 1;  // the last job whose first item is <= item
@@ -714,7 +716,17 @@ __device__ __forceinline__ void gather_table_body(const GatherParams *__restrict
         const int mid = (lo + hi + 1) >> 1;
         if (item_start[mid] <= item) lo = mid; else hi = mid - 1;
     }
-    const GatherParams &p = jobs[lo];
+    const GatherParams *pp = jobs + lo;
+    if constexpr (SMEM_P) {
+        extern __shared__ __align__(128) unsigned char sm[];
+        static_assert(sizeof(GatherParams) % 8 == 0, "copied as 8-byte words");
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(pp);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(sm + p_off);
+        for (int i = threadIdx.x; i < (int)(sizeof(GatherParams) / 8); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        pp = reinterpret_cast<const GatherParams *>(sm + p_off);
+    }
+    const GatherParams &p = *pp;
     const int li = item - item_start[lo];
     const int tiles = (p.ncx + TX - 1) / TX;
     gather_tiled_body<KIND, T, TX, DX, DY, BB, false, true>(p, li % tiles, li / tiles, 0);
@@ -729,18 +741,24 @@ __global__ void __launch_bounds__(128 + 32, 5)
 
 template <int KIND>
 __global__ void __launch_bounds__(256 + 32, 4)
-    gather_table_me256_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs)
+    gather_table_me256_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs,
+                              int p_off)
 {
-    gather_table_body<KIND, uint32_t, 256, 0, 0, 4>(jobs, item_start, n_jobs);
+    gather_table_body<KIND, uint32_t, 256, 0, 0, 4, true>(jobs, item_start, n_jobs, p_off);
 }
+
+// the shapes served by gather_table_me256_kernel (which takes the parameters'
+// shared-memory offset as a fourth argument)
+template <int KIND, typename T, int TX, int BB>
+constexpr bool is_me256 =
+    (KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && BB == 4 && sizeof(T) == 4;
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
 constexpr auto table_kernel()
 {
     if constexpr (KIND == kGatherGaussian && TX == 128 && BB == 1)
         return gather_table_gauss128_kernel<T, DX, DY>;
-    else if constexpr ((KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && BB == 4 &&
-                       sizeof(T) == 4)
+    else if constexpr (is_me256<KIND, T, TX, BB>)
         return gather_table_me256_kernel<KIND>;
     else
         return gather_table_kernel<KIND, T, TX, DX, DY, BB>;
@@ -782,9 +800,17 @@ cudaError_t run_op(TiledOp &op)
     }
     case TiledOp::kTable: {
         auto fn = table_kernel<K, T, TX, DX, DY, BB>();
-        cudaError_t e = set_smem(fn, op.sh->smem);
-        if (e != cudaSuccess) return e;
-        fn<<<(unsigned)op.n_items, TX + 32, op.sh->smem, op.s>>>(op.d_jobs, op.d_items, op.n_jobs);
+        if constexpr (is_me256<K, T, TX, BB>) {
+            // the job's parameters follow the shape's layout in shared memory
+            const size_t smem = (size_t)op.sh->smem + sizeof(GatherParams);
+            cudaError_t e = set_smem(fn, smem);
+            if (e != cudaSuccess) return e;
+            fn<<<(unsigned)op.n_items, TX + 32, smem, op.s>>>(op.d_jobs, op.d_items, op.n_jobs, (int)op.sh->smem);
+        } else {
+            cudaError_t e = set_smem(fn, op.sh->smem);
+            if (e != cudaSuccess) return e;
+            fn<<<(unsigned)op.n_items, TX + 32, op.sh->smem, op.s>>>(op.d_jobs, op.d_items, op.n_jobs);
+        }
         count_launches(1);
         return cudaGetLastError();
     }
