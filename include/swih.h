@@ -317,7 +317,8 @@ swih_status swih_batch_destroy(swih_batch_t batch);
  * depth of the shared-memory copy ring (2..8; 0 = automatic, the deepest that
  * keeps the register-limited number of CTAs resident), bins_per_step = bins
  * carried per pipeline step by the plain, Manhattan and Euclidean kernels
- * (4 or 8; 0 = automatic; the Gaussian always carries one). A shape whose row
+ * (2, 4 or 8; 2 only with 256 columns and 32-bit elements, else 4 is used;
+ * 0 = automatic; the Gaussian always carries one). A shape whose row
  * segments do not fit falls back to the automatic choice, then to the direct
  * gather. Results do not depend on the shape; only speed does. */
 swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, int stages,

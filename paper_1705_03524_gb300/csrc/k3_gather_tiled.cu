@@ -36,7 +36,6 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
 {
     const bool gau = kind == kGatherGaussian;
     const int A = 16 / elem_bytes;
-    const int bb = gau ? 1 : (want_bb == 8 ? 8 : 4);
     const int per_bin = gau ? 2 * gdx + 1 : nl_per_bin;
     const int want = want_stages > 0 ? std::min(want_stages, kMaxStages) : kDefaultStages;
     // wide tiles amortise the window halo; narrow ones when wide segments do
@@ -52,6 +51,12 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
     }
     for (int i = 0; i < ntx; ++i) {
         const int tx = txs[i];
+        // bins per pipeline step. Steps of 2 bins exist for the 256-column 32-bit
+        // kernels only; by default the Euclidean takes them there (its 5 planes
+        // per bin make a 4-bin stage too large for 4 resident CTAs)
+        int bb = gau ? 1 : (want_bb == 8 ? 8 : 4);
+        if (!gau && tx == 256 && elem_bytes == 4 && (want_bb == 2 || (want_bb == 0 && kind == kGatherEuclidean)))
+            bb = 2;
         GatherShape sh;
         sh.tx = tx;
         sh.bb = bb;
@@ -80,7 +85,10 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
         // want resident CTAs. Settle for two stages when nothing deeper fits.
         // the 256-column 32-bit Manhattan/Euclidean table kernel keeps a copy of
         // its job's parameters past the layout
-        const size_t extra = (!gau && tx == 256 && bb == 4 && elem_bytes == 4) ? sizeof(GatherParams) : 0;
+        const size_t extra = ((kind == kGatherManhattan || kind == kGatherEuclidean) && tx == 256 &&
+                              (bb == 4 || bb == 2) && elem_bytes == 4)
+                                 ? sizeof(GatherParams)
+                                 : 0;
         int ns = 0;
         for (int min_ns = std::min(gau ? 3 : 2, want); min_ns >= 2 && ns < 2; --min_ns) {
             for (int c = ctas; c >= 1; --c) {

@@ -665,14 +665,14 @@ __global__ void __launch_bounds__(128 + 32, 5) gather_gauss128_kernel(const __gr
 // The 256-column Manhattan and Euclidean gathers in the 32-bit ring with 4 bins
 // per step, compiled for 4 resident CTAs (56 registers instead of 71-72, a few
 // bytes of spills): 3-6% faster at the benchmark's windows.
-template <int KIND, bool SPLIT>
+template <int KIND, int BB, bool SPLIT>
 __global__ void __launch_bounds__(256 + 32, 4) gather_me256_kernel(const __grid_constant__ GatherParams p)
 {
     if constexpr (SPLIT)
-        gather_tiled_body<KIND, uint32_t, 256, 0, 0, 4, true, true>(p, blockIdx.x, blockIdx.y / p.nbg,
-                                                                    blockIdx.y % p.nbg);
+        gather_tiled_body<KIND, uint32_t, 256, 0, 0, BB, true, true>(p, blockIdx.x, blockIdx.y / p.nbg,
+                                                                     blockIdx.y % p.nbg);
     else
-        gather_tiled_body<KIND, uint32_t, 256, 0, 0, 4, false, true>(p, blockIdx.x, blockIdx.y, 0);
+        gather_tiled_body<KIND, uint32_t, 256, 0, 0, BB, false, true>(p, blockIdx.x, blockIdx.y, 0);
 }
 
 // the single-job kernel of an instantiation
@@ -681,9 +681,9 @@ constexpr auto single_kernel()
 {
     if constexpr (KIND == kGatherGaussian && TX == 128 && BB == 1)
         return gather_gauss128_kernel<T, DX, DY, SPLIT>;
-    else if constexpr ((KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && BB == 4 &&
+    else if constexpr ((KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && (BB == 4 || BB == 2) &&
                        sizeof(T) == 4)
-        return gather_me256_kernel<KIND, SPLIT>;
+        return gather_me256_kernel<KIND, BB, SPLIT>;
     else
         return gather_tiled_kernel<KIND, T, TX, DX, DY, BB, SPLIT>;
 }
@@ -739,19 +739,19 @@ __global__ void __launch_bounds__(128 + 32, 5)
     gather_table_body<kGatherGaussian, T, 128, DX, DY, 1>(jobs, item_start, n_jobs);
 }
 
-template <int KIND>
+template <int KIND, int BB>
 __global__ void __launch_bounds__(256 + 32, 4)
     gather_table_me256_kernel(const GatherParams *__restrict__ jobs, const int *__restrict__ item_start, int n_jobs,
                               int p_off)
 {
-    gather_table_body<KIND, uint32_t, 256, 0, 0, 4, true>(jobs, item_start, n_jobs, p_off);
+    gather_table_body<KIND, uint32_t, 256, 0, 0, BB, true>(jobs, item_start, n_jobs, p_off);
 }
 
 // the shapes served by gather_table_me256_kernel (which takes the parameters'
 // shared-memory offset as a fourth argument)
 template <int KIND, typename T, int TX, int BB>
 constexpr bool is_me256 =
-    (KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && BB == 4 && sizeof(T) == 4;
+    (KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && (BB == 4 || BB == 2) && sizeof(T) == 4;
 
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
 constexpr auto table_kernel()
@@ -759,7 +759,7 @@ constexpr auto table_kernel()
     if constexpr (KIND == kGatherGaussian && TX == 128 && BB == 1)
         return gather_table_gauss128_kernel<T, DX, DY>;
     else if constexpr (is_me256<KIND, T, TX, BB>)
-        return gather_table_me256_kernel<KIND>;
+        return gather_table_me256_kernel<KIND, BB>;
     else
         return gather_table_kernel<KIND, T, TX, DX, DY, BB>;
 }
@@ -838,6 +838,11 @@ cudaError_t dispatch_kind(int elem_bytes, int gdx, int gdy, int tx, int bb, Tile
     } else {
         auto by_type = [&](auto t_tag) -> cudaError_t {
             using T = typename decltype(t_tag)::type;
+            if (bb == 2) {  // the 256-column 32-bit kernels only
+                if constexpr (sizeof(T) == 4)
+                    if (tx == 256) return run_op<K, T, 256, 0, 0, 2>(op);
+                return cudaErrorInvalidValue;
+            }
             if (tx == 128) return bb == 8 ? run_op<K, T, 128, 0, 0, 8>(op) : run_op<K, T, 128, 0, 0, 4>(op);
             return bb == 8 ? run_op<K, T, 256, 0, 0, 8>(op) : run_op<K, T, 256, 0, 0, 4>(op);
         };

@@ -896,8 +896,8 @@ swih_status swih_set_gather_config(swih_plan_t pl, int kernel, int tile_cols, in
         return fail(pl, SWIH_ERR_INVALID_ARG, "tile_cols must be 0, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8))
         return fail(pl, SWIH_ERR_INVALID_ARG, "stages must be 0 or 2..8");
-    if (bins_per_step != 0 && bins_per_step != 4 && bins_per_step != 8)
-        return fail(pl, SWIH_ERR_INVALID_ARG, "bins_per_step must be 0, 4 or 8");
+    if (bins_per_step != 0 && bins_per_step != 2 && bins_per_step != 4 && bins_per_step != 8)
+        return fail(pl, SWIH_ERR_INVALID_ARG, "bins_per_step must be 0, 2, 4 or 8");
     pl->cfg_tx[kernel] = tile_cols;
     pl->cfg_stages[kernel] = stages;
     pl->cfg_bb[kernel] = bins_per_step;

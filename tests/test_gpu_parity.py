@@ -503,3 +503,47 @@ def test_gather_counts_the_bytes_it_loads():
             plan.sync_status()
             got = plan.load_bytes()
             assert lo * dense <= got <= hi * dense, (got, dense)
+
+
+def test_every_gather_shape_gives_the_same_maps():
+    """swih_set_gather_config picks the tiled gather's tile width, copy-ring
+    depth and bins per pipeline step (2 only for 256 columns of 32-bit
+    elements; any other request falls back to an automatic shape). Every shape
+    gives maps equal to the oracle's within the tolerance, through single-window
+    launches and the multi-window table launch, on a 32-bit plan wide enough
+    for 256-column tiles with ragged tails."""
+    img = synth.blob_scene(96, 610, 8, seed=23, n_blobs=6, margin=24).image
+    B = 12
+    kinds = ("manhattan", "euclidean")
+    plan, _buf = make_plan(img, 8, B, kinds, (41, 41))
+    bins = oracle_bins(img, 8, B)
+    windows = [(21, 21), (41, 11), (5, 41)]
+    with plan:
+        assert plan.info().elem_bytes == 4
+        refs = {}
+        for kind in kinds:
+            for i, (w, h) in enumerate(windows):
+                K = O.kernel_weights(kind, w, h)
+                x0, y0, nx, ny = O.valid_centres(96, 610, w, h)
+                q = O.target_hist(bins, B, K, x0 + (11 * i) % nx, y0 + (3 * i) % ny)
+                refs[kind, w, h] = (torch.tensor(q, dtype=torch.float32, device=DEV),
+                                    O.likelihood_map(bins, B, K, q), (ny, nx))
+        for kind in kinds:
+            k = S.KERNELS[kind]
+            for tile_cols in (0, 128, 256):
+                for stages in (0, 2, 3):
+                    for bps in (0, 2, 4, 8):
+                        S.swih_set_gather_config(plan.handle, k, tile_cols, stages, bps)
+                        targets = [refs[kind, w, h][0] for w, h in windows]
+                        multis = [torch.full(refs[kind, w, h][2], -1.0, device=DEV) for w, h in windows]
+                        plan.likelihood_scales(kind, windows, targets, multis)
+                        w, h = windows[0]
+                        single = torch.full(refs[kind, w, h][2], -1.0, device=DEV)
+                        plan.likelihood(kind, w, h, targets[0], single)
+                        plan.sync_status()
+                        for (w, h), m in zip(windows, multis):
+                            err = np.abs(m.cpu().numpy().astype(np.float64) - refs[kind, w, h][1]).max()
+                            assert err <= TOL, (kind, tile_cols, stages, bps, w, h, err)
+                        err = np.abs(single.cpu().numpy().astype(np.float64) - refs[kind, *windows[0]][1]).max()
+                        assert err <= TOL, (kind, tile_cols, stages, bps, "single", err)
+            S.swih_set_gather_config(plan.handle, k, 0, 0, 0)
