@@ -222,10 +222,12 @@ swih_status swih_batch_autotune(swih_batch_t b, void *stream)
         int bt = 0, bs = 0, bbb = 0;
         const int txs[2] = {128, 256};
         const int stages[4] = {2, 3, 4, 6};
-        const int bbs[2] = {4, 8};
+        // bins per step: 2 exists only with 256 columns and 32-bit elements
+        const int bbs[3] = {4, 8, 2};
         for (int ti = 0; ti < 2 && st == SWIH_OK; ++ti)
             for (int si = 0; si < 4 && st == SWIH_OK; ++si)
-                for (int bi = 0; bi < (gau ? 1 : 2) && st == SWIH_OK; ++bi) {
+                for (int bi = 0; bi < (gau ? 1 : 3) && st == SWIH_OK; ++bi) {
+                    if (bbs[bi] == 2 && (txs[ti] != 256 || w.elem_bytes() != 4)) continue;
                     w.set_group_want(gi, txs[ti], stages[si], gau ? 0 : bbs[bi]);
                     st = w.rebuild(err);
                     if (st != SWIH_OK) {

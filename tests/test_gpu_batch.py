@@ -193,6 +193,30 @@ def test_rerun_is_deterministic_follows_the_frame_and_survives_autotune():
         check_against_oracle(img2, 8, B, specs)
 
 
+def test_autotune_of_32bit_groups_keeps_results():
+    """A Manhattan + Euclidean batch keeps 32-bit integral histograms, where the
+    autotuner also tries steps of 2 bins (256-column tiles only); whatever it
+    picks, the maps are unchanged and match the oracle."""
+    img = synth.blob_scene(300, 500, 8, seed=5, n_blobs=5, margin=40).image
+    specs = [Spec(0, 0, 300, 150, "euclidean", [(21, 21), (41, 41)]),
+             Spec(150, 100, 333, 181, "manhattan", [(15, 15), (41, 21)])]
+    B = 16
+    batch, _buf, _ptr = make_batch(img, 8, B, ("manhattan", "euclidean"), specs)
+    with batch:
+        batch.run()
+        batch.sync_status()
+        before = [m.clone() for sp in specs for m in sp.maps]
+        batch.autotune()
+        for sp in specs:
+            for m in sp.maps:
+                m.fill_(-1.0)
+        batch.run()
+        batch.sync_status()
+        after = [m for sp in specs for m in sp.maps]
+        assert max((a - b).abs().max().item() for a, b in zip(before, after)) <= 1e-6
+        check_against_oracle(img, 8, B, specs)
+
+
 def test_runs_on_a_user_stream():
     img = synth.uniform_image(100, 120, 8, seed=3)
     specs = [Spec(0, 0, 120, 100, "manhattan", [(11, 11)]), Spec(20, 30, 64, 64, "euclidean", [(9, 9)])]
