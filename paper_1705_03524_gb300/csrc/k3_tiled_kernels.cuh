@@ -662,9 +662,13 @@ __global__ void __launch_bounds__(128 + 32, 5) gather_gauss128_kernel(const __gr
         gather_tiled_body<kGatherGaussian, T, 128, DX, DY, 1, false, true>(p, blockIdx.x, blockIdx.y, 0);
 }
 
-// The 256-column Manhattan and Euclidean gathers in the 32-bit ring with 4 bins
-// per step, compiled for 4 resident CTAs (56 registers instead of 71-72, a few
-// bytes of spills): 3-6% faster at the benchmark's windows.
+// The 256-column Manhattan and Euclidean gathers in the 32-bit ring with 4 or 2
+// bins per step, compiled for 4 resident CTAs (56 registers instead of 71-72, a
+// few bytes of spills): 3-6% faster at the benchmark's windows.
+template <int KIND, typename T, int TX, int BB>
+constexpr bool is_me256 =
+    (KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && (BB == 4 || BB == 2) && sizeof(T) == 4;
+
 template <int KIND, int BB, bool SPLIT>
 __global__ void __launch_bounds__(256 + 32, 4) gather_me256_kernel(const __grid_constant__ GatherParams p)
 {
@@ -681,8 +685,7 @@ constexpr auto single_kernel()
 {
     if constexpr (KIND == kGatherGaussian && TX == 128 && BB == 1)
         return gather_gauss128_kernel<T, DX, DY, SPLIT>;
-    else if constexpr ((KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && (BB == 4 || BB == 2) &&
-                       sizeof(T) == 4)
+    else if constexpr (is_me256<KIND, T, TX, BB>)
         return gather_me256_kernel<KIND, BB, SPLIT>;
     else
         return gather_tiled_kernel<KIND, T, TX, DX, DY, BB, SPLIT>;
@@ -747,12 +750,8 @@ __global__ void __launch_bounds__(256 + 32, 4)
     gather_table_body<KIND, uint32_t, 256, 0, 0, BB, true>(jobs, item_start, n_jobs, p_off);
 }
 
-// the shapes served by gather_table_me256_kernel (which takes the parameters'
-// shared-memory offset as a fourth argument)
-template <int KIND, typename T, int TX, int BB>
-constexpr bool is_me256 =
-    (KIND == kGatherManhattan || KIND == kGatherEuclidean) && TX == 256 && (BB == 4 || BB == 2) && sizeof(T) == 4;
-
+// (gather_table_me256_kernel, for the shapes is_me256 names, takes the
+// parameters' shared-memory offset as a fourth argument)
 template <int KIND, typename T, int TX, int DX, int DY, int BB>
 constexpr auto table_kernel()
 {
