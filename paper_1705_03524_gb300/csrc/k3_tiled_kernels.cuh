@@ -345,51 +345,65 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
     const int nlist = s_list[p.B];
     const int steps = s_rows[p.B] * G;
 
-    // producer warp, lane 0: steps in order, each into stage m % NS once the
-    // consumers have released that stage's previous step
+    // producer warp: steps in order, each into stage m % NS once the consumers
+    // have released that stage's previous step. The step's copies (bin j, plane
+    // t) are spread over the lanes; lane 0 posts the step's byte count on the
+    // full barrier before any lane issues its copies.
     if (producer) {
-        if (lane != 0) return;
         int g = 0, s = 0, li = 0;
         int bb = nlist > 0 ? s_list[0] : 0;
         unsigned rmask = nlist > 0 ? (unsigned)s_rows[0] : 0u;
         while (s < S && !((rmask >> s) & 1u)) ++s;  // the first row to load
-        unsigned long long loaded = 0;  // bytes of integral histogram requested
+        unsigned long long loaded = 0;  // bytes of integral histogram requested (lane 0)
         for (int m = 0; m < steps; ++m) {
             const int st_i = m % NS;
-            if (m >= NS && !mbar_wait(&empty[st_i], (uint32_t)(((m / NS) - 1) & 1))) {
-                atomicOr(p.status, kStatusTimeout);
-                return;
+            if (m >= NS) {
+                const bool ok = mbar_wait(&empty[st_i], (uint32_t)(((m / NS) - 1) & 1));
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) atomicOr(p.status, kStatusTimeout);
+                    return;
+                }
             }
             uint64_t *br = &full[st_i];
             const int b0 = bb * BB;
             const int nb = min(BB, p.B - b0);
-            int n_rows = 0;  // bins of the block whose row is stored (the others read as zero)
-            for (int j = 0; j < nb; ++j) n_rows += stored_row(b0 + j, s) >= 0;
-            if (n_rows == 0) {  // zero rows only (above the image, or before the bin's first pixel)
-                mbar_arrive(br);
+            int nt;
+            const int *list;
+            if constexpr (kGau) {
+                nt = KX + 1;
+                list = p.load_even + g * (KX + 1);
             } else {
-                int nt;
-                const int *list;
-                if constexpr (kGau) {
-                    nt = KX + 1;
-                    list = p.load_even + g * (KX + 1);
+                const bool odd = kMan && (s & 1);
+                nt = odd ? p.n_load_odd : p.n_load_even;
+                list = odd ? p.load_odd : p.load_even;
+            }
+            // copies of bins whose row is stored (the others read as zero)
+            const int n_copies = nb * nt;
+            int n_valid = 0;
+            for (int c0 = 0; c0 < n_copies; c0 += 32) {
+                const int c = c0 + lane;
+                const bool v = c < n_copies && stored_row(b0 + c / nt, s) >= 0;
+                n_valid += __popc(__ballot_sync(0xffffffffu, v));
+            }
+            if (lane == 0) {
+                if (n_valid == 0) {  // zero rows only (above the image, or before the bin's first pixel)
+                    mbar_arrive(br);
                 } else {
-                    const bool odd = kMan && (s & 1);
-                    nt = odd ? p.n_load_odd : p.n_load_even;
-                    list = odd ? p.load_odd : p.load_even;
+                    mbar_arrive_expect_tx(br, (uint32_t)n_valid * seg_bytes);
+                    loaded += (unsigned long long)n_valid * seg_bytes;
                 }
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(br, (uint32_t)(n_rows * nt) * seg_bytes);
-                loaded += (unsigned long long)(n_rows * nt) * seg_bytes;
+            }
+            __syncwarp();
+            if (n_valid > 0) {
                 T *dst = stages + (size_t)st_i * stage_elems + land;
-                for (int j = 0; j < nb; ++j) {
+                for (int c = lane; c < n_copies; c += 32) {
+                    const int j = c / nt, t = c - j * nt;
                     const int Y = stored_row(b0 + j, s);
                     if (Y < 0) continue;
-                    const T *row = reinterpret_cast<const T *>(p.ih) + (int64_t)Y * p.pitch + x_begin;
-                    for (int t = 0; t < nt; ++t) {
-                        const T *src = row + ((int64_t)list[t] * p.B + b0 + j) * p.plane;
-                        bulk_copy_g2s(dst + (size_t)(j * nt + t) * p.seg, src, seg_bytes, br);
-                    }
+                    const T *src = reinterpret_cast<const T *>(p.ih) + (int64_t)Y * p.pitch + x_begin +
+                                   ((int64_t)list[t] * p.B + b0 + j) * p.plane;
+                    fence_proxy_async_smem();
+                    bulk_copy_g2s(dst + (size_t)c * p.seg, src, seg_bytes, br);
                 }
             }
             if (++g == G) {
@@ -405,7 +419,7 @@ __device__ __forceinline__ void gather_tiled_body(const GatherParams &p, const i
                 }
             }
         }
-        if (p.load_bytes) atomicAdd(p.load_bytes, loaded);
+        if (lane == 0 && p.load_bytes) atomicAdd(p.load_bytes, loaded);
         return;
     }
 
