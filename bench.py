@@ -126,21 +126,47 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def code_sha256(path: str) -> str:
+    """sha256 of a C++/CUDA source with its comments removed and whitespace runs
+    collapsed: edits to comments alone keep the hash, any change to the code
+    changes it. String and character literals are kept as written."""
+    text = open(path).read()
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return hashlib.sha256(" ".join("".join(out).split()).encode()).hexdigest()
+
+
 def profile_traffic(kernel_name: str, source: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current source of the kernel (sha256 recorded in the summary), else None."""
+    current code of the kernel (code_sha256 recorded in the summary), else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel_name}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m = re.search(r"code_sha256:\s*([0-9a-f]{64})", text)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not (m and t):
         return None
     src = os.path.join(ROOT, "paper_1705_03524_gb300", "csrc", source)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return float(t.group(1)) if sha == m.group(1) else None
+    return float(t.group(1)) if code_sha256(src) == m.group(1) else None
 
 
 def reduce_max_over_ranks(values):

@@ -13,10 +13,11 @@
 // * Work is a sequence of pipeline steps (bin block, lattice row, plane group).
 //   A step carries BB bins (several for the cheap kernels, one for the
 //   Gaussian) and, for the Gaussian, one y-exponent l, i.e. the planes
-//   x^0..x^2Dx y^l. A dedicated producer warp (one lane) issues, for each step,
-//   TMA bulk copies (cp.async.bulk, completion counted on a "full" mbarrier)
-//   of the row segments [xs-rx-1, xs+TX+rx) into one stage of a ring of NS
-//   shared-memory stages, up to NS steps ahead of the consumers. Each consumer
+//   x^0..x^2Dx y^l. A dedicated producer warp issues, for each step, TMA bulk
+//   copies (cp.async.bulk, completion counted on a "full" mbarrier) of the row
+//   segments [xs-rx-1, xs+TX+rx) into one stage of a ring of NS shared-memory
+//   stages, up to NS steps ahead of the consumers; its lanes share the step's
+//   copies, and lane 0 posts their byte count on the barrier first. Each consumer
 //   warp releases a stage through an "empty" mbarrier, and the producer refills
 //   a stage only after every consumer warp has released it.
 // * Every thread forms its horizontal differences I(X2) - I(X0) (and the
