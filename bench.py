@@ -186,6 +186,10 @@ def whole_job_rate(units_per_rank_step, steps, world, max_ms):
 
 
 # ----------------------------------------------------------------------------- swih arm
+# inputs and final maps of the benchmark run, for the oracle comparison
+_ORACLE_CHECK = []
+
+
 def run_swih(args, rank, world, local_rank):
     import torch
 
@@ -407,6 +411,11 @@ def run_swih(args, rank, world, local_rank):
         pl.sync_status(stream)
     bi = h_img.numel() * h_img.element_size() + h_targets.numel() * 4
     bo = sum(m.numel() * 4 for m in h_maps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:  # every step computes the same maps; compared with the oracle after the timed parts
+            _ORACLE_CHECK[:] = [img, B, list(jobs), [m.numpy().copy() for m in h_maps], h_targets.numpy().copy()]
+        except Exception:
+            _ORACLE_CHECK[:] = []
 
     if dist:
         ms, e2e_ms = reduce_max_over_ranks([ms, e2e_ms])
@@ -859,6 +868,30 @@ def run_fig6(args):
 
 
 # ----------------------------------------------------------------------------- oracle
+def oracle_errors(img, B, jobs, maps, targets, n=2048, seed=11):
+    """Largest |GPU - oracle| of each likelihood map at n random valid centres.
+
+    The FP64 brute-force oracle is evaluated with the target histograms the GPU
+    used (float32, as copied back) and compared with the map values copied back
+    from the device; maps[j] is [H - w + 1, W - w + 1] for job (kernel, w)."""
+    from oracle import swih_oracle as O
+
+    bins = O.quantize(img, 8, B)
+    H, W = bins.shape
+    rng = np.random.default_rng(seed)
+    per = {}
+    for j, (k, w) in enumerate(jobs):
+        r = (w - 1) // 2
+        cx = rng.integers(r, W - r, n)
+        cy = rng.integers(r, H - r, n)
+        ref = O.likelihood_at(bins, B, O.kernel_weights(k, w, w), np.asarray(targets[j], dtype=np.float64), cx, cy)
+        got = np.asarray(maps[j], dtype=np.float64)[cy - r, cx - r]
+        per[f"{k}_{w}"] = float(np.abs(got - ref).max())
+    return {"max_abs": max(per.values()), "tolerance": 1e-5, "per_map": per,
+            "sample": (f"{n} random valid centres per map (seed {seed}), FP64 brute-force oracle with the "
+                       "targets the GPU used, against the maps copied back at the end of the end-to-end run")}
+
+
 def oracle_sample(budget_s: float, seed: int = 7):
     """Time the CPU oracle on random valid centres of the same workload (all nine
     kernel/window maps, round robin) for about budget_s seconds."""
@@ -996,6 +1029,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(args.cpu_seconds)
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        if _ORACLE_CHECK:
+            try:
+                line["oracle_error"] = oracle_errors(*_ORACLE_CHECK)
+            except Exception as e:  # the bench line is printed either way
+                line["oracle_error"] = {"error": repr(e)}
     if rank == 0:
         line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -10,6 +10,8 @@ parse.
 import os
 import re
 
+import numpy as np
+
 import bench
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -42,3 +44,30 @@ def test_the_summaries_bench_reads_parse():
         t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
         assert t and float(t.group(1)) > 0, name
         assert os.path.exists(os.path.join(SRC, src))
+
+
+def test_oracle_error_report_finds_a_planted_difference():
+    """bench.oracle_errors compares maps with the oracle at sampled centres;
+    maps made by the oracle itself (with float32 targets, as the GPU's) give
+    zero, and a changed value at a sampled centre shows up in its map only."""
+    from oracle import swih_oracle as O
+    from paper_1705_03524_gb300 import synth
+
+    img = synth.uniform_image(40, 52, 8, seed=4)
+    B = 6
+    jobs = [("manhattan", 5), ("gaussian", 9), ("euclidean", 3)]
+    bins = O.quantize(img, 8, B)
+    maps, targets = [], []
+    for k, w in jobs:
+        K = O.kernel_weights(k, w, w)
+        q = O.target_hist(bins, B, K, 20, 18).astype(np.float32)
+        targets.append(q)
+        maps.append(O.likelihood_map(bins, B, K, q.astype(np.float64)).astype(np.float32))
+    res = bench.oracle_errors(img, B, jobs, maps, np.stack(targets), n=64, seed=3)
+    assert res["max_abs"] <= 1e-6, res
+    # every valid centre is sampled on maps this small with enough draws: plant one error
+    bad = [m.copy() for m in maps]
+    bad[1][0, 0] += 0.25
+    res = bench.oracle_errors(img, B, jobs, bad, np.stack(targets), n=4000, seed=3)
+    assert abs(res["per_map"]["gaussian_9"] - 0.25) < 1e-3, res
+    assert res["per_map"]["manhattan_5"] <= 1e-6 and res["per_map"]["euclidean_3"] <= 1e-6, res
