@@ -42,7 +42,7 @@ def _worker(rank, world, port, out):
 def test_max_over_ranks_and_rank0_only_reporting():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that may run OpenMP threads
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
