@@ -370,7 +370,14 @@ def likelihood_at(bins, B, K, q, cx, cy) -> np.ndarray:
     h, w = K.shape
     cx = np.ascontiguousarray(cx, dtype=np.int32)
     cy = np.ascontiguousarray(cy, dtype=np.int32)
+    rx, ry = (w - 1) // 2, (h - 1) // 2
+    if cx.size != cy.size:
+        raise ValueError("cx and cy differ in length")
+    if cx.size and (cx.min() < rx or cy.min() < ry or cx.max() >= W - rx or cy.max() >= H - ry):
+        raise ValueError("a window leaves the image")
     q = np.ascontiguousarray(q, dtype=np.float64)
+    if q.size != B:
+        raise ValueError("the target needs B entries")
     L = np.empty(cx.size, dtype=np.float64)
     _lib().swih_oracle_likelihood_at(_ptr(bins), H, W, B, _ptr(K), w, h, _ptr(cx), _ptr(cy),
                                      cx.size, _ptr(q), _ptr(L))

@@ -204,6 +204,61 @@ def test_likelihood_is_one_at_target_centre(kind):
     assert L.max() <= 1.0 + 1e-12
 
 
+def test_bhattacharyya_hand_values():
+    # A 3 x 3 plain window with six pixels of bin 0 and three of bin 1 has
+    # H = (2/3, 1/3). Against q = (1/3, 2/3), L = 2 sqrt(2/9) = 2 sqrt(2) / 3;
+    # against q = (1/4, 3/4), L = sqrt(1/6) + sqrt(1/4).
+    bins = np.array([[0, 1, 0],
+                     [0, 1, 0],
+                     [0, 1, 0]], dtype=np.uint8)
+    K = O.kernel_weights("plain", 3, 3)
+    L = O.likelihood_at(bins, 2, K, [1.0 / 3.0, 2.0 / 3.0], [1], [1])
+    assert abs(L[0] - 2.0 * np.sqrt(2.0) / 3.0) < 1e-15
+    L = O.likelihood_at(bins, 2, K, [0.25, 0.75], [1], [1])
+    assert abs(L[0] - (np.sqrt(1.0 / 6.0) + 0.5)) < 1e-15
+    # Manhattan 3 x 3 weights: corners 0, edge midpoints 1, centre 2 (M = 6).
+    # Bin 1 holds the centre and the top edge: U = (3, 3), H = (1/2, 1/2);
+    # against q = (1, 0), L = sqrt(1/2).
+    bins = np.array([[1, 1, 1],
+                     [0, 1, 0],
+                     [0, 0, 0]], dtype=np.uint8)
+    K = O.kernel_weights("manhattan", 3, 3)
+    L = O.likelihood_at(bins, 2, K, [1.0, 0.0], [1], [1])
+    assert abs(L[0] - np.sqrt(0.5)) < 1e-15
+
+
+def test_likelihood_at_listed_centres_by_slicing():
+    # Listed centres on a non-square image with a non-square window, near
+    # opposite borders (cx != cy everywhere, and a swapped pair would leave the
+    # image or land on other pixels), checked against a histogram of the
+    # window taken by numpy slicing and against the rectangle routine.
+    rng = np.random.default_rng(31)
+    H, W, B = 23, 41, 5
+    bins = rng.integers(0, B, size=(H, W)).astype(np.uint8)
+    w, h = 7, 5
+    rx, ry = 3, 2
+    K = O.kernel_weights("manhattan", w, h)
+    q = rng.gamma(0.5, size=B)
+    q = q / q.sum()
+    cx = np.array([rx, W - 1 - rx, rx + 1, W - 2 - rx, 20, 37], dtype=np.int32)
+    cy = np.array([H - 1 - ry, ry, ry + 1, H - 2 - ry, 11, 3], dtype=np.int32)
+    got = O.likelihood_at(bins, B, K, q, cx, cy)
+    for i in range(cx.size):
+        win = bins[cy[i] - ry: cy[i] + ry + 1, cx[i] - rx: cx[i] + rx + 1]
+        U = np.array([K[win == b].sum() for b in range(B)])
+        Hc = U / U.sum()
+        assert abs(got[i] - np.sqrt(Hc * q).sum()) < 1e-14, i
+    L = O.likelihood_rect(bins, B, K, q, rx, ry, W - w + 1, H - h + 1)
+    np.testing.assert_array_equal(got, L[cy - ry, cx - rx])
+    # the listed-centre histograms agree with the same slicing
+    U = O.hist_at(bins, B, K, cx, cy)
+    for i in range(cx.size):
+        win = bins[cy[i] - ry: cy[i] + ry + 1, cx[i] - rx: cx[i] + rx + 1]
+        assert np.array_equal(U[i], [K[win == b].sum() for b in range(B)])
+    with pytest.raises(ValueError):
+        O.likelihood_at(bins, B, K, q, cy, cx)  # swapped: windows leave the image
+
+
 @pytest.mark.parametrize("kind", O.KINDS)
 def test_mirror_invariance(kind):
     rng = np.random.default_rng(21)
