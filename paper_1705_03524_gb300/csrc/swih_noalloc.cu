@@ -156,7 +156,15 @@ extern "C" swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const v
         layout->n_bands = L.n_bands;
         layout->workspace_bytes = ih_need;  // bytes the caller's d_ih must hold
     }
-    if (!d_ih) return SWIH_OK;  // size query only
+    // Every call, a size query included, looks up the static array's device
+    // address on the current device, so a size query made before a stream
+    // capture already counts as the device's first call.
+    void *base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) return cuda_fail_na("cudaGetSymbolAddress(static scratch)", e);
+    char *sc = static_cast<char *>(base);
+    if (layout) layout->d_bins = sc + m.bins;
+    if (!d_ih) return SWIH_OK;  // size query: nothing is enqueued
     if (ih_bytes < ih_need) return fail_na(SWIH_ERR_INVALID_ARG, "ih_bytes is smaller than the layout needs");
     if (!d_image) return fail_na(SWIH_ERR_INVALID_ARG, "d_image is NULL");
     if (d.pixel_type == SWIH_PIXEL_U16 && (reinterpret_cast<uintptr_t>(d_image) & 1))
@@ -164,12 +172,7 @@ extern "C" swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const v
     if (reinterpret_cast<uintptr_t>(d_ih) % 16)
         return fail_na(SWIH_ERR_INVALID_ARG, "d_ih must be 16-byte aligned");
 
-    void *base = nullptr;
-    cudaError_t e = scratch_address(&base);
-    if (e != cudaSuccess) return cuda_fail_na("cudaGetSymbolAddress(static scratch)", e);
-    char *sc = static_cast<char *>(base);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (layout) layout->d_bins = sc + m.bins;
 
     // tile flags and ticket must start at zero; so must the built-in status word
     e = cudaMemsetAsync(sc + m.flags, 0, m.flags_bytes, s);

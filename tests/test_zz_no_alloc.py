@@ -47,6 +47,23 @@ def planes(ptr, info):
 @pytest.mark.parametrize("kernels,shape,B", [(("manhattan", "euclidean"), (300, 500), 16),
                                               (("gaussian",), (160, 210), 8)])
 def test_noalloc_build_equals_plan_build_two_calls(kernels, shape, B):
+    two_calls_against_plan(kernels, shape, B)
+
+
+def test_noalloc_raises_the_band_height_when_the_scratch_is_short():
+    # With the default 32-row bands this frame's look-back state (5 terms, 3
+    # y-exponents, 32 bins, 2048 columns, 16 bands) is far above the static
+    # scratch; the entry point raises the band height until it fits. Bands
+    # taller than 64 rows take the scan's path without shared-memory row copies.
+    kernels, shape, B = ("manhattan", "euclidean"), (512, 2048), 32
+    desc = S.make_desc(shape[0], shape[1], bins=B, kernels=kernels, max_win=(31, 31))
+    with S.Plan(desc) as plan:
+        assert plan.info().band_rows <= 64
+    lay = two_calls_against_plan(kernels, shape, B)
+    assert lay.band_rows > 64
+
+
+def two_calls_against_plan(kernels, shape, B):
     H, W = shape
     desc = S.make_desc(H, W, bins=B, kernels=kernels, max_win=(31, 31))
     stream = torch.cuda.Stream()
@@ -79,6 +96,7 @@ def test_noalloc_build_equals_plan_build_two_calls(kernels, shape, B):
         assert np.array_equal(got, ref), f"call {call}: integral histograms differ"
         if call == 1:
             assert free_after == free_before
+    return lay
 
 
 def test_noalloc_rejects_oversized_scratch():
