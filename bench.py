@@ -58,6 +58,11 @@ def windows_per_step(H=1024, W=1024):
 
 
 # ----------------------------------------------------------------------------- helpers
+def progress(msg: str) -> None:
+    """One line of progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -186,8 +191,107 @@ def whole_job_rate(units_per_rank_step, steps, world, max_ms):
 
 
 # ----------------------------------------------------------------------------- swih arm
+
+class FrameStep:
+    """One benchmark step over a frame: the Manhattan+Euclidean plan's and the
+    Gaussian plan's integral histograms, then each kernel's windows in one
+    multi-window launch (swih_likelihood_scales). Targets are the window of
+    each kernel and size centred on (tx, ty), set up untimed."""
+
+    def __init__(self, S, dev, img, B, kernels, tx, ty, stream, windows=WINDOWS):
+        import torch
+
+        H, W = img.shape
+        self.stream = stream
+        self.kernels = kernels
+        self.windows = windows
+        self.d_img = torch.from_numpy(img).to(dev)
+        me = tuple(k for k in kernels if k != "gaussian")
+        mw = max(windows)
+        self.plan_me = S.Plan(S.make_desc(H, W, bins=B, kernels=me, max_win=(mw, mw))) if me else None
+        self.plan_g = (S.Plan(S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(mw, mw)))
+                       if "gaussian" in kernels else None)
+        self.plans = [pl for pl in (self.plan_me, self.plan_g) if pl is not None]
+        self.plan_of = {"manhattan": self.plan_me, "euclidean": self.plan_me, "gaussian": self.plan_g}
+        self.info_me = self.plan_me.info() if self.plan_me else None
+        self.info_g = self.plan_g.info() if self.plan_g else None
+        self.jobs = [(k, w) for k in kernels for w in windows]
+        self.job_of = {k: [j for j, (kk, _) in enumerate(self.jobs) if kk == k] for k in kernels}
+        for pl in self.plans:
+            pl.build_ih(self.d_img, stream)
+        self.targets = torch.empty((len(self.jobs), B), dtype=torch.float32, device=dev)
+        for j, (k, w) in enumerate(self.jobs):
+            self.plan_of[k].local_hist(k, w, w, tx, ty, 1, 1, self.targets[j], stream)
+        self.maps = [torch.empty((H - w + 1, W - w + 1), dtype=torch.float32, device=dev) for _, w in self.jobs]
+        for pl in self.plans:
+            pl.sync_status(stream)
+        self.windows_per_step = sum(m.numel() for m in self.maps)
+
+    def step(self, ev=None):
+        """ev (optional): 3 + len(kernels) events, recorded before the builds,
+        after each build and after each kernel's gather launch."""
+        s = self.stream
+        if ev is not None:
+            ev[0].record(s)
+        if self.plan_me:
+            self.plan_me.build_ih(self.d_img, s)
+        if ev is not None:
+            ev[1].record(s)
+        if self.plan_g:
+            self.plan_g.build_ih(self.d_img, s)
+        if ev is not None:
+            ev[2].record(s)
+        for ki, k in enumerate(self.kernels):  # the kernel's windows in one launch (multi-scale search)
+            js = self.job_of[k]
+            self.plan_of[k].likelihood_scales(k, [(self.jobs[j][1], self.jobs[j][1]) for j in js],
+                                              [self.targets[j] for j in js], [self.maps[j] for j in js], s)
+            if ev is not None:
+                ev[3 + ki].record(s)
+
+    def timed(self, steps, clocks=None):
+        """Time `steps` steps with CUDA events (after a synchronize); returns
+        (total ms, per-launch mean ms by stage, integral-histogram bytes the
+        Gaussian gathers loaded per launch, clock summary or None)."""
+        import torch
+
+        n_ev = 3 + len(self.kernels)
+        events = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.start()
+            clocks.wait_first()
+        wall0 = time.time()
+        for pl in self.plans:
+            pl.load_bytes(reset=True)
+        t0.record(self.stream)
+        for i in range(steps):
+            self.step(events[i])
+        t1.record(self.stream)
+        torch.cuda.synchronize()
+        wall1 = time.time()
+        clk = clocks.stop(wall0, wall1) if clocks is not None else None
+        for pl in self.plans:
+            pl.sync_status(self.stream)
+        loaded_g = self.plan_g.load_bytes() / steps if self.plan_g else 0.0
+        seg = {"build_me": [], "build_g": []}
+        for i in range(steps):
+            ev = events[i]
+            seg["build_me"].append(ev[0].elapsed_time(ev[1]))
+            seg["build_g"].append(ev[1].elapsed_time(ev[2]))
+            for ki, k in enumerate(self.kernels):
+                seg.setdefault(f"gather_{k}", []).append(ev[2 + ki].elapsed_time(ev[3 + ki]))
+        return t0.elapsed_time(t1), {k: float(np.mean(v)) for k, v in seg.items()}, loaded_g, clk
+
+    def close(self):
+        for pl in self.plans:
+            pl.close()
+
 # inputs and final maps of the benchmark run, for the oracle comparison
 _ORACLE_CHECK = []
+# (block name, thunk) pairs: oracle comparisons of the extra measurements, run
+# after every timed part; each thunk returns the block's "oracle_error"
+_ORACLE_LATER = []
 
 
 def run_swih(args, rank, world, local_rank):
@@ -205,45 +309,12 @@ def run_swih(args, rank, world, local_rank):
     kernels = tuple(k for k in KERNELS if k in args.kernels.split(","))
     tx, ty = cfg["target_centre"]
     stream = torch.cuda.Stream(device=dev)
-    d_img = torch.from_numpy(img).to(dev)
-    me = tuple(k for k in kernels if k != "gaussian")
-    plan_me = S.Plan(S.make_desc(H, W, bins=B, kernels=me, max_win=(81, 81))) if me else None
-    plan_g = (S.Plan(S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(81, 81)))
-              if "gaussian" in kernels else None)
-    plans = [pl for pl in (plan_me, plan_g) if pl is not None]
-    plan_of = {"manhattan": plan_me, "euclidean": plan_me, "gaussian": plan_g}
-    info_me = plan_me.info() if plan_me else None
-    info_g = plan_g.info() if plan_g else None
-
-    jobs = [(k, w) for k in kernels for w in WINDOWS]
-    job_of = {k: [j for j, (kk, _) in enumerate(jobs) if kk == k] for k in kernels}
-    # targets: the window of each kernel and size centred on object 0 (untimed set-up)
-    for pl in plans:
-        pl.build_ih(d_img, stream)
-    targets = torch.empty((len(jobs), B), dtype=torch.float32, device=dev)
-    for j, (k, w) in enumerate(jobs):
-        plan_of[k].local_hist(k, w, w, tx, ty, 1, 1, targets[j], stream)
-    maps = [torch.empty((H - w + 1, W - w + 1), dtype=torch.float32, device=dev) for _, w in jobs]
-    for pl in plans:
-        pl.sync_status(stream)
-
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        if plan_me:
-            plan_me.build_ih(d_img, stream)
-        if ev is not None:
-            ev[1].record(stream)
-        if plan_g:
-            plan_g.build_ih(d_img, stream)
-        if ev is not None:
-            ev[2].record(stream)
-        for ki, k in enumerate(kernels):  # the kernel's windows in one launch (multi-scale search)
-            js = job_of[k]
-            plan_of[k].likelihood_scales(k, [(jobs[j][1], jobs[j][1]) for j in js], [targets[j] for j in js],
-                                         [maps[j] for j in js], stream)
-            if ev is not None:
-                ev[3 + ki].record(stream)
+    fr = FrameStep(S, dev, img, B, kernels, tx, ty, stream)
+    d_img = fr.d_img
+    plan_me, plan_g, plans, plan_of = fr.plan_me, fr.plan_g, fr.plans, fr.plan_of
+    info_me, info_g = fr.info_me, fr.info_g
+    jobs, job_of, targets, maps = fr.jobs, fr.job_of, fr.targets, fr.maps
+    step = fr.step
 
     n_ev = 3 + len(kernels)
     for _ in range(args.warmup):
@@ -336,6 +407,16 @@ def run_swih(args, rank, world, local_rank):
     if H != 1024 or B != 32:
         prof = None  # the committed counters are for the benchmark workload only
     traffic = profile_traffic(prof, src) if prof else None
+
+    # ---- the same step over a timed region of at least 1.5 s (>= 400 steps),
+    # with the clocks sampled throughout: the sustained rate beside the K-step line
+    sustained = None
+    if world == 1 and not args.no_extras:
+        n_sus = max(400, int(np.ceil(1500.0 / max(ms / args.steps, 1e-3))))
+        sus_ms, sus_seg, _, sus_clk = fr.timed(n_sus, ClockSampler(local_rank))
+        sustained = {"steps": n_sus, "timed_s": sus_ms * 1e-3, "ms_per_step": sus_ms / n_sus,
+                     "value": fr.windows_per_step * n_sus / (sus_ms * 1e-3), "unit": "windows/s",
+                     "per_launch_ms": sus_seg, "clocks": sus_clk}
 
     # ---- end to end through the C ABI from pinned host buffers. Every step
     # uploads its frame and targets and downloads its nine maps. The transfers
@@ -457,10 +538,151 @@ def run_swih(args, rank, world, local_rank):
         "per_launch_ms": seg_ms,
         "clocks": clk,
     }
+    if sustained:
+        line["sustained"] = sustained
     if line_note:
         line["note"] = line_note
     return line
 
+
+
+# ----------------------------------------------------------------------------- dense scene
+def stage_bytes(fr, H, W, B):
+    """Dense algorithmic bytes of each stage of one FrameStep: a build reads the
+    pixels, writes the bins and every integral-histogram element of its plan
+    once; a kernel's gather launch reads every element of the planes its kernel
+    uses once per window and writes each window's map."""
+    def ih(info, terms):
+        return terms * B * H * W * info.elem_bytes
+
+    out = {}
+    if fr.info_me:
+        out["build_me"] = 2 * H * W + ih(fr.info_me, fr.info_me.n_terms)
+    if fr.info_g:
+        out["build_g"] = 2 * H * W + ih(fr.info_g, fr.info_g.n_terms)
+    used = {"manhattan": 3, "euclidean": 5, "gaussian": fr.info_g.n_terms if fr.info_g else 0}
+    for k in fr.kernels:
+        info = fr.info_g if k == "gaussian" else fr.info_me
+        out[f"gather_{k}"] = sum(ih(info, used[k]) + 4 * (H - w + 1) * (W - w + 1) for w in fr.windows)
+    return out
+
+
+def run_dense_scene(args, dev):
+    """The benchmark step on a frame without spatial structure: 1024x1024 u8
+    pixels i.i.d. uniform over 0-255 (seed 1, the generator of the 128x128
+    case), B = 32, the same kernels and windows. Every row holds nearly every
+    bin and every window holds most bins, so the scans store every row and the
+    gathers skip almost nothing: the worst case for the method's exact
+    skipping of absent bins and rows. Timed like the main line (CUDA events,
+    per launch); the roofline uses the dense bytes of each stage."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    H = W = 1024
+    B = 32
+    img = synth.uniform_image(H, W, 8, seed=1)
+    stream = torch.cuda.Stream(device=dev)
+    fr = FrameStep(S, dev, img, B, KERNELS, W // 2, H // 2, stream)
+    try:
+        for _ in range(max(3, args.warmup)):
+            fr.step()
+        steps = max(args.steps, 50)
+        ms, seg, loaded_g, _ = fr.timed(steps)
+        algo = stage_bytes(fr, H, W, B)
+    finally:
+        fr.close()
+    peak, peak_kind = read_peaks()
+    dom = max(seg, key=seg.get)
+    stages = {k: {"ms": seg[k], "dense_bytes": algo[k], "dense_gbs": algo[k] / (seg[k] * 1e-3) / 1e9,
+                  "frac_dense": algo[k] / (seg[k] * 1e-3) / 1e9 / peak} for k in seg}
+    stages["gather_gaussian"]["loaded_bytes"] = loaded_g
+    ach = algo[dom] / (seg[dom] * 1e-3) / 1e9
+    return {
+        "workload": ("1024x1024 u8 i.i.d. uniform 0-255 (seed 1), B=32, Manhattan/Euclidean/Gaussian "
+                     "x windows 21/41/81, full valid maps (no spatial structure: nothing to skip)"),
+        "windows_per_step": fr.windows_per_step, "steps": steps, "ms_per_step": ms / steps,
+        "windows_per_s": fr.windows_per_step * steps / (ms * 1e-3),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": algo[dom],
+                     "bytes_basis": "dense: every integral-histogram element of the stage, once, plus the maps",
+                     "avg_launch_ms": seg[dom]},
+        "stages": stages,
+    }
+
+
+# ----------------------------------------------------------------------------- small frame latency
+def run_small_frame(args, dev, reps=200):
+    """Latency of one small search (128x128 u8 i.i.d. frame, B = 16, one 31x31
+    Manhattan map, 9,604 windows): its integral histograms fit in L2 and the
+    GPU is far from full, so the figure of merit is the time per call. Device
+    latency = CUDA events around build + likelihood on device-resident input;
+    end-to-end latency = host time from the upload of the frame from pinned
+    memory to the map copied back, synchronised per call. The map is compared
+    with the FP64 oracle after the timed parts."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    cfg = synth.config1()
+    img = cfg["image"]
+    H, W = img.shape
+    B, w = cfg["B"], cfg["windows"][0]
+    tx, ty = cfg["target_centre"]
+    stream = torch.cuda.Stream(device=dev)
+    h_img = torch.from_numpy(img).pin_memory()
+    d_img = h_img.to(dev)
+    h_map = torch.empty((H - w + 1, W - w + 1), dtype=torch.float32).pin_memory()
+    d_map = torch.empty((H - w + 1, W - w + 1), dtype=torch.float32, device=dev)
+    q = torch.empty((1, 1, B), dtype=torch.float32, device=dev)
+    dev_ms, e2e_ms = [], []
+    with S.Plan(S.make_desc(H, W, bins=B, kernels=("manhattan",), max_win=(w, w))) as p:
+        p.build_ih(d_img, stream)
+        p.local_hist("manhattan", w, w, tx, ty, 1, 1, q, stream)  # set-up: the target window
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(reps + 10):
+            e0.record(stream)
+            p.build_ih(d_img, stream)
+            p.likelihood("manhattan", w, w, q.reshape(B), d_map, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 10:
+                dev_ms.append(e0.elapsed_time(e1))
+        for i in range(reps + 10):
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                d_img.copy_(h_img, non_blocking=True)
+                p.build_ih(d_img, stream)
+                p.likelihood("manhattan", w, w, q.reshape(B), d_map, stream)
+                h_map.copy_(d_map, non_blocking=True)
+            stream.synchronize()
+            if i >= 10:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        p.sync_status(stream)
+        target = q.reshape(B).cpu().numpy().astype(np.float64)
+    out = {
+        "workload": "128x128 u8 i.i.d. uniform (seed 1), B=16, one 31x31 Manhattan map (9,604 windows)",
+        "reps": reps,
+        "device_latency_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
+        "e2e_latency_ms": {"p50": float(np.percentile(e2e_ms, 50)), "p99": float(np.percentile(e2e_ms, 99)),
+                           "h2d_bytes": H * W, "d2h_bytes": h_map.numel() * 4},
+        "windows_per_call": h_map.numel(),
+    }
+    if not args.no_cpu_baseline:
+        _ORACLE_LATER.append(("small_frame", lambda: small_frame_error(img, B, w, target, h_map.numpy().copy())))
+    return out
+
+
+def small_frame_error(img, B, w, target, got):
+    """Largest |GPU - oracle| over the whole 128x128 map (FP64 brute force)."""
+    from oracle import swih_oracle as O
+
+    bins = O.quantize(img, 8, B)
+    ref = O.likelihood_map(bins, B, O.kernel_weights("manhattan", w, w), target)
+    return {"max_abs": float(np.abs(got.astype(np.float64) - ref).max()), "tolerance": 1e-5,
+            "sample": "every valid centre"}
 
 # ----------------------------------------------------------------------------- batches
 def run_regions(args, dev, per_region=True):
@@ -546,6 +768,19 @@ def run_regions(args, dev, per_region=True):
         batch_ms = e0.elapsed_time(e1) / steps
     diff = (max((m - r).abs().max().item() for ms, rs in zip(maps, ref) for m, r in zip(ms, rs))
             if per_region else None)
+    if per_region and not args.no_cpu_baseline:
+        # sampled centres of every (region, scale) map, copied back for the oracle
+        rng = np.random.default_rng(13)
+        samples = []
+        for i, ((x0, y0, w, h), ks, ms) in enumerate(zip(rois, wins, maps)):
+            for k, m in zip(ks, ms):
+                r = (k - 1) // 2
+                cx = rng.integers(r, w - r, 64)
+                cy = rng.integers(r, h - r, 64)
+                idx = torch.from_numpy((cy - r) * (w - k + 1) + (cx - r)).to(dev)
+                samples.append((i, k, cx, cy, m.reshape(-1)[idx].cpu().numpy()))
+        tg = targets.cpu().numpy().astype(np.float64)
+        _ORACLE_LATER.append(("batched_regions", lambda: regions_error(img, B, rois, samples, tg)))
     del maps, ref
     torch.cuda.empty_cache()
     return {
@@ -563,11 +798,19 @@ def run_regions(args, dev, per_region=True):
 
 
 # ----------------------------------------------------------------------------- large frame
-def run_large_frame(args, dev, budget_gb=100):
+def run_large_frame(args, dev, budget_gb=100, passes=3):
     """8192x8192 u16 frame, B = 64, Gaussian and Euclidean kernels at windows
     15/25/43/75/127: the integral histograms (25 terms, 64-bit) would need
     ~860 GB, so the frame is streamed in bands within budget_gb of device
-    memory; one pass = every band's quantise + scan + 10 gathers (CUDA graph)."""
+    memory; one pass = every band's quantise + scan + 10 gathers (CUDA graph).
+
+    Reported: windows/s of the graph replay (CUDA events, inputs resident);
+    per-stage times of one pass launched stage by stage with events between
+    stages, and the roofline of the dominant stage (bytes the gathers loaded,
+    counted by the kernels, or the scan's dense bytes); an end-to-end rate
+    with the frame uploaded from pinned host memory and all ten maps copied
+    back every pass; and the largest |GPU - oracle| over a 512x512 block of
+    centres that straddles the first band boundary (after the timed parts)."""
     import torch
 
     from paper_1705_03524_gb300 import swih as S
@@ -577,43 +820,114 @@ def run_large_frame(args, dev, budget_gb=100):
     img = cfg["image"]
     H, W = img.shape
     B = cfg["B"]
-    d_img = torch.from_numpy(img.view(np.int16)).to(dev)
-    del img
+    h_img = torch.from_numpy(img.view(np.int16)).pin_memory()
+    d_img = h_img.to(dev)
     stream = torch.cuda.Stream(device=dev)
-    tgt = torch.rand((len(cfg["kernels"]) * len(cfg["windows"]), B), device=dev) + 0.01
+    n_jobs = len(cfg["kernels"]) * len(cfg["windows"])
+    g = torch.Generator(device="cpu").manual_seed(4)
+    tgt = (torch.rand((n_jobs, B), generator=g) + 0.01).to(dev)
     tgt /= tgt.sum(1, keepdim=True)  # targets: positive normalised histograms (set-up)
-    jobs, maps = [], []
+    jobs, maps, job_kw = [], [], []
     for k in cfg["kernels"]:
         for w in cfg["windows"]:
             m = torch.empty((H - w + 1, W - w + 1), device=dev)
             jobs.append(S.make_frame_job(k, w, w, tgt[len(maps)], m))
             maps.append(m)
+            job_kw.append((k, w))
     wpp = sum(m.numel() for m in maps)
     desc = S.make_desc(H, W, pixel_type=S.SWIH_PIXEL_U16, bitdepth=16, bins=B, kernels=cfg["kernels"],
                        max_win=(127, 127), hbm_budget_bytes=budget_gb << 30)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    passes = 3
+    h_maps = [torch.empty(m.shape, dtype=torch.float32).pin_memory() for m in maps]
     with S.Stream(desc, jobs, d_img) as st:
         info = st.info()
         st.run(stream)
         st.sync_status(stream)
+        st.load_bytes(reset=True)
         e0.record(stream)
         for _ in range(passes):
             st.run(stream)
         e1.record(stream)
         st.sync_status(stream)
-    ms = e0.elapsed_time(e1) / passes
-    del maps
-    torch.cuda.empty_cache()
-    return {
+        ms = e0.elapsed_time(e1) / passes
+        loaded = {k: v / passes for k, v in st.load_bytes(reset=True).items() if v}
+        stages = st.run_timed(stream)
+        st.sync_status(stream)
+        # end to end: frame up from pinned memory, the pass, every map back
+        e2e_passes = 2
+        e0.record(stream)
+        for _ in range(e2e_passes):
+            with torch.cuda.stream(stream):
+                d_img.copy_(h_img, non_blocking=True)
+                st.run(stream)
+                for hm, m in zip(h_maps, maps):
+                    hm.copy_(m, non_blocking=True)
+        e1.record(stream)
+        st.sync_status(stream)
+        e2e_ms = e0.elapsed_time(e1) / e2e_passes
+    # dense bytes of a pass: each band region's planes once per job (gathers),
+    # every element of the band's planes written once (scan)
+    R, Hb, nb = 63, info["band_height"], info["n_bands"]
+    rows = [(H if k == nb - 1 else min(H, (k + 1) * Hb + 2 * R)) - k * Hb for k in range(nb)]
+    terms = {"gaussian": 25, "euclidean": 5}
+    dense = {"scan": sum(r * W * (2 + 1 + 25 * B * 8) for r in rows)}
+    for k in cfg["kernels"]:
+        dense[k] = sum(len(cfg["windows"]) * terms[k] * B * r * W * 8 for r in rows)
+    peak, peak_kind = read_peaks()
+    dom = max(stages, key=stages.get)
+    if dom in loaded:
+        dom_bytes, basis = loaded[dom] + 4.0 * sum(
+            m.numel() for (k, _), m in zip(job_kw, maps) if k == dom), (
+            "integral-histogram row segments the gathers of this kernel loaded over all bands "
+            "(counted by the kernels) + the maps")
+    else:
+        dom_bytes, basis = dense[dom], "dense: every element of every band's planes written once, plus pixels and bins"
+    ach = dom_bytes / (stages[dom] * 1e-3) / 1e9
+    out = {
         "workload": ("8192x8192 u16 fractal terrain + 200 blobs, B=64, Gaussian + Euclidean x windows "
                      "15/25/43/75/127, full valid maps, streamed in bands"),
-        "windows_per_pass": wpp, "ms_per_pass": ms, "windows_per_s": wpp / (ms * 1e-3),
-        "band_height": info["band_height"], "n_bands": info["n_bands"],
+        "windows_per_pass": wpp, "ms_per_pass": ms, "windows_per_s": wpp / (ms * 1e-3), "passes": passes,
+        "band_height": Hb, "n_bands": nb,
         "workspace_gb": info["workspace_bytes"] / 1e9,
-        "halo_rows_per_band": 126,
+        "halo_rows_per_band": 2 * R,
         "whole_frame_ih_gb": 25 * B * H * W * 8 / 1e9,
+        "stage_ms_per_pass": stages,
+        "loaded_bytes_per_pass": loaded, "dense_bytes_per_pass": dense,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": dom_bytes,
+                     "bytes_basis": basis, "launch": "one pass, summed over bands (stage by stage)",
+                     "avg_launch_ms": stages[dom]},
+        "e2e": {"value": wpp / (e2e_ms * 1e-3), "unit": "windows/s", "ms_per_pass": e2e_ms,
+                "h2d_bytes_per_step": h_img.numel() * 2, "d2h_bytes_per_step": sum(m.numel() * 4 for m in h_maps)},
     }
+    if not args.no_cpu_baseline:
+        rng = np.random.default_rng(4)
+        bx = int(rng.integers(R, W - R - 512))
+        by = max(R, min(H - R - 512, R + Hb - 256))  # rows on both sides of the first band boundary
+        sub = img[by - R: by + 512 + R, bx - R: bx + 512 + R].copy()
+        blocks = [hm.numpy()[by - (w - 1) // 2: by - (w - 1) // 2 + 512, bx - (w - 1) // 2: bx - (w - 1) // 2 + 512].copy()
+                  for hm, (_, w) in zip(h_maps, job_kw)]
+        targets = tgt.cpu().numpy().astype(np.float64)
+        _ORACLE_LATER.append(("large_frame", lambda: large_frame_error(sub, B, job_kw, targets, blocks, bx, by, R)))
+    del maps, h_maps
+    torch.cuda.empty_cache()
+    return out
+
+
+def large_frame_error(sub, B, job_kw, targets, blocks, bx, by, R, n=512):
+    """Largest |GPU - oracle| per map over an n x n block of centres; sub is
+    the frame's pixels around the block (an R-pixel halo on every side) and
+    blocks[j] the GPU's values of map j at those centres."""
+    from oracle import swih_oracle as O
+
+    bins = O.quantize(sub, 16, B)
+    per = {}
+    for j, ((k, w), got) in enumerate(zip(job_kw, blocks)):
+        ref = O.likelihood_rect(bins, B, O.kernel_weights(k, w, w), targets[j], R, R, n, n)
+        per[f"{k}_{w}"] = float(np.abs(got.astype(np.float64) - ref).max())
+    return {"max_abs": max(per.values()), "tolerance": 1e-5, "per_map": per,
+            "sample": (f"{n}x{n} centres at x {bx}..{bx + n - 1}, y {by}..{by + n - 1} (across the first band "
+                       "boundary), every map, FP64 brute force with the targets the GPU used")}
 
 
 # ----------------------------------------------------------------------------- exponential kernel
@@ -761,6 +1075,21 @@ def run_serving(args, dev, n_queries=400, rate=2000.0):
     server.update({"mean_queries_per_micro_batch": float(np.mean([c.batch_queries for c in comps])),
                    "failed": bad, "config": {k: v for k, v in srv_cfg.items()}})
     server_out = [o.clone() for o in outs]
+    if not args.no_cpu_baseline:
+        rng = np.random.default_rng(17)
+        samples = []
+        for i, q in enumerate(qs):
+            off = 0
+            for t in range(len(q["targets"])):
+                for (w, h) in q["windows"]:
+                    nx, ny = q["w"] - w + 1, q["h"] - h + 1
+                    cx = rng.integers(0, nx, 16)
+                    cy = rng.integers(0, ny, 16)
+                    idx = torch.from_numpy(off + cy * nx + cx).to(dev)
+                    samples.append((i, t, w, h, cx + (w - 1) // 2, cy + (h - 1) // 2,
+                                    server_out[i][idx].cpu().numpy()))
+                    off += nx * ny
+        _ORACLE_LATER.append(("serving", lambda: serving_error(frames, qs, samples)))
 
     stream = torch.cuda.Stream(device=dev)
     lat = []
@@ -879,7 +1208,7 @@ def oracle_errors(img, B, jobs, maps, targets, n=2048, seed=11):
     bins = O.quantize(img, 8, B)
     H, W = bins.shape
     rng = np.random.default_rng(seed)
-    per = {}
+    per, approx = {}, {}
     for j, (k, w) in enumerate(jobs):
         r = (w - 1) // 2
         cx = rng.integers(r, W - r, n)
@@ -887,9 +1216,59 @@ def oracle_errors(img, B, jobs, maps, targets, n=2048, seed=11):
         ref = O.likelihood_at(bins, B, O.kernel_weights(k, w, w), np.asarray(targets[j], dtype=np.float64), cx, cy)
         got = np.asarray(maps[j], dtype=np.float64)[cy - r, cx - r]
         per[f"{k}_{w}"] = float(np.abs(got - ref).max())
+        if k == "gaussian":
+            true = O.likelihood_at(bins, B, O.true_gaussian(w, w), np.asarray(targets[j], dtype=np.float64),
+                                   cx, cy)
+            approx[f"{k}_{w}"] = float(np.abs(got - true).max())
     return {"max_abs": max(per.values()), "tolerance": 1e-5, "per_map": per,
+            "gaussian_vs_true_gaussian": {
+                "per_map": approx,
+                "note": ("approximation error, not parity: the Gaussian kernel is the degree-2 polynomial "
+                         "stand-in P(dx^2/rx^2) P(dy^2/ry^2) fitted to exp(-d^2/2 sigma^2), sigma = w/4; this "
+                         "is the largest |L_gpu - L| with L the brute-force likelihood under the exact "
+                         "Gaussian weights, same centres and targets")},
             "sample": (f"{n} random valid centres per map (seed {seed}), FP64 brute-force oracle with the "
                        "targets the GPU used, against the maps copied back at the end of the end-to-end run")}
+
+
+def regions_error(img, B, rois, samples, targets):
+    """Largest |GPU - oracle| over 64 sampled centres of each (region, scale) map."""
+    from oracle import swih_oracle as O
+
+    worst = 0.0
+    n = 0
+    for i, k, cx, cy, got in samples:
+        x0, y0, w, h = rois[i]
+        bins = O.quantize(img[y0:y0 + h, x0:x0 + w], 16, B)
+        ref = O.likelihood_at(bins, B, O.kernel_weights("gaussian", k, k), targets[i], cx, cy)
+        worst = max(worst, float(np.abs(got.astype(np.float64) - ref).max()))
+        n += cx.size
+    return {"max_abs": worst, "tolerance": 1e-5,
+            "sample": f"{n} centres: 64 random valid centres of every (region, scale) map, FP64 brute force"}
+
+
+def serving_error(frames, qs, samples):
+    """Largest |GPU - oracle| over 16 sampled centres of every (query, target,
+    window) map the server returned."""
+    from oracle import swih_oracle as O
+
+    worst = 0.0
+    n = 0
+    cache = {}
+    for i, t, w, h, cx, cy, got in samples:
+        q = qs[i]
+        img, bd = frames[q["frame"]]
+        key = i
+        if key not in cache:
+            cache.clear()
+            cache[key] = O.quantize(img[q["y0"]:q["y0"] + q["h"], q["x0"]:q["x0"] + q["w"]], bd, q["B"])
+        ref = O.likelihood_at(cache[key], q["B"], O.kernel_weights(q["kernel"], w, h),
+                              q["targets"][t].astype(np.float64), cx, cy)
+        worst = max(worst, float(np.abs(got.astype(np.float64) - ref).max()))
+        n += cx.size
+    return {"max_abs": worst, "tolerance": 1e-5,
+            "sample": f"{n} centres: 16 random valid centres of every (query, target, window) map, FP64 brute force"}
+
 
 
 def oracle_sample(budget_s: float, seed: int = 7):
@@ -1017,23 +1396,38 @@ def main():
         import torch.distributed as tdist
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    t0 = time.perf_counter()
     line = run_swih(args, rank, world, local_rank)
+    progress(f"frame benchmark: {time.perf_counter() - t0:.1f} s")
     if world == 1 and not args.no_extras:
         import torch
         torch.cuda.empty_cache()
         dev = torch.device("cuda", local_rank)
-        line["batched_regions"] = run_regions(args, dev)
-        line["serving"] = run_serving(args, dev, n_queries=args.serve_queries)
-        line["large_frame"] = run_large_frame(args, dev)
-        line["exponential"] = run_exponential(args, dev)
+        for name, fn in (("small_frame", run_small_frame), ("dense_scene", run_dense_scene),
+                         ("batched_regions", run_regions),
+                         ("serving", lambda a, d: run_serving(a, d, n_queries=a.serve_queries)),
+                         ("large_frame", run_large_frame), ("exponential", run_exponential)):
+            t0 = time.perf_counter()
+            line[name] = fn(args, dev)
+            progress(f"{name}: {time.perf_counter() - t0:.1f} s")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
         res = oracle_sample(args.cpu_seconds)
+        progress(f"cpu baseline: {time.perf_counter() - t0:.1f} s")
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
         if _ORACLE_CHECK:
             try:
                 line["oracle_error"] = oracle_errors(*_ORACLE_CHECK)
             except Exception as e:  # the bench line is printed either way
                 line["oracle_error"] = {"error": repr(e)}
+        for name, thunk in _ORACLE_LATER:
+            if name in line:
+                t0 = time.perf_counter()
+                try:
+                    line[name]["oracle_error"] = thunk()
+                except Exception as e:
+                    line[name]["oracle_error"] = {"error": repr(e)}
+                progress(f"oracle check of {name}: {time.perf_counter() - t0:.1f} s")
     if rank == 0:
         line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

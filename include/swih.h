@@ -227,9 +227,61 @@ typedef struct swih_plan_info {
      * d_row_map[b * height + y]. NULL: every row is stored (band_rows > 64,
      * or more than 32767 rows). */
     const int32_t *d_row_map;
+    /* Feature channels (swih_plan_channels; 1 for a plan over one image): the
+     * bin plane of channel c is at d_bins + c * height * bins_pitch and holds
+     * global bin numbers (channel c's bins follow those of channels 0..c-1). */
+    int32_t n_channels;
 } swih_plan_info;
 
 swih_status swih_plan_get_info(swih_plan_t plan, swih_plan_info *info);
+
+/* ---------------------------------------------------------------- feature channels
+ * Several features per pixel, each with its own likelihood map (Sec. 4: the
+ * tracker matches chromatic, shape and texture features, one likelihood map per
+ * feature). A channel is one single-valued image of the plan's size with its
+ * own pixel type, bit depth, row pitch and bin count B_c, quantised with the
+ * equal-width Q of Sec. 2.1 into its own bins. The plan numbers the bins of
+ * all channels globally: channel c owns bins [bin0_c, bin0_c + B_c) with bin0_c =
+ * B_0 + ... + B_{c-1}, B = sum B_c <= 256. Every pixel falls in exactly one bin
+ * of each channel, so every channel's kernel-weighted window histogram has the
+ * same total weight M and normalises by it. One quantisation launch per
+ * channel, one scan launch for the integral histograms of every bin of every
+ * channel, and one gather launch for every channel's map.
+ *
+ * On a channel plan swih_local_hist returns the histograms over all B global
+ * bins (each channel's part sums to 1), and swih_likelihood with a [B] target
+ * returns the sum over channels of the per-channel coefficients (targets that
+ * sum to 1 per channel). The exponential kernel is not served (UNSUPPORTED). */
+#define SWIH_MAX_CHANNELS 8
+
+typedef struct swih_channel_desc {
+    int64_t pitch_bytes;       /* row stride in bytes, >= width * pixel size */
+    int32_t pixel_type;        /* swih_pixel_type */
+    int32_t bitdepth;          /* significant bits, as in swih_plan_desc */
+    int32_t bins;              /* B_c >= 1 */
+    int32_t reserved;          /* 0 */
+} swih_channel_desc;
+
+/* Plan over n_channels (1..SWIH_MAX_CHANNELS) feature channels. From *desc:
+ * height, width, kernel_mask, Gaussian settings, windows, precision, band_rows,
+ * hbm_budget_bytes, wedding_rings; its bins, pixel_type, bitdepth and
+ * pitch_bytes are ignored (taken from the channels). */
+swih_status swih_plan_channels(const swih_plan_desc *desc, int n_channels, const swih_channel_desc *channels,
+                               swih_plan_t *out);
+
+/* Steps (1)-(2) of Sec. 1 for every channel: d_images is a host array of
+ * n_channels device pointers, image c laid out as channels[c] says. */
+swih_status swih_build_ih_channels(swih_plan_t plan, const void *const *d_images, void *stream);
+
+/* Steps (3)-(5) and the matching of Fig. 3 for every channel at once:
+ * d_maps (float32 [n_channels][H-win_h+1][W-win_w+1], packed, channel-major)
+ * receives each channel's map L_c(x) = sum over channel c's bins of
+ * sqrt(H_x(b) q(b)). d_target: float32 [B], the channels' target histograms
+ * side by side, each channel's part summing to 1 (not checked). The per-channel
+ * targets are laid out in a table inside the plan on the stream, so calls on
+ * one plan must not overlap on the GPU. */
+swih_status swih_likelihood_channels(swih_plan_t plan, int kernel, int win_w, int win_h, const float *d_target,
+                                     float *d_maps, void *stream);
 
 /* Kernels this library has enqueued in this process so far, counted on the
  * host at each launch (a CUDA graph's kernels count once, when the graph is
@@ -348,7 +400,7 @@ swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, 
  *   desc      plan description (hbm_budget_bytes is ignored)
  *   d_image   device image as for swih_build_ih
  *   d_ih      device output, 16-byte aligned, ih_bytes long; NULL = size
- *             query: fill *layout and return without touching the device
+ *             query: fill *layout and return without enqueueing device work
  *   ih_bytes  capacity of d_ih; must be >= layout->workspace_bytes
  *   d_status  optional device uint32 the scan ORs its error bits into
  *             (1 = a bounded look-back wait gave up); the caller clears it.
@@ -361,9 +413,10 @@ swih_status swih_set_gather_config(swih_plan_t plan, int kernel, int tile_cols, 
  *   stream    as for swih_build_ih
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine. The first
- * call on each device looks up the static array's device address
- * (cudaGetSymbolAddress) with that device current and caches it; make that
- * first call before any stream capture begins. Every call shares the one
+ * call on each device, a size query included, looks up the static array's
+ * device address (cudaGetSymbolAddress) with that device current and caches
+ * it; make that first call before any stream capture begins. A call that
+ * cannot look the address up (no usable device) returns SWIH_ERR_CUDA. Every call shares the one
  * array and leaves its contents behind; the tile flags are cleared at each
  * call. Calls whose work overlaps on the GPU (other streams, other host
  * threads) race on the array and must be serialised by the caller. */
@@ -416,6 +469,20 @@ swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *j
 
 /* Enqueue one pass (every band, every job) on the stream. */
 swih_status swih_stream_run(swih_stream_t st, void *stream);
+
+/* One pass as swih_stream_run, for measurement: the bands' launches are
+ * enqueued one by one (not as the graph) with CUDA events between stages, the
+ * stream is synchronised, and stage_ms (7 floats) receives milliseconds summed
+ * over the bands: stage_ms[0] = table upload + quantise + scan + row map,
+ * stage_ms[1 + k] = the window gathers of kernel k (swih_kernel, 0..5).
+ * Results are those of swih_stream_run. */
+swih_status swih_stream_run_timed(swih_stream_t st, void *stream, float *stage_ms);
+
+/* Integral-histogram bytes the tiled gathers of this streamed pass requested
+ * since the last reset (as swih_plan_load_bytes), per kernel: bytes[k] for
+ * swih_kernel k = 0..4 (5 entries). Synchronises the device; reset = 1 zeroes
+ * the counts. */
+swih_status swih_stream_load_bytes(swih_stream_t st, uint64_t *bytes, int reset);
 
 /* As swih_sync_status, for a streamed pass. */
 swih_status swih_stream_sync_status(swih_stream_t st, void *stream);

@@ -392,6 +392,19 @@ def likelihood_map(bins, B, K, q) -> np.ndarray:
     return likelihood_rect(bins, B, K, q, x0, y0, nx, ny)
 
 
+def likelihood_channels_map(bins_list, B_list, K, q_list) -> np.ndarray:
+    """Per-feature likelihood maps, float64 [C, H - h + 1, W - w + 1].
+
+    Sec. 4: the tracker computes one likelihood map per feature (chromatic,
+    shape, texture) by sliding-window histogram matching. Each feature c is its
+    own image of bins in [0, B_c); its map is the brute-force likelihood of its
+    own kernel-weighted histograms against its own target q_c.
+    """
+    if not (len(bins_list) == len(B_list) == len(q_list)) or not bins_list:
+        raise ValueError("one bin image, bin count and target per channel")
+    return np.stack([likelihood_map(b, B, K, q) for b, B, q in zip(bins_list, B_list, q_list)])
+
+
 def target_hist(bins, B, K, xc, yc) -> np.ndarray:
     """Normalised weighted histogram of the window centred at (xc, yc), float64 [B]."""
     return normalise(hist_at(bins, B, K, [xc], [yc]))[0]

@@ -2,6 +2,8 @@
 //
 //   b = floor(min(v, 2^bitdepth - 1) * B / 2^bitdepth)   (equal-width bins)
 //
+// (plus a constant bin0 for a feature channel whose bins follow other channels')
+//
 // One thread per 16 consecutive pixels of a row. With a 16-byte aligned image
 // a u8 chunk is one 16-byte load and a u16 chunk two; the 16 bins leave as one
 // 16-byte store. HBM-bound: (pixel bytes + 1) bytes per pixel.
@@ -20,7 +22,7 @@ __device__ __forceinline__ uint32_t bin_of(uint32_t v, uint32_t vmax, uint32_t B
 template <int PB>
 __device__ __forceinline__ void quantize_chunk(const uint8_t *image, int64_t pitch, int W, int y, int x0,
                                                bool vec, uint32_t vmax, uint32_t B, int bitdepth,
-                                               uint8_t *bins, int64_t bins_pitch)
+                                               uint8_t *bins, int64_t bins_pitch, uint32_t bin0 = 0)
 {
     const uint8_t *row = image + (int64_t)y * pitch;
     uint32_t v[16];
@@ -50,7 +52,7 @@ __device__ __forceinline__ void quantize_chunk(const uint8_t *image, int64_t pit
     }
     uint32_t o[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < 16; ++i) o[i >> 2] |= bin_of(v[i], vmax, B, bitdepth) << (8 * (i & 3));
+    for (int i = 0; i < 16; ++i) o[i >> 2] |= (bin0 + bin_of(v[i], vmax, B, bitdepth)) << (8 * (i & 3));
     *reinterpret_cast<uint4 *>(bins + (int64_t)y * bins_pitch + x0) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256) quantize_kernel(QuantParams p)
         const int y = (int)(c / chunks_per_row);
         const int x0 = (int)(c - (long long)y * chunks_per_row) << 4;
         quantize_chunk<PB>(p.image, p.pitch, p.W, y, x0, p.vec != 0, vmax, (uint32_t)p.B, p.bitdepth, p.bins,
-                           p.bins_pitch);
+                           p.bins_pitch, (uint32_t)p.bin0);
     }
 }
 

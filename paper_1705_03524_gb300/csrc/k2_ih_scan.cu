@@ -202,6 +202,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     const bool has_cols = x0 < r.W;               // any real column in this thread
     const bool in_pitch = x0 < r.ih_pitch;        // chunk lies inside a stored row
     const uint8_t bb = (uint8_t)b;
+    const uint8_t *bins = r.bins + (int64_t)p.ch_of_bin[b] * p.ch_stride;  // the plane of b's feature channel
     if (ticket == p.stall_tile && band == 0) return;  // injected stall: publish nothing
 
     // ---- 1. band aggregate of [bin == b] * y^q per column, and which rows hold the bin
@@ -213,7 +214,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     if (has_cols) {
         for (int y = y_begin; y < y_end; ++y) {
             uint8_t v[E];
-            load_bins<E>(r.bins + (int64_t)y * r.bins_pitch, x0, v);
+            load_bins<E>(bins + (int64_t)y * r.bins_pitch, x0, v);
             if (p.sb_rows > 0) put_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
             bool hit[E];
             bool any = false;
@@ -323,7 +324,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     const int y_first = next_row(y_begin);
     uint8_t vnext[E];
     const bool cached = p.sb_rows > 0;  // each thread reads back the bins it stored in step 1
-    if (!cached && has_cols && y_first < y_end) load_bins<E>(r.bins + (int64_t)y_first * r.bins_pitch, x0, vnext);
+    if (!cached && has_cols && y_first < y_end) load_bins<E>(bins + (int64_t)y_first * r.bins_pitch, x0, vnext);
     // Rows without a pixel of bin b leave every column sum, hence every term's
     // row, as in the row above. With up to 3 terms per chain such a row is
     // copied from the row this thread stored last (still in L2) instead of
@@ -344,7 +345,7 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = vnext[e];
-                if (yn < y_end) load_bins<E>(r.bins + (int64_t)yn * r.bins_pitch, x0, vnext);
+                if (yn < y_end) load_bins<E>(bins + (int64_t)yn * r.bins_pitch, x0, vnext);
             }
             const T yq = ring_pow<T>((T)y, q);
 #pragma unroll

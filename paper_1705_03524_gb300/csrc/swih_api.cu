@@ -173,6 +173,8 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     if (!(sf > 0.0) || !std::isfinite(sf))
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "gauss_sigma_frac must be positive");
     const bool want_exp = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_EXPONENTIAL);
+    if (want_exp && pl->n_ch > 0)
+        return fail(nullptr, SWIH_ERR_UNSUPPORTED, "feature channels serve the integer kernels only (no exponential)");
     const double lam = d->exp_lambda == 0.0 ? 0.1 : d->exp_lambda;
     if (want_exp && !(lam >= 1.0 / 1024.0 && lam <= 16.0))
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "exp_lambda must be in [2^-10, 16]");
@@ -267,7 +269,8 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         off = (off + bytes + 255) / 256 * 256;
         return at;
     };
-    take((uint64_t)H * pl->bins_pitch);  // bins at offset 0
+    take((uint64_t)std::max(1, pl->n_ch) * H * pl->bins_pitch);  // bins at offset 0 (one plane per channel)
+    if (pl->n_ch > 0) pl->off_chtgt = take((uint64_t)pl->n_ch * d->bins * sizeof(float));
     pl->off_ih = take((uint64_t)pl->n_terms * d->bins * pl->plane * es);
     pl->off_agg = take(n_chains * pl->n_bands * pl->ih_pitch * es);
     pl->off_incl = take(n_chains * pl->n_bands * pl->ih_pitch * es);
@@ -566,6 +569,15 @@ swih_status swih_plan(const swih_plan_desc *desc, swih_plan_t *out)
         delete pl;
         return st;
     }
+    return swih::allocate_plan(pl, out);
+}
+
+}  // extern "C"
+
+namespace swih {
+
+swih_status allocate_plan(swih_plan_s *pl, swih_plan_t *out)
+{
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e != cudaSuccess) {
         delete pl;
@@ -589,35 +601,18 @@ swih_status swih_plan(const swih_plan_desc *desc, swih_plan_t *out)
     return SWIH_OK;
 }
 
-swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
+// Steps after quantisation: the weighted integral histograms (K2), the row map
+// and the exponential kernel's tables (K2e), from the plan's bin planes.
+swih_status build_scans(swih_plan_s *pl, cudaStream_t s)
 {
-    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
-    if (!d_image) return fail(pl, SWIH_ERR_INVALID_ARG, "d_image is NULL");
     const swih_plan_desc &d = pl->desc;
-    if (d.pixel_type == SWIH_PIXEL_U16 && (reinterpret_cast<uintptr_t>(d_image) & 1))
-        return fail(pl, SWIH_ERR_INVALID_ARG, "a U16 image must be 2-byte aligned");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-
-    QuantParams qp;
-    qp.image = static_cast<const uint8_t *>(d_image);
-    qp.pitch = d.pitch_bytes;
-    qp.H = d.height;
-    qp.W = d.width;
-    qp.B = d.bins;
-    qp.bitdepth = d.bitdepth;
-    qp.bins = reinterpret_cast<uint8_t *>(pl->d_mem);
-    qp.bins_pitch = pl->bins_pitch;
-    qp.pixel_bytes = d.pixel_type == SWIH_PIXEL_U8 ? 1 : 2;
-    qp.vec = (d.pitch_bytes % 16 == 0) && (reinterpret_cast<uintptr_t>(d_image) % 16 == 0);
-    cudaError_t e = launch_quantize(qp, s);
-    if (e != cudaSuccess) return cuda_fail(pl, "quantize launch", e);
-
+    cudaError_t e;
     e = cudaMemsetAsync(pl->d_mem + pl->off_flags, 0, pl->flags_bytes, s);
     if (e != cudaSuccess) return cuda_fail(pl, "cudaMemsetAsync(scan flags)", e);
 
     ScanParams sp;
     std::memset(&sp, 0, sizeof sp);
-    sp.bins = qp.bins;
+    sp.bins = reinterpret_cast<const uint8_t *>(pl->d_mem);
     sp.bins_pitch = pl->bins_pitch;
     sp.ih = pl->d_mem + pl->off_ih;
     sp.ih_pitch = pl->ih_pitch;
@@ -644,6 +639,11 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
     sp.spin_limit = 1LL << 22;  // with 64 ns sleeps: well under a few seconds
     sp.stall_tile = -1;
     sp.occ = pl->sparse_rows ? reinterpret_cast<unsigned long long *>(pl->d_mem + pl->off_occ) : nullptr;
+    if (pl->n_ch > 0) {  // bin b's chain reads its channel's bin plane
+        sp.ch_stride = (int64_t)d.height * pl->bins_pitch;
+        for (int c = 0; c < pl->n_ch; ++c)
+            for (int b = pl->ch_bin0[c]; b < pl->ch_bin0[c + 1]; ++b) sp.ch_of_bin[b] = (uint8_t)c;
+    }
     if (pl->inject == SWIH_INJECT_STALL_SCAN_TILE) {
         sp.stall_tile = 0;        // chain 0, band 0 never publishes
         sp.spin_limit = 1LL << 12;
@@ -659,7 +659,7 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
     if (pl->has_exp) {
         ExpScanParams xp;
         std::memset(&xp, 0, sizeof xp);
-        xp.bins = qp.bins;
+        xp.bins = reinterpret_cast<const uint8_t *>(pl->d_mem);
         xp.bins_pitch = pl->bins_pitch;
         xp.J = reinterpret_cast<unsigned long long *>(pl->d_mem + pl->off_exp);
         xp.pitch = pl->ih_pitch;
@@ -686,6 +686,37 @@ swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
     }
     pl->built = true;
     return SWIH_OK;
+}
+
+}  // namespace swih
+
+extern "C" {
+
+swih_status swih_build_ih(swih_plan_t pl, const void *d_image, void *stream)
+{
+    if (!pl) return fail(nullptr, SWIH_ERR_INVALID_ARG, "plan is NULL");
+    if (!d_image) return fail(pl, SWIH_ERR_INVALID_ARG, "d_image is NULL");
+    const swih_plan_desc &d = pl->desc;
+    if (d.pixel_type == SWIH_PIXEL_U16 && (reinterpret_cast<uintptr_t>(d_image) & 1))
+        return fail(pl, SWIH_ERR_INVALID_ARG, "a U16 image must be 2-byte aligned");
+    if (pl->n_ch > 0) return fail(pl, SWIH_ERR_INVALID_ARG, "a feature-channel plan is built by swih_build_ih_channels");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    QuantParams qp;
+    qp.image = static_cast<const uint8_t *>(d_image);
+    qp.pitch = d.pitch_bytes;
+    qp.H = d.height;
+    qp.W = d.width;
+    qp.B = d.bins;
+    qp.bitdepth = d.bitdepth;
+    qp.bins = reinterpret_cast<uint8_t *>(pl->d_mem);
+    qp.bins_pitch = pl->bins_pitch;
+    qp.pixel_bytes = d.pixel_type == SWIH_PIXEL_U8 ? 1 : 2;
+    qp.vec = (d.pitch_bytes % 16 == 0) && (reinterpret_cast<uintptr_t>(d_image) % 16 == 0);
+    cudaError_t e = launch_quantize(qp, s);
+    if (e != cudaSuccess) return cuda_fail(pl, "quantize launch", e);
+
+    return build_scans(pl, s);
 }
 
 swih_status swih_local_hist(swih_plan_t pl, int kernel, int win_w, int win_h, int cx0, int cy0,
@@ -930,6 +961,7 @@ swih_status swih_plan_get_info(swih_plan_t pl, swih_plan_info *info)
         info->exp_frac_bits = pl->exp_F;
     }
     if (pl->sparse_rows && pl->d_mem) info->d_row_map = reinterpret_cast<const int32_t *>(pl->d_mem + pl->off_row_map);
+    info->n_channels = pl->n_ch > 0 ? pl->n_ch : 1;
     return SWIH_OK;
 }
 

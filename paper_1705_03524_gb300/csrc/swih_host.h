@@ -52,6 +52,12 @@ struct swih_plan_s {
     int cfg_tx[5] = {0, 0, 0, 0, 0};      // tiled gather tile width per kernel (0: automatic)
     int cfg_stages[5] = {0, 0, 0, 0, 0};  // tiled gather ring depth per kernel (0: automatic)
     int cfg_bb[5] = {0, 0, 0, 0, 0};      // tiled gather bins per step per kernel (0: automatic)
+    // feature channels (swih_plan_channels): n_ch bin planes of H x bins_pitch
+    // at offset 0; channel c owns the global bins [ch_bin0[c], ch_bin0[c + 1])
+    int n_ch = 0;  // 0: a plan over one image (swih_plan)
+    swih_channel_desc ch[SWIH_MAX_CHANNELS];
+    int ch_bin0[SWIH_MAX_CHANNELS + 1] = {};
+    uint64_t off_chtgt = 0;  // per-channel target table [n_ch][bins] (floats)
     std::string err;
 };
 
@@ -71,6 +77,15 @@ long double int_kernel_mass(int kernel, int w, int h);
 swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl);
 // gather parameters of one kernel and window over the plan's integral histograms
 swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams &g, int &kind);
+// allocate a laid-out plan's workspace on the current device and hand it out
+// (the plan is deleted on failure)
+swih_status allocate_plan(swih_plan_s *pl, swih_plan_t *out);
+// after quantisation into the plan's bin planes: K2, the row map and K2e
+swih_status build_scans(swih_plan_s *pl, cudaStream_t s);
+// a kernel and window the built plan serves
+swih_status check_window(swih_plan_s *pl, int kernel, int w, int h);
+// the tiled gather when its row segments fit in shared memory, else the direct one
+cudaError_t run_gather(swih_plan_s *pl, const GatherParams &g, int kind, cudaStream_t s);
 // floor(exp(-lambda n) 2^64): the fixed-point power q^n of the exponential kernel (n >= 1)
 unsigned long long exp_pow_fixed(long double lambda, long double n);
 
@@ -85,6 +100,10 @@ struct WorkSpec {
     double gauss_sigma_frac = 0.0;
     int precision = SWIH_PREC_AUTO;
     int band_rows = 0;
+    // the term set and ring must also serve windows up to this size (0: only
+    // the jobs' windows); lets a set without jobs build integral histograms a
+    // later set's jobs read
+    int want_win_w = 0, want_win_h = 0;
 };
 
 // An image rectangle whose integral histograms are built: H x W pixels at
@@ -93,6 +112,13 @@ struct WorkRegion {
     const void *image = nullptr;
     int64_t pitch = 0;
     int H = 0, W = 0;
+    // Prebuilt (pre_ih != NULL): the region's integral histograms already exist
+    // (built by another work set with the same term set, ring and bins); the set
+    // neither quantises nor scans it and its jobs read them there. image is then
+    // unused. pre_row_map: its row map, or NULL when every row is stored.
+    const void *pre_ih = nullptr;
+    const int *pre_row_map = nullptr;
+    int64_t pre_ih_pitch = 0, pre_plane = 0;
 };
 
 // Likelihood maps of one kernel and window over a rectangle of centres of a
@@ -131,8 +157,16 @@ class WorkSet {
     size_t tables_bytes() const { return blob_.size(); }
     char *tables_device() const { return d_mem_ + off_tables_; }
     uint32_t *status_device() const { return reinterpret_cast<uint32_t *>(d_mem_ + off_status_); }
-    // clear the scan state (and the status word when zero_status), then K1, K2, K3
-    cudaError_t enqueue(cudaStream_t s, bool zero_status) const;
+    // clear the scan state (and the status block when zero_status), then K1, K2, K3.
+    // ev (optional, 1 + n_groups() events): ev[0] is recorded after the scan and
+    // row map, ev[1 + g] after job group g's gathers.
+    cudaError_t enqueue(cudaStream_t s, bool zero_status, cudaEvent_t const *ev = nullptr) const;
+    // integral-histogram bytes the tiled gathers requested, one 64-bit counter
+    // per GatherKind (0..4), in the status block (cleared with it)
+    unsigned long long *load_counters_device() const
+    {
+        return reinterpret_cast<unsigned long long *>(d_mem_ + off_status_) + 1;
+    }
     // autotuning: per job group
     int n_groups() const { return (int)groups_.size(); }
     bool group_tiled(int g) const { return groups_[g].tiled; }
@@ -144,10 +178,17 @@ class WorkSet {
     uint64_t n_evaluations() const { return n_centres_; }  // (centre, window, target) triples
     int elem_bytes() const { return tmpl_.elem_bytes; }
     int n_terms() const { return tmpl_.n_terms; }
+    // term set and ring as one comparable value: sets whose signatures are equal
+    // can read each other's integral histograms (prebuilt regions)
+    std::string signature() const;
+    // where region i's integral histograms live (after bind)
+    WorkRegion region_as_prebuilt(int i) const;
+    int n_built() const { return (int)built_.size(); }
 
   private:
     struct Region {
         WorkRegion in;
+        bool prebuilt = false;
         int n_bands = 0;
         int64_t bins_pitch = 0, ih_pitch = 0, plane = 0;
         uint64_t off_bins = 0, off_ih = 0, off_agg = 0, off_incl = 0, off_flags = 0;
@@ -170,6 +211,7 @@ class WorkSet {
     WorkSpec spec_;
     swih_plan_s tmpl_;
     std::vector<Region> regions_;
+    std::vector<int> built_;  // regions this set quantises and scans, in ticket order
     std::vector<WorkJob> in_jobs_;
     std::vector<GatherParams> jobs_;
     std::vector<int> items_;

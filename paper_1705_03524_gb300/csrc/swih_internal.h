@@ -30,6 +30,7 @@ struct QuantParams {
     int64_t bins_pitch;  // bytes, multiple of 16
     int pixel_bytes;     // 1 or 2
     int vec;             // 1 when every 16-pixel chunk can use aligned vector loads
+    int bin0 = 0;        // added to every bin: a feature channel's first bin (B + bin0 <= 256)
 };
 cudaError_t launch_quantize(const QuantParams &p, cudaStream_t s);
 
@@ -75,6 +76,11 @@ struct ScanParams {
     // nor stored; occ[b * n_bands + band] receives the band's mask of stored rows
     // (bit r: band row r holds bin b). NULL: every row is stored.
     unsigned long long *occ;
+    // Feature channels (several bin planes per pixel): bin b's chain reads the
+    // bin plane bins + ch_of_bin[b] * ch_stride, whose pixels carry the global
+    // bin numbers of one channel. ch_stride = 0: one plane.
+    int64_t ch_stride;
+    uint8_t ch_of_bin[256];
 };
 // row_map[b * H + y] = the last stored row <= y of bin b's planes (-1: none, the
 // row is all zero), from the occupancy words of a sparse-row scan

@@ -155,6 +155,7 @@ extern "C" swih_status swih_build_ih_noalloc(const swih_plan_desc *desc, const v
         layout->band_rows = L.band_rows;
         layout->n_bands = L.n_bands;
         layout->workspace_bytes = ih_need;  // bytes the caller's d_ih must hold
+        layout->n_channels = 1;
     }
     // Every call, a size query included, looks up the static array's device
     // address on the current device, so a size query made before a stream

@@ -61,9 +61,22 @@ struct MicroBatch {
     swih_server_s *srv = nullptr;
     int slot = 0;
     std::vector<Query> queries;
-    std::vector<std::unique_ptr<WorkSet>> sets;
+    std::vector<std::unique_ptr<WorkSet>> sets;  // build sets (K1, K2) first, then gather sets (K3)
     std::vector<std::vector<int>> set_queries;  // queries whose work is in each set
-    std::vector<std::pair<uint64_t, uint64_t>> dev_blocks;
+    std::vector<std::pair<uint64_t, uint64_t>> dev_blocks;  // gather sets' memory: freed at retirement
+    // build sets: their memory becomes resident integral histograms at
+    // retirement (keep_ih), else it is freed; one block per build set
+    struct Built {
+        uint64_t off = 0, bytes = 0;
+        int set = 0;                    // index into sets
+        std::vector<int> frames;        // per region of the set
+        std::vector<Rect> rects;
+        int pixel_type = 0, bitdepth = 0, bins = 0;
+        std::string sig;
+    };
+    std::vector<Built> built;
+    std::vector<int> held;              // resident blocks this micro-batch reads (one use each)
+    std::vector<char> reused;           // per query: its integral histograms were resident
     uint64_t host_off = 0, host_bytes = 0;
     uint32_t *h_status = nullptr;  // pinned, one word per set
     cudaEvent_t ev = nullptr;      // recorded after the status read-back

@@ -238,6 +238,57 @@ swih_status swih_stream_run(swih_stream_t S, void *stream)
     return SWIH_OK;
 }
 
+swih_status swih_stream_run_timed(swih_stream_t S, void *stream, float *stage_ms)
+{
+    if (!S || !stage_ms) return tfail(SWIH_ERR_INVALID_ARG, "stream plan and stage_ms are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < 7; ++i) stage_ms[i] = 0.f;
+    // per band: start, after the scan, after each job group
+    std::vector<std::vector<cudaEvent_t>> ev(S->bands.size());
+    auto destroy = [&]() {
+        for (auto &v : ev)
+            for (cudaEvent_t x : v) cudaEventDestroy(x);
+    };
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < S->bands.size() && e == cudaSuccess; ++k) {
+        const WorkSet &ws = *S->bands[k];
+        ev[k].assign(2 + ws.n_groups(), nullptr);
+        for (auto &x : ev[k])
+            if (e == cudaSuccess) e = cudaEventCreate(&x);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k][0], s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws.tables_device(), S->h_tables + S->tab_off[k], ws.tables_bytes(),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = ws.enqueue(s, false, ev[k].data() + 1);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (size_t k = 0; k < S->bands.size() && e == cudaSuccess; ++k) {
+        const WorkSet &ws = *S->bands[k];
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[k][0], ev[k][1]);
+        stage_ms[0] += ms;
+        for (int g = 0; g < ws.n_groups() && e == cudaSuccess; ++g) {
+            e = cudaEventElapsedTime(&ms, ev[k][1 + g], ev[k][2 + g]);
+            stage_ms[1 + ws.group_kind(g)] += ms;  // GatherKind numbers the kernels as swih_kernel does
+        }
+    }
+    destroy();
+    if (e != cudaSuccess) return cuda_fail(nullptr, "timed streamed pass", e);
+    return SWIH_OK;
+}
+
+swih_status swih_stream_load_bytes(swih_stream_t S, uint64_t *bytes, int reset)
+{
+    if (!S || !bytes) return tfail(SWIH_ERR_INVALID_ARG, "stream plan and bytes are required");
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c, S->d_mem + 8, sizeof c, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(S->d_mem + 8, 0, sizeof c);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "stream load counters", e);
+    for (int i = 0; i < 5; ++i) bytes[i] = c[i];
+    return SWIH_OK;
+}
+
 swih_status swih_stream_sync_status(swih_stream_t S, void *stream)
 {
     if (!S) return tfail(SWIH_ERR_INVALID_ARG, "stream plan is NULL");

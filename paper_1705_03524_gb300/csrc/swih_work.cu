@@ -34,6 +34,13 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
         const WorkRegion &r = regions[i];
         const std::string tag = "region " + std::to_string(i);
         if (r.H < 3 || r.W < 3) return bad(SWIH_ERR_INVALID_ARG, tag + " must be at least 3 x 3");
+        if (r.pre_ih) {
+            if (r.pre_ih_pitch < r.W || r.pre_plane < (int64_t)r.H * r.pre_ih_pitch || (r.pre_ih_pitch & 31))
+                return bad(SWIH_ERR_INVALID_ARG, tag + ": prebuilt layout too small");
+            maxH = std::max(maxH, r.H);
+            maxW = std::max(maxW, r.W);
+            continue;
+        }
         if (!r.image) return bad(SWIH_ERR_INVALID_ARG, tag + ": image is NULL");
         if (r.pitch < (int64_t)r.W * pb) return bad(SWIH_ERR_INVALID_ARG, tag + ": pitch smaller than a row");
         if (pb == 2 && ((r.pitch & 1) || (reinterpret_cast<uintptr_t>(r.image) & 1)))
@@ -91,8 +98,12 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
     pd.kernel_mask = spec.kernel_mask;
     pd.gauss_degree = spec.gauss_degree;
     pd.gauss_sigma_frac = spec.gauss_sigma_frac;
-    pd.max_win_w = mw;
-    pd.max_win_h = mh;
+    pd.max_win_w = std::min(maxW, std::max(mw, spec.want_win_w));
+    pd.max_win_h = std::min(maxH, std::max(mh, spec.want_win_h));
+    if (pd.max_win_w % 2 == 0) --pd.max_win_w;
+    if (pd.max_win_h % 2 == 0) --pd.max_win_h;
+    pd.max_win_w = std::max(pd.max_win_w, mw);
+    pd.max_win_h = std::max(pd.max_win_h, mh);
     pd.precision = spec.precision;
     tmpl_ = swih_plan_s();
     const swih_status st = build_layout(&pd, &tmpl_);
@@ -106,11 +117,19 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
     const uint64_t n_chains = (uint64_t)spec.bins * tmpl_.n_q;
     const size_t nR = regions.size(), nJ = in_jobs_.size();
     regions_.assign(nR, Region());
+    built_.clear();
     long long ticket = 0, chunk = 0;
     uint64_t flag_ints = 0;
     for (size_t i = 0; i < nR; ++i) {
         Region &R = regions_[i];
         R.in = regions[i];
+        if (R.in.pre_ih) {  // read in place: no bins, scan state or tickets here
+            R.prebuilt = true;
+            R.ih_pitch = R.in.pre_ih_pitch;
+            R.plane = R.in.pre_plane;
+            continue;
+        }
+        built_.push_back((int)i);
         R.n_bands = (R.in.H + band_rows_ - 1) / band_rows_;
         R.bins_pitch = round_up(R.in.W, 128);
         R.ih_pitch = round_up(R.in.W, 32);
@@ -138,8 +157,9 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
     // rows that hold no pixel of a bin are not stored (bands of at most 64 rows,
     // regions below 32768 rows: the gathers keep stored rows as int16)
     sparse_ = band_rows_ <= 64;
-    for (const auto &R : regions_) sparse_ = sparse_ && R.in.H <= 32767;
+    for (const auto &R : regions_) sparse_ = sparse_ && (R.prebuilt || R.in.H <= 32767);
     for (auto &R : regions_) {
+        if (R.prebuilt) continue;
         R.off_bins = off;
         off = align256(off + (uint64_t)R.in.H * R.bins_pitch);
         R.off_ih = off;
@@ -206,7 +226,7 @@ swih_status WorkSet::build_jobs(std::string &err)
         view.desc.width = R.in.W;
         view.plane = R.plane;
         view.ih_pitch = R.ih_pitch;
-        view.d_mem = d_mem_ + R.off_ih;
+        view.d_mem = R.prebuilt ? static_cast<char *>(const_cast<void *>(R.in.pre_ih)) : d_mem_ + R.off_ih;
         view.off_ih = 0;
         view.d_status = status_device();
         GatherParams g;
@@ -223,9 +243,12 @@ swih_status WorkSet::build_jobs(std::string &err)
         g.target = jb.target;
         g.map = jb.map;
         g.hist = nullptr;
-        g.row_map = sparse_ ? reinterpret_cast<const int *>(d_mem_ + R.off_row_map) : nullptr;
+        g.row_map = R.prebuilt ? R.in.pre_row_map
+                    : sparse_  ? reinterpret_cast<const int *>(d_mem_ + R.off_row_map)
+                               : nullptr;
         g.nbg = 1;  // table launches span many waves already; no split-gather scratch here
-        g.load_bytes = nullptr;
+        // bytes the tiled gathers request, one counter per kind in the status block
+        g.load_bytes = reinterpret_cast<unsigned long long *>(d_mem_ + off_status_) + 1 + kind;
         g.partial = nullptr;
         g.partial_cap = 0;
         g.n_targets = jb.n_targets;
@@ -299,8 +322,9 @@ void WorkSet::build_blob()
     QuantRoi *qt = reinterpret_cast<QuantRoi *>(blob_.data() + tab_quant_);
     ScanRoi *stt = reinterpret_cast<ScanRoi *>(blob_.data() + tab_scan_);
     int *flags = reinterpret_cast<int *>(d_mem_ + off_flags_);
-    for (size_t i = 0; i < nR; ++i) {
-        const Region &R = regions_[i];
+    (void)nR;
+    for (size_t i = 0; i < built_.size(); ++i) {  // quantisation and scan tables: the regions built here
+        const Region &R = regions_[built_[i]];
         qt[i].image = static_cast<const uint8_t *>(R.in.image);
         qt[i].pitch = R.in.pitch;
         qt[i].H = R.in.H;
@@ -344,12 +368,21 @@ cudaError_t WorkSet::enqueue_group(int gi, cudaStream_t s) const
     return cudaSuccess;
 }
 
-cudaError_t WorkSet::enqueue(cudaStream_t s, bool zero_status) const
+cudaError_t WorkSet::enqueue(cudaStream_t s, bool zero_status, cudaEvent_t const *ev) const
 {
     const uint64_t from = zero_status ? off_status_ : off_flags_;
     cudaError_t e = cudaMemsetAsync(d_mem_ + from, 0, off_flags_ + flags_ints_ * sizeof(int) - from, s);
     if (e != cudaSuccess) return e;
-    e = launch_quantize_table(reinterpret_cast<const QuantRoi *>(tables_device() + tab_quant_), (int)regions_.size(),
+    if (built_.empty()) {  // every region prebuilt: the gathers alone
+        if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+        for (int g = 0; g < (int)groups_.size(); ++g) {
+            e = enqueue_group(g, s);
+            if (e != cudaSuccess) return e;
+            if (ev && (e = cudaEventRecord(ev[1 + g], s)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    e = launch_quantize_table(reinterpret_cast<const QuantRoi *>(tables_device() + tab_quant_), (int)built_.size(),
                               quant_chunks_, spec_.bins, spec_.bitdepth, spec_.pixel_type == SWIH_PIXEL_U16 ? 2 : 1,
                               s);
     if (e != cudaSuccess) return e;
@@ -371,21 +404,43 @@ cudaError_t WorkSet::enqueue(cudaStream_t s, bool zero_status) const
     sp.spin_limit = 1LL << 22;  // with 64 ns sleeps: well under a few seconds
     sp.stall_tile = -1;
     // a table launch only tests occ for non-NULL; each region writes its own
-    sp.occ = sparse_ && !regions_.empty() ? reinterpret_cast<unsigned long long *>(d_mem_ + regions_[0].off_occ)
-                                          : nullptr;
+    sp.occ = sparse_ ? reinterpret_cast<unsigned long long *>(d_mem_ + regions_[built_[0]].off_occ) : nullptr;
     const ScanRoi *d_scan = reinterpret_cast<const ScanRoi *>(tables_device() + tab_scan_);
-    e = launch_ih_scan_table(sp, d_scan, (int)regions_.size(), scan_tiles_, tmpl_.elem_bytes, scan_E_, scan_threads_,
+    e = launch_ih_scan_table(sp, d_scan, (int)built_.size(), scan_tiles_, tmpl_.elem_bytes, scan_E_, scan_threads_,
                              s);
     if (e != cudaSuccess) return e;
     if (sparse_) {
-        e = launch_row_map_table(d_scan, (int)regions_.size(), spec_.bins, band_rows_, s);
+        e = launch_row_map_table(d_scan, (int)built_.size(), spec_.bins, band_rows_, s);
         if (e != cudaSuccess) return e;
     }
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     for (int g = 0; g < (int)groups_.size(); ++g) {
         e = enqueue_group(g, s);
         if (e != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecord(ev[1 + g], s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+std::string WorkSet::signature() const
+{
+    std::string sig = "e" + std::to_string(tmpl_.elem_bytes) + "b" + std::to_string(spec_.bins) + "r" +
+                      std::to_string(band_rows_) + (sparse_ ? "s" : "d") + "t";
+    for (int t = 0; t < tmpl_.n_terms; ++t)
+        sig += std::to_string(tmpl_.term_p[t]) + std::to_string(tmpl_.term_q[t]);
+    return sig;
+}
+
+WorkRegion WorkSet::region_as_prebuilt(int i) const
+{
+    const Region &R = regions_[i];
+    if (R.prebuilt) return R.in;
+    WorkRegion out = R.in;
+    out.pre_ih = d_mem_ + R.off_ih;
+    out.pre_row_map = sparse_ ? reinterpret_cast<const int *>(d_mem_ + R.off_row_map) : nullptr;
+    out.pre_ih_pitch = R.ih_pitch;
+    out.pre_plane = R.plane;
+    return out;
 }
 
 }  // namespace swih

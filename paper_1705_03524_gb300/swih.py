@@ -96,10 +96,22 @@ class swih_plan_info(ctypes.Structure):
         ("d_exp", ctypes.c_void_p),
         ("exp_frac_bits", ctypes.c_int32),
         ("d_row_map", ctypes.c_void_p),
+        ("n_channels", ctypes.c_int32),
     ]
 
 
 SWIH_MAX_SCALES = 8
+SWIH_MAX_CHANNELS = 8
+
+
+class swih_channel_desc(ctypes.Structure):
+    _fields_ = [
+        ("pitch_bytes", ctypes.c_int64),
+        ("pixel_type", ctypes.c_int32),
+        ("bitdepth", ctypes.c_int32),
+        ("bins", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
 
 
 class swih_batch_desc(ctypes.Structure):
@@ -229,6 +241,13 @@ def _load() -> ctypes.CDLL:
     lib.swih_build_ih_noalloc.argtypes = [ctypes.POINTER(swih_plan_desc), P, P, ctypes.c_uint64, P,
                                           ctypes.POINTER(swih_plan_info), P]
     lib.swih_build_ih_noalloc.restype = S
+    lib.swih_plan_channels.argtypes = [ctypes.POINTER(swih_plan_desc), I, ctypes.POINTER(swih_channel_desc),
+                                       ctypes.POINTER(P)]
+    lib.swih_plan_channels.restype = S
+    lib.swih_build_ih_channels.argtypes = [P, ctypes.POINTER(P), P]
+    lib.swih_build_ih_channels.restype = S
+    lib.swih_likelihood_channels.argtypes = [P, I, I, I, P, P, P]
+    lib.swih_likelihood_channels.restype = S
     lib.swih_set_gather_config.argtypes = [P, I, I, I, I]
     lib.swih_set_gather_config.restype = S
     lib.swih_debug_inject.argtypes = [P, I]
@@ -269,8 +288,10 @@ def _load() -> ctypes.CDLL:
     lib.swih_stream_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_uint64)]
     lib.swih_stream_destroy.argtypes = [P]
+    lib.swih_stream_run_timed.argtypes = [P, P, ctypes.POINTER(ctypes.c_float)]
+    lib.swih_stream_load_bytes.argtypes = [P, U64P, I]
     for name in ("swih_stream_plan", "swih_stream_run", "swih_stream_sync_status", "swih_stream_get_info",
-                 "swih_stream_destroy"):
+                 "swih_stream_destroy", "swih_stream_run_timed", "swih_stream_load_bytes"):
         getattr(lib, name).restype = S
     for name in ("swih_server_create", "swih_server_add_frame", "swih_query_out_elems",
                  "swih_server_query_bytes", "swih_server_submit", "swih_server_poll",
@@ -477,6 +498,42 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def make_channel(width, *, pixel_type=SWIH_PIXEL_U8, bitdepth=None, bins=16, pitch_bytes=None) -> swih_channel_desc:
+    """One feature channel of a channel plan (image row stride defaults to width pixels)."""
+    pb = 1 if pixel_type == SWIH_PIXEL_U8 else 2
+    c = swih_channel_desc()
+    c.pitch_bytes = int(pitch_bytes if pitch_bytes is not None else width * pb)
+    c.pixel_type = int(pixel_type)
+    c.bitdepth = int(bitdepth if bitdepth is not None else 8 * pb)
+    c.bins = int(bins)
+    c.reserved = 0
+    return c
+
+
+class ChannelPlan(Plan):
+    """Owning wrapper of a feature-channel plan (swih_plan_channels): one bin
+    plane per channel, every channel's map from one gather launch."""
+
+    def __init__(self, desc: swih_plan_desc, channels):
+        self.desc = desc
+        self.channels = list(channels)
+        arr = (swih_channel_desc * len(self.channels))(*self.channels)
+        h = ctypes.c_void_p()
+        _check(LIB.swih_plan_channels(ctypes.byref(desc), len(self.channels), arr, ctypes.byref(h)))
+        self.handle = int(h.value)
+        self.bins = sum(c.bins for c in self.channels)
+
+    def build_ih(self, images, stream=None):
+        ptrs = (ctypes.c_void_p * len(images))(*[_ptr(im) for im in images])
+        _check(LIB.swih_build_ih_channels(self.handle, ptrs, _stream(stream)), self.handle)
+
+    def likelihood_channels(self, kernel, win_w, win_h, target, out_maps, stream=None):
+        """target: [B] (the channels' targets side by side); out_maps: [C][H-h+1][W-w+1]."""
+        k = KERNELS[kernel] if isinstance(kernel, str) else kernel
+        _check(LIB.swih_likelihood_channels(self.handle, k, int(win_w), int(win_h), _ptr(target), _ptr(out_maps),
+                                            _stream(stream)), self.handle)
 
 
 # ---------------------------------------------------------------- batches
@@ -732,6 +789,23 @@ class Stream:
 
     def sync_status(self, stream=None):
         _check(LIB.swih_stream_sync_status(self.handle, _stream(stream)))
+
+    def run_timed(self, stream=None):
+        """One pass launched stage by stage with CUDA events; returns
+        {"scan": ms, kernel name: ms of its gathers} summed over the bands."""
+        ms = (ctypes.c_float * 7)()
+        _check(LIB.swih_stream_run_timed(self.handle, _stream(stream), ms))
+        out = {"scan": float(ms[0])}
+        for name, k in KERNELS.items():
+            if 0 <= k <= 5 and ms[1 + k] > 0:
+                out[name] = float(ms[1 + k])
+        return out
+
+    def load_bytes(self, reset=False):
+        """Integral-histogram bytes the tiled gathers requested, per kernel name."""
+        b = (ctypes.c_uint64 * 5)()
+        _check(LIB.swih_stream_load_bytes(self.handle, b, int(bool(reset))))
+        return {name: int(b[k]) for name, k in KERNELS.items() if 0 <= k < 5}
 
     def info(self):
         bh, nb, wb = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_uint64(0)

@@ -32,10 +32,11 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "swih.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(swih_plan_desc), offsetof(swih_plan_desc, gauss_sigma_frac),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(swih_plan_desc), offsetof(swih_plan_desc, gauss_sigma_frac),
          offsetof(swih_plan_desc, hbm_budget_bytes), sizeof(swih_plan_info),
          offsetof(swih_plan_info, workspace_bytes), offsetof(swih_plan_desc, exp_lambda),
-         offsetof(swih_plan_info, d_exp), offsetof(swih_plan_info, exp_frac_bits));
+         offsetof(swih_plan_info, d_exp), offsetof(swih_plan_info, exp_frac_bits),
+         offsetof(swih_plan_info, n_channels), sizeof(swih_channel_desc), offsetof(swih_channel_desc, bins));
   return 0;
 }
 '''
@@ -49,7 +50,9 @@ int main(void) {
     assert vals == [ctypes.sizeof(S.swih_plan_desc), S.swih_plan_desc.gauss_sigma_frac.offset,
                     S.swih_plan_desc.hbm_budget_bytes.offset, ctypes.sizeof(S.swih_plan_info),
                     S.swih_plan_info.workspace_bytes.offset, S.swih_plan_desc.exp_lambda.offset,
-                    S.swih_plan_info.d_exp.offset, S.swih_plan_info.exp_frac_bits.offset]
+                    S.swih_plan_info.d_exp.offset, S.swih_plan_info.exp_frac_bits.offset,
+                    S.swih_plan_info.n_channels.offset, ctypes.sizeof(S.swih_channel_desc),
+                    S.swih_channel_desc.bins.offset]
 
 
 def _desc(**kw):
@@ -238,3 +241,20 @@ def test_batch_workspace_grows_with_rois_and_terms():
     # the Gaussian in the mask switches every ROI to 25 terms in the 64-bit ring
     g = S.swih_batch_workspace_bytes(_bdesc(kernels=("manhattan", "gaussian")), two)
     assert g >= 25 * 16 * (48 * 64 + 90 * 128) * 8
+
+
+def test_channel_plan_refusals_on_the_host():
+    # refused while the plan is laid out, before any device call
+    desc = S.make_desc(64, 64, bins=1, kernels=("exponential",), max_win=(9, 9))
+    with pytest.raises(S.SwihError) as ei:
+        S.ChannelPlan(desc, [S.make_channel(64, bins=8)])
+    assert ei.value.status == S.SWIH_ERR_UNSUPPORTED
+    desc = S.make_desc(64, 64, bins=1, kernels=("manhattan",), max_win=(9, 9))
+    for chans in ([S.make_channel(64, bins=200), S.make_channel(64, bins=57)],   # 257 bins
+                  [S.make_channel(64, bins=8, bitdepth=9)],                      # u8 with 9 bits
+                  [S.make_channel(64, bins=8, pitch_bytes=63)],                  # pitch below a row
+                  [S.make_channel(64, bins=0)],
+                  [S.make_channel(64, bins=4)] * 9):                             # more than 8 channels
+        with pytest.raises(S.SwihError) as ei:
+            S.ChannelPlan(desc, chans)
+        assert ei.value.status == S.SWIH_ERR_INVALID_ARG

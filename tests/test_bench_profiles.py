@@ -71,3 +71,92 @@ def test_oracle_error_report_finds_a_planted_difference():
     res = bench.oracle_errors(img, B, jobs, bad, np.stack(targets), n=4000, seed=3)
     assert abs(res["per_map"]["gaussian_9"] - 0.25) < 1e-3, res
     assert res["per_map"]["manhattan_5"] <= 1e-6 and res["per_map"]["euclidean_3"] <= 1e-6, res
+
+
+def test_oracle_error_reports_the_true_gaussian_distance():
+    """The Gaussian maps also get their distance from the likelihood under
+    exact Gaussian weights, labelled as approximation error; it is well above
+    the parity tolerance for the degree-2 stand-in and absent for other kernels."""
+    from oracle import swih_oracle as O
+    from paper_1705_03524_gb300 import synth
+
+    img = synth.blob_scene(64, 64, 8, 5, n_blobs=2, axes=(6, 14), margin=12).image
+    B = 8
+    jobs = [("gaussian", 21), ("manhattan", 9)]
+    bins = O.quantize(img, 8, B)
+    maps, targets = [], []
+    for k, w in jobs:
+        K = O.kernel_weights(k, w, w)
+        q = O.target_hist(bins, B, K, 30, 30).astype(np.float32)
+        targets.append(q)
+        maps.append(O.likelihood_map(bins, B, K, q.astype(np.float64)).astype(np.float32))
+    res = bench.oracle_errors(img, B, jobs, maps, np.stack(targets), n=256, seed=1)
+    g = res["gaussian_vs_true_gaussian"]["per_map"]
+    assert set(g) == {"gaussian_21"}
+    assert 1e-5 < g["gaussian_21"] < 0.2, g
+
+
+def test_sampled_error_reports_of_the_extra_blocks_find_planted_differences():
+    """regions_error, serving_error and large_frame_error index the values the
+    bench copied back by centre; fed values computed by the oracle itself they
+    report zero, and a changed value shows up."""
+    from oracle import swih_oracle as O
+    from paper_1705_03524_gb300 import synth
+
+    rng = np.random.default_rng(2)
+    # search regions of a u16 frame, Gaussian kernel
+    img16 = synth.uniform_image(90, 120, 16, seed=3)
+    B = 16
+    rois = [(5, 7, 40, 30), (50, 20, 60, 55)]
+    targets = rng.gamma(0.5, size=(2, B))
+    targets /= targets.sum(1, keepdims=True)
+    samples = []
+    for i, (x0, y0, w, h) in enumerate(rois):
+        bins = O.quantize(img16[y0:y0 + h, x0:x0 + w], 16, B)
+        for k in (5, 9):
+            r = k // 2
+            cx, cy = rng.integers(r, w - r, 20), rng.integers(r, h - r, 20)
+            m = O.likelihood_map(bins, B, O.kernel_weights("gaussian", k, k), targets[i]).astype(np.float32)
+            samples.append((i, k, cx, cy, m[cy - r, cx - r]))
+    assert bench.regions_error(img16, B, rois, samples, targets)["max_abs"] <= 1e-6
+    samples[3][4][2] += 0.125
+    assert abs(bench.regions_error(img16, B, rois, samples, targets)["max_abs"] - 0.125) < 1e-4
+
+    # served queries: crops of u8 / u16 frames, several targets and windows
+    frames = [(synth.uniform_image(70, 80, 8, seed=5), 8), (synth.uniform_image(70, 80, 16, seed=6), 16)]
+    qs = [dict(frame=1, x0=3, y0=4, w=50, h=40, B=8, kernel="euclidean", windows=[(5, 5), (9, 7)],
+               targets=(np.full((2, 8), 1 / 8.0) + np.arange(8) / 80.0).astype(np.float32)),
+          dict(frame=0, x0=10, y0=2, w=33, h=61, B=4, kernel="manhattan", windows=[(3, 3)],
+               targets=np.array([[0.1, 0.2, 0.3, 0.4]], dtype=np.float32))]
+    for q in qs:
+        q["targets"] /= q["targets"].sum(1, keepdims=True)
+    samples = []
+    for i, q in enumerate(qs):
+        img, bd = frames[q["frame"]]
+        bins = O.quantize(img[q["y0"]:q["y0"] + q["h"], q["x0"]:q["x0"] + q["w"]], bd, q["B"])
+        for t in range(len(q["targets"])):
+            for (w, h) in q["windows"]:
+                m = O.likelihood_map(bins, q["B"], O.kernel_weights(q["kernel"], w, h),
+                                     q["targets"][t].astype(np.float64)).astype(np.float32)
+                cx = rng.integers(0, q["w"] - w + 1, 8) + (w - 1) // 2
+                cy = rng.integers(0, q["h"] - h + 1, 8) + (h - 1) // 2
+                samples.append((i, t, w, h, cx, cy, m[cy - (h - 1) // 2, cx - (w - 1) // 2]))
+    assert bench.serving_error(frames, qs, samples)["max_abs"] <= 1e-6
+    samples[-1][6][0] -= 0.5
+    assert abs(bench.serving_error(frames, qs, samples)["max_abs"] - 0.5) < 1e-4
+
+    # a block of centres of a streamed frame (sub-image with an R-pixel halo)
+    R = 4
+    sub = synth.uniform_image(16 + 2 * R, 16 + 2 * R, 16, seed=7)
+    job_kw = [("gaussian", 9), ("euclidean", 5)]
+    tg = np.stack([targets[0], targets[1]])
+    bins = O.quantize(sub, 16, B)
+    blocks = []
+    for j, (k, w) in enumerate(job_kw):
+        full = O.likelihood_rect(bins, B, O.kernel_weights(k, w, w), tg[j], R, R, 16, 16)
+        blocks.append(full.astype(np.float32))
+    res = bench.large_frame_error(sub, B, job_kw, tg, blocks, 100, 200, R, n=16)
+    assert res["max_abs"] <= 1e-6, res
+    blocks[1][15, 0] += 0.25
+    res = bench.large_frame_error(sub, B, job_kw, tg, blocks, 100, 200, R, n=16)
+    assert abs(res["per_map"]["euclidean_5"] - 0.25) < 1e-4 and res["per_map"]["gaussian_9"] <= 1e-6, res

@@ -150,3 +150,34 @@ def test_large_frame_sampled():
         got = j["map"][by - r: by - r + 512, bx - r: bx - r + 512].cpu().numpy()
         err = np.abs(got - ref).max()
         assert err <= TOL, (j["kernel"], j["w"], err)
+
+
+def test_timed_pass_equals_the_graph_pass_and_counts_loaded_bytes():
+    """swih_stream_run_timed (stage by stage, with events) writes the maps the
+    captured pass writes; its stage times are positive for the scan and for
+    each kernel used; the gathers' load counters grow with each pass and reset."""
+    img, d = setup_frame(seed=9)
+    bd, B = 12, 16
+    _bins, jobs = make_jobs(img, bd, B, JOBS)
+    desc = desc_for(img, bd, B)
+    fj = [S.make_frame_job(j["kernel"], j["w"], j["h"], j["target"], j["map"]) for j in jobs]
+    with S.Stream(desc, fj, d, band_height=101) as st:
+        st.run()
+        st.sync_status()
+        ref = [j["map"].clone() for j in jobs]
+        for j in jobs:
+            j["map"].fill_(-1.0)
+        st.load_bytes(reset=True)
+        ms = st.run_timed()
+        st.sync_status()
+        one = st.load_bytes()
+        assert set(ms) == {"scan", "manhattan", "euclidean", "gaussian"}, ms
+        assert all(v > 0 for v in ms.values()), ms
+        for a, j in zip(ref, jobs):
+            assert torch.equal(a, j["map"])
+        assert one["gaussian"] > 0 and one["euclidean"] > 0 and one["manhattan"] > 0, one
+        assert one["plain"] == 0 and one["wedding"] == 0
+        st.run()
+        two = st.load_bytes(reset=True)
+        assert two == {k: 2 * v for k, v in one.items()}, (one, two)
+        assert all(v == 0 for v in st.load_bytes().values())

@@ -567,3 +567,57 @@ def test_exponential_quadrant_decomposition_matches_brute_force(lam):
         got = np.array([[exp_quadrant_sums(J[b], lam, w, h, x, y) for b in range(B)]
                         for x, y in zip(cx, cy)])
         np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------
+# feature channels (Sec. 4: one likelihood map per feature)
+# ----------------------------------------------------------------------------
+def read_channel_fixture():
+    with open(os.path.join(GOLDEN, "channels_3x3.txt")) as f:
+        lines = [ln.split("#")[0].strip() for ln in f]
+    lines = [ln for ln in lines if ln]
+    chans = []
+    i = 0
+    while i < len(lines):
+        _, c, _, B = lines[i].split()
+        rows = [[int(v) for v in lines[i + k].split()] for k in (1, 2, 3)]
+        U = [int(v) for v in lines[i + 4].split()[1:]]
+        chans.append((int(B), np.array(rows, dtype=np.uint8), U))
+        i += 5
+    return chans
+
+
+def test_channel_hand_fixture():
+    chans = read_channel_fixture()
+    K = O.kernel_weights("manhattan", 3, 3)
+    for B, bins, U in chans:
+        assert np.array_equal(O.hist_at(bins, B, K, [1], [1])[0], np.array(U, dtype=np.float64))
+    q = [np.array([0.5, 0.5]), np.array([1.0, 1.0, 1.0]) / 3.0]
+    L = O.likelihood_channels_map([c[1] for c in chans], [c[0] for c in chans], K, q)
+    assert L.shape == (2, 1, 1)
+    assert abs(L[0, 0, 0] - (np.sqrt(1 / 6) + np.sqrt(1 / 3))) < 1e-15
+    assert abs(L[1, 0, 0] - (np.sqrt(1 / 6) + np.sqrt(1 / 9) + np.sqrt(1 / 18))) < 1e-15
+
+
+def test_channels_reduce_to_one_image_and_share_the_mass():
+    rng = np.random.default_rng(41)
+    H, W = 21, 30
+    imgs = [rng.integers(0, 256, size=(H, W)).astype(np.uint8), rng.integers(0, 4096, size=(H, W)).astype(np.uint16)]
+    Bs = [8, 5]
+    bins = [O.quantize(imgs[0], 8, 8), O.quantize(imgs[1], 12, 5)]
+    K = O.kernel_weights("euclidean", 7, 5)
+    qs = []
+    for b, B in zip(bins, Bs):
+        q = rng.gamma(0.5, size=B)
+        qs.append(q / q.sum())
+    L = O.likelihood_channels_map(bins, Bs, K, qs)
+    for c in range(2):
+        np.testing.assert_array_equal(L[c], O.likelihood_map(bins[c], Bs[c], K, qs[c]))
+    # one channel is the single-image path
+    np.testing.assert_array_equal(O.likelihood_channels_map(bins[:1], Bs[:1], K, qs[:1])[0],
+                                  O.likelihood_map(bins[0], Bs[0], K, qs[0]))
+    # every pixel is in one bin of each channel: both channels' windows weigh M
+    M = 5 * 3 * 7 * 5 // 3 + 7 * 2 * 5 * 3 // 3  # h rx(2rx+1)(2rx-1)/3 + w ry(2ry+1)(2ry-1)/3
+    x0, y0, nx, ny = O.valid_centres(H, W, 7, 5)
+    for b, B in zip(bins, Bs):
+        assert np.all(O.hist_rect(b, B, K, x0, y0, nx, ny).sum(-1) == M)
