@@ -1047,7 +1047,27 @@ def run_serving(args, dev, n_queries=400, rate=2000.0):
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                 "span_s": span_s}
 
-    srv_cfg = dict(hbm_budget_bytes=96 << 30, max_inflight=8, max_batch_queries=8, merge_regions=True)
+    srv_cfg = dict(hbm_budget_bytes=96 << 30, max_inflight=8, max_batch_queries=8, merge_regions=True,
+                   keep_ih=True)
+
+    def serve_stream(srv, qq):
+        t0 = time.monotonic_ns()
+        arrival = []
+        for i, q in enumerate(qs):
+            a = t0 + int(q["t"] * 1e9)
+            while time.monotonic_ns() < a:
+                pass
+            arrival.append(a)
+            srv.submit(qq[i])
+        srv.drain()
+        comps = srv.poll(n_queries + 16)
+        lat = [(c.done_ns - arrival[c.user_tag]) / 1e6 for c in comps]
+        out = stats(lat, (max(c.done_ns for c in comps) - t0) / 1e9)
+        out.update({"mean_queries_per_micro_batch": float(np.mean([c.batch_queries for c in comps])),
+                    "failed": sum(c.status != 0 for c in comps),
+                    "ih_reused_fraction": float(np.mean([c.ih_reused for c in comps]))})
+        return out
+
     with S.Server(**srv_cfg) as srv:
         ids = []
         for (img, bd), d in zip(frames, d_frames):
@@ -1059,21 +1079,14 @@ def run_serving(args, dev, n_queries=400, rate=2000.0):
             srv.submit(qq[i])
         srv.drain()
         srv.poll(64)
-        t0 = time.monotonic_ns()
-        arrival = []
-        for i, q in enumerate(qs):
-            a = t0 + int(q["t"] * 1e9)
-            while time.monotonic_ns() < a:
-                pass
-            arrival.append(a)
-            srv.submit(qq[i])
-        srv.drain()
-        comps = srv.poll(n_queries + 16)
-    bad = sum(c.status != 0 for c in comps)
-    lat = [(c.done_ns - arrival[c.user_tag]) / 1e6 for c in comps]
-    server = stats(lat, (max(c.done_ns for c in comps) - t0) / 1e9)
-    server.update({"mean_queries_per_micro_batch": float(np.mean([c.batch_queries for c in comps])),
-                   "failed": bad, "config": {k: v for k, v in srv_cfg.items()}})
+        for f in ids:  # the stream starts with nothing resident
+            srv.frame_changed(f)
+        server = serve_stream(srv, qq)
+        server["config"] = {k: v for k, v in srv_cfg.items()}
+        server["ih_stats"] = srv.stats()
+        # the same stream again over the unchanged frames: integral histograms resident
+        warm = serve_stream(srv, qq)
+        warm["ih_stats"] = srv.stats()
     server_out = [o.clone() for o in outs]
     if not args.no_cpu_baseline:
         rng = np.random.default_rng(17)
@@ -1115,16 +1128,76 @@ def run_serving(args, dev, n_queries=400, rate=2000.0):
         lat.append((time.monotonic_ns() - a) / 1e6)
     plain = stats(lat, (time.monotonic_ns() - t0) / 1e9)
     diff = max((a - b).abs().max().item() for a, b in zip(outs, server_out))
+    repeats = run_serving_repeats(S, synth, dev, frames, d_frames, stats_fn=stats)
     return {
         "workload": (f"{n_queries} queries, Poisson {rate:.0f}/s, 16 resident 2048x2048 u8/u16 frames, crops "
                      "U{64..1024}^2, B in {16,32,64}, M/E/G kernel, 1-8 targets, 1-5 windows of "
                      "15/25/43/75/127"),
         "windows_per_query_mean": total / n_queries,
-        "server": server, "plain_per_query": plain,
+        "server": server, "server_warm_replay": warm, "plain_per_query": plain,
         "p99_ratio_plain_over_server": plain["p99_ms"] / server["p99_ms"],
         "throughput_ratio_server_over_plain": server["queries_per_s"] / plain["queries_per_s"],
         "max_abs_diff_server_vs_plain": diff,
+        "revisited_regions": repeats,
     }
+
+
+def run_serving_repeats(S, synth, dev, frames, d_frames, stats_fn):
+    """A stream that comes back to the same search regions (80 regions on the
+    16 resident frames, 5 queries each, Poisson 2000/s), served with the
+    integral histograms kept resident between micro-batches and without: the
+    hit rate, latency and throughput of each, and the largest difference
+    between their maps (0: the integer integral histograms are exact)."""
+    import torch
+
+    qs = synth.config5_repeat_queries()
+
+    def n_eval(q):
+        return len(q["targets"]) * sum((q["h"] - h + 1) * (q["w"] - w + 1) for w, h in q["windows"])
+
+    targets = [torch.from_numpy(q["targets"]).to(dev) for q in qs]
+    res, outs_by = {}, {}
+    for keep in (True, False):
+        outs = [torch.empty(n_eval(q), device=dev) for q in qs]
+        cfg = dict(hbm_budget_bytes=96 << 30, max_inflight=8, max_batch_queries=8, merge_regions=True,
+                   keep_ih=keep)
+        with S.Server(**cfg) as srv:
+            ids = []
+            for (img, bd), d in zip(frames, d_frames):
+                pt = S.SWIH_PIXEL_U8 if img.dtype == np.uint8 else S.SWIH_PIXEL_U16
+                ids.append(srv.add_frame(d, img.shape[0], img.shape[1], pixel_type=pt, bitdepth=bd))
+            qq = [S.make_query(ids[q["frame"]], q["x0"], q["y0"], q["w"], q["h"], q["B"], q["kernel"],
+                               q["windows"], targets[i], outs[i], n_targets=len(q["targets"]), user_tag=i)
+                  for i, q in enumerate(qs)]
+            for i in range(8):  # warm-up, then nothing resident
+                srv.submit(qq[i])
+            srv.drain()
+            srv.poll(64)
+            for f in ids:
+                srv.frame_changed(f)
+            t0 = time.monotonic_ns()
+            arrival = []
+            for i, q in enumerate(qs):
+                a = t0 + int(q["t"] * 1e9)
+                while time.monotonic_ns() < a:
+                    pass
+                arrival.append(a)
+                srv.submit(qq[i])
+            srv.drain()
+            comps = srv.poll(len(qs) + 16)
+            st = stats_fn([(c.done_ns - arrival[c.user_tag]) / 1e6 for c in comps],
+                          (max(c.done_ns for c in comps) - t0) / 1e9)
+            st.update({"ih_reused_fraction": float(np.mean([c.ih_reused for c in comps])),
+                       "failed": sum(c.status != 0 for c in comps), "ih_stats": srv.stats()})
+            # windows/s of this stream (the stats helper's figure is the main stream's)
+            st["windows_per_s"] = sum(n_eval(q) for q in qs) / st["span_s"]
+        res["resident_ih" if keep else "rebuilt_each_micro_batch"] = st
+        outs_by[keep] = outs
+    res["max_abs_diff"] = max((a - b).abs().max().item() for a, b in zip(outs_by[True], outs_by[False]))
+    res["workload"] = ("400 queries, Poisson 2000/s: 80 search regions (U{256..512}^2, B in {16,32}, "
+                       "Manhattan/Euclidean) on the 16 resident frames, each queried 5 times in random order, "
+                       "1-4 targets, 1-3 windows of 15/25/43/75/127")
+    return res
 
 
 # ----------------------------------------------------------------------------- Fig. 6

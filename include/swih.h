@@ -518,6 +518,13 @@ typedef struct swih_server_desc {
     int32_t gauss_degree;       /* as in swih_plan_desc */
     double gauss_sigma_frac;
     uint64_t staging_bytes;     /* pinned host staging for job tables (0: 64 MiB) */
+    int32_t keep_ih;            /* 1: keep built integral histograms resident in the arena after
+                                   their micro-batch; a later query whose crop lies inside a
+                                   resident region of the same frame (same pixel type, bit
+                                   depth, B and term set) skips quantisation and scan. Resident
+                                   regions nobody reads are evicted, least recently used first,
+                                   when the arena is needed. */
+    int32_t reserved;           /* 0 */
 } swih_server_desc;
 
 typedef struct swih_frame_desc {
@@ -550,14 +557,26 @@ typedef struct swih_completion {
     int32_t status;             /* swih_status of the query's work */
     int32_t batch_queries;      /* queries in its micro-batch */
     uint64_t submit_ns, start_ns, done_ns;  /* steady-clock (CLOCK_MONOTONIC) times */
+    int32_t ih_reused;          /* 1: the query's integral histograms were resident (no K1, K2) */
+    int32_t reserved;
 } swih_completion;
+
+/* Counters of a server since its creation. */
+typedef struct swih_server_stats {
+    uint64_t queries;           /* queries completed by micro-batches */
+    uint64_t ih_reused;         /* of them, served from resident integral histograms */
+    uint64_t regions_built;     /* crop regions quantised and scanned */
+    uint64_t evictions;         /* resident blocks evicted to make room */
+    uint64_t resident_bytes;    /* arena bytes held by resident integral histograms now */
+} swih_server_stats;
 
 /* Create a server on the current device: allocates the arena and staging
  * and starts the scheduler thread. */
 swih_status swih_server_create(const swih_server_desc *desc, swih_server_t *out);
 
 /* Register a resident frame; *frame_id is its handle for queries. The caller
- * may rewrite the pixels between queries (not while queries on it run). */
+ * may rewrite the pixels between queries (not while queries on it run; with
+ * keep_ih, call swih_server_frame_changed afterwards). */
 swih_status swih_server_add_frame(swih_server_t server, const swih_frame_desc *frame, int32_t *frame_id);
 
 /* Floats d_out must hold for a query (host only, no server needed). */
@@ -580,6 +599,16 @@ swih_status swih_server_poll(swih_server_t server, swih_completion *out, int32_t
  * admitted (or finished, or unknown) is left alone and SWIH_ERR_INVALID_ARG
  * is returned. */
 swih_status swih_server_cancel(swih_server_t server, uint64_t id);
+
+/* The pixels of a frame were rewritten: its resident integral histograms are
+ * dropped before any query submitted after this call is admitted. Call it
+ * after rewriting the pixels and before submitting queries on the new
+ * contents, with no query on the frame still waiting or running (with
+ * keep_ih = 0 it is not needed). */
+swih_status swih_server_frame_changed(swih_server_t server, int32_t frame_id);
+
+/* Counters of the server (queries served, resident reuse, evictions). */
+swih_status swih_server_get_stats(swih_server_t server, swih_server_stats *stats);
 
 /* Block until every submitted query has completed (completions stay queued
  * for swih_server_poll). */

@@ -71,8 +71,7 @@ struct MicroBatch {
         int set = 0;                    // index into sets
         std::vector<int> frames;        // per region of the set
         std::vector<Rect> rects;
-        int pixel_type = 0, bitdepth = 0, bins = 0;
-        std::string sig;
+        std::string key;                // pixel type, bit depth, bins, term set and ring
     };
     std::vector<Built> built;
     std::vector<int> held;              // resident blocks this micro-batch reads (one use each)
@@ -130,18 +129,19 @@ WorkSpec spec_of(const swih_server_desc &d, const Query &qr)
     return sp;
 }
 
-// regions and jobs of a group of queries (indices into qs); merge: share
-// regions between overlapping crops of one frame
-void group_work(const std::vector<Query> &qs, const std::vector<int> &idx, bool merge,
-                std::vector<WorkRegion> &regions, std::vector<WorkJob> &jobs)
+// Regions of the crops of queries qs[idx] (merge: overlapping crops of one
+// frame share a region where that adds no pixels): regions (image rectangles),
+// their frame rectangles, and each query's region (region_of, indexed like qs).
+void crop_regions(const std::vector<Query> &qs, const std::vector<int> &idx, bool merge,
+                  std::vector<WorkRegion> &regions, std::vector<Rect> &rects, std::vector<int> &frames,
+                  std::vector<int> &region_of)
 {
     regions.clear();
-    jobs.clear();
-    // per frame: crops -> regions
-    std::map<const void *, std::vector<int>> by_frame;
-    for (int i : idx) by_frame[qs[i].f.d_pixels].push_back(i);
-    std::vector<int> region_of(qs.size(), -1);
-    std::vector<Rect> rect_of_region;
+    rects.clear();
+    frames.clear();
+    region_of.assign(qs.size(), -1);
+    std::map<int, std::vector<int>> by_frame;
+    for (int i : idx) by_frame[qs[i].q.frame].push_back(i);
     for (auto &kv : by_frame) {
         std::vector<Rect> crops, merged;
         for (int i : kv.second) crops.push_back(Rect{qs[i].q.x0, qs[i].q.y0, qs[i].q.width, qs[i].q.height});
@@ -163,15 +163,24 @@ void group_work(const std::vector<Query> &qs, const std::vector<int> &idx, bool 
             wr.H = r.h;
             wr.W = r.w;
             regions.push_back(wr);
-            rect_of_region.push_back(r);
+            rects.push_back(r);
+            frames.push_back(kv.first);
         }
         for (size_t c = 0; c < kv.second.size(); ++c) region_of[kv.second[c]] = base + of[c];
     }
+}
+
+// One job per window of each query qs[i], i in idx, over region region_of[i]
+// whose frame rectangle is rects[region_of[i]]: its histograms are scored
+// against every target of the query.
+void query_jobs(const std::vector<Query> &qs, const std::vector<int> &idx, const std::vector<Rect> &rects,
+                const std::vector<int> &region_of, std::vector<WorkJob> &jobs)
+{
+    jobs.clear();
     for (int i : idx) {
         const swih_query &q = qs[i].q;
         const int r = region_of[i];
-        const Rect &R = rect_of_region[r];
-        // one job per window: its histograms are scored against every target
+        const Rect &R = rects[r];
         for (int s = 0; s < q.n_scales; ++s) {
             WorkJob jb;
             jb.region = r;
@@ -190,6 +199,16 @@ void group_work(const std::vector<Query> &qs, const std::vector<int> &idx, bool 
             jobs.push_back(jb);
         }
     }
+}
+
+// regions and jobs of a group of queries (indices into qs) in one set
+void group_work(const std::vector<Query> &qs, const std::vector<int> &idx, bool merge,
+                std::vector<WorkRegion> &regions, std::vector<WorkJob> &jobs)
+{
+    std::vector<Rect> rects;
+    std::vector<int> frames, region_of;
+    crop_regions(qs, idx, merge, regions, rects, frames, region_of);
+    query_jobs(qs, idx, rects, region_of, jobs);
 }
 
 }  // namespace
@@ -215,8 +234,18 @@ struct swih_server_s {
     std::vector<MicroBatch *> zombies;  // failed micro-batches whose callback never ran
     std::thread th;
 
+    // resident integral histograms (keep_ih): the policy, and where each
+    // resident (block, region) lives; scheduler thread only
+    ResidentCache cache;
+    std::map<std::pair<int, int>, WorkRegion> resident_where;
+    std::vector<int> pending_invalidate;  // frames whose pixels changed (guarded by mu)
+    swih_server_stats stats{};            // guarded by mu
+
     void run();
     MicroBatch *try_build(const std::vector<Query> &qs, int si, bool &fatal, std::string &err);
+    int plan_part(MicroBatch *mb, const std::vector<int> &part, std::string &err);
+    bool alloc_dev(uint64_t bytes, uint64_t &off);
+    void free_block(int id, uint64_t off, uint64_t bytes);
     void release(MicroBatch *mb);
     void launch(MicroBatch *mb);
     void retire(MicroBatch *mb, std::vector<swih_completion> &out);
@@ -237,12 +266,145 @@ void CUDART_CB on_done(void *p)
 
 }  // namespace
 
+void swih_server_s::free_block(int id, uint64_t off, uint64_t bytes)
+{
+    for (auto it = resident_where.begin(); it != resident_where.end();)
+        it = it->first.first == id ? resident_where.erase(it) : std::next(it);
+    dev.release(off, bytes);
+}
+
+// arena memory, evicting resident integral histograms nobody uses (least
+// recently used first) until it fits
+bool swih_server_s::alloc_dev(uint64_t bytes, uint64_t &off)
+{
+    for (;;) {
+        if (dev.alloc(bytes, off)) return true;
+        uint64_t o = 0, b = 0;
+        int id = -1;
+        if (!cache.evict_one(o, b, &id)) return false;
+        free_block(id, o, b);
+    }
+}
+
 void swih_server_s::release(MicroBatch *mb)
 {
     for (auto &b : mb->dev_blocks) dev.release(b.first, b.second);
     mb->dev_blocks.clear();
+    for (auto &b : mb->built) dev.release(b.off, b.bytes);
+    mb->built.clear();
+    for (int id : mb->held) {
+        uint64_t off = 0, bytes = 0;
+        if (cache.release(id, off, bytes)) free_block(id, off, bytes);
+    }
+    mb->held.clear();
     if (mb->host_bytes) host.release(mb->host_off, mb->host_bytes);
     mb->host_bytes = 0;
+}
+
+enum { kPartOk = 0, kPartNoRoom = 1, kPartLayout = 2, kPartFail = 3 };
+
+// The work of queries `part` (same pixel type, bit depth, bins and kernel):
+// a build set (K1, K2) over the crops whose integral histograms are not
+// resident, then a gather set (K3 only) whose regions are all prebuilt: the
+// build set's and the resident ones. kPartLayout when the part's term set and
+// ring cannot be laid out (the caller splits it), kPartNoRoom when the arena
+// is full even after evicting what nobody uses.
+int swih_server_s::plan_part(MicroBatch *mb, const std::vector<int> &part, std::string &err)
+{
+    const std::vector<Query> &qs = mb->queries;
+    WorkSpec spec = spec_of(desc, qs[part[0]]);
+    for (int i : part)
+        for (int k = 0; k < qs[i].q.n_scales; ++k) {
+            spec.want_win_w = std::max(spec.want_win_w, qs[i].q.win_w[k]);
+            spec.want_win_h = std::max(spec.want_win_h, qs[i].q.win_h[k]);
+        }
+    // the part's term set and ring: a layout of its crops and jobs in one set
+    std::vector<WorkRegion> regions;
+    std::vector<WorkJob> jobs;
+    std::vector<Rect> rects;
+    std::vector<int> frames, region_of;
+    crop_regions(qs, part, false, regions, rects, frames, region_of);
+    query_jobs(qs, part, rects, region_of, jobs);
+    WorkSet dry;
+    if (dry.plan(spec, regions, jobs, err) != SWIH_OK) return kPartLayout;
+    const Query &q0 = qs[part[0]];
+    const std::string tail = "p" + std::to_string(q0.f.pixel_type) + "d" + std::to_string(q0.f.bitdepth);
+    const std::string key = dry.signature() + tail;
+    // resident hits; their blocks are taken before any allocation, so that
+    // making room for this part never evicts what it is about to read
+    std::vector<int> hit(qs.size(), -1), miss;
+    std::vector<ResidentCache::Entry> hit_entry(qs.size());
+    for (int i : part) {
+        const Rect c{qs[i].q.x0, qs[i].q.y0, qs[i].q.width, qs[i].q.height};
+        hit[i] = desc.keep_ih ? cache.find(qs[i].q.frame, key, c) : -1;
+        if (hit[i] < 0) {
+            miss.push_back(i);
+            continue;
+        }
+        hit_entry[i] = cache.entry(hit[i]);
+        if (std::find(mb->held.begin(), mb->held.end(), hit_entry[i].block) == mb->held.end()) {
+            cache.acquire(hit_entry[i].block);
+            mb->held.push_back(hit_entry[i].block);
+        }
+    }
+    std::vector<WorkRegion> pre;
+    std::vector<Rect> pre_rect;
+    std::vector<int> pre_of(qs.size(), -1);
+    if (!miss.empty()) {
+        std::vector<WorkRegion> br;
+        std::vector<Rect> brect;
+        std::vector<int> bframe, bof;
+        crop_regions(qs, miss, desc.merge_regions != 0, br, brect, bframe, bof);
+        std::unique_ptr<WorkSet> bs(new WorkSet());
+        if (bs->plan(spec, br, {}, err) != SWIH_OK) return kPartFail;
+        if (bs->signature() + tail != key) {
+            err = "internal: the build's term set differs from the gather's";
+            return kPartFail;
+        }
+        uint64_t off = 0;
+        if (!alloc_dev(bs->bytes(), off)) return kPartNoRoom;
+        MicroBatch::Built b;
+        b.off = off;
+        b.bytes = bs->bytes();
+        b.set = (int)mb->sets.size();
+        b.frames = bframe;
+        b.rects = brect;
+        b.key = key;
+        mb->built.push_back(b);
+        if (bs->bind(d_arena + off, err) != SWIH_OK) return kPartFail;
+        const int base = (int)pre.size();
+        for (int k = 0; k < (int)br.size(); ++k) {
+            pre.push_back(bs->region_as_prebuilt(k));
+            pre_rect.push_back(brect[k]);
+        }
+        for (int i : miss) pre_of[i] = base + bof[i];
+        mb->sets.push_back(std::move(bs));
+        mb->set_queries.push_back(miss);
+    }
+    std::map<std::pair<int, int>, int> entry_region;  // (block, region) -> gather-set region
+    for (int i : part) {
+        if (hit[i] < 0) continue;
+        const ResidentCache::Entry &E = hit_entry[i];
+        const std::pair<int, int> at{E.block, E.region};
+        if (!entry_region.count(at)) {
+            entry_region[at] = (int)pre.size();
+            pre.push_back(resident_where.at(at));
+            pre_rect.push_back(E.rect);
+        }
+        pre_of[i] = entry_region[at];
+        mb->reused[i] = 1;
+    }
+    std::vector<WorkJob> gj;
+    query_jobs(qs, part, pre_rect, pre_of, gj);
+    std::unique_ptr<WorkSet> gs(new WorkSet());
+    if (gs->plan(spec, pre, gj, err) != SWIH_OK) return kPartFail;
+    uint64_t off = 0;
+    if (!alloc_dev(gs->bytes(), off)) return kPartNoRoom;
+    mb->dev_blocks.push_back({off, gs->bytes()});
+    if (gs->bind(d_arena + off, err) != SWIH_OK) return kPartFail;
+    mb->sets.push_back(std::move(gs));
+    mb->set_queries.push_back(part);
+    return kPartOk;
 }
 
 // Lay out the micro-batch of queries qs and take its memory; nullptr when the
@@ -254,62 +416,31 @@ MicroBatch *swih_server_s::try_build(const std::vector<Query> &qs, int si, bool 
     mb->srv = this;
     mb->slot = si;
     mb->queries = qs;
-    // groups: queries that can share one work set
+    mb->reused.assign(qs.size(), 0);
+    // groups: queries that can share integral histograms
     std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
     for (int i = 0; i < (int)qs.size(); ++i)
         groups[std::make_tuple(qs[i].f.pixel_type, qs[i].f.bitdepth, qs[i].q.bins, qs[i].q.kernel)].push_back(i);
     for (auto &kv : groups) {
-        // one set per group; a group whose combined windows leave the exact
-        // ring (the largest window of one query with the largest of another)
-        // falls back to one set per query
-        std::vector<std::vector<int>> parts{kv.second};
-        for (int attempt = 0; attempt < 2; ++attempt) {
-            bool ok = true;
-            std::vector<std::unique_ptr<WorkSet>> made;
-            for (auto &part : parts) {
-                std::vector<WorkRegion> regions;
-                std::vector<WorkJob> jobs;
-                group_work(mb->queries, part, desc.merge_regions != 0, regions, jobs);
-                std::unique_ptr<WorkSet> ws(new WorkSet());
-                if (ws->plan(spec_of(desc, mb->queries[part[0]]), regions, jobs, err) != SWIH_OK) {
-                    ok = false;
-                    break;
-                }
-                made.push_back(std::move(ws));
+        // a group whose combined windows leave the exact ring (the largest
+        // window of one query with the largest of another) runs one part per query
+        int r = plan_part(mb.get(), kv.second, err);
+        if (r == kPartLayout && kv.second.size() > 1) {
+            r = kPartOk;
+            for (int i : kv.second) {
+                r = plan_part(mb.get(), {i}, err);
+                if (r != kPartOk) break;
             }
-            if (ok) {
-                for (size_t p = 0; p < parts.size(); ++p) {
-                    mb->sets.push_back(std::move(made[p]));
-                    mb->set_queries.push_back(parts[p]);
-                }
-                break;
-            }
-            if (attempt == 1 || kv.second.size() == 1) {
-                fatal = true;
-                return nullptr;
-            }
-            parts.clear();
-            for (int i : kv.second) parts.push_back({i});
+        }
+        if (r != kPartOk) {
+            release(mb.get());
+            fatal = r != kPartNoRoom;
+            return nullptr;
         }
     }
-    // memory: device blocks per set, one staging block for tables + status words
+    // one staging block for the tables and the status words
     uint64_t staging = 0;
-    for (auto &ws : mb->sets) {
-        uint64_t off = 0;
-        if (!dev.alloc(ws->bytes(), off)) {
-            release(mb.get());
-            return nullptr;
-        }
-        mb->dev_blocks.push_back({off, ws->bytes()});
-        std::string e2;
-        if (ws->bind(d_arena + off, e2) != SWIH_OK) {
-            err = e2;
-            release(mb.get());
-            fatal = true;
-            return nullptr;
-        }
-        staging += Arena::granules(ws->tables_bytes());
-    }
+    for (auto &ws : mb->sets) staging += Arena::granules(ws->tables_bytes());
     staging += Arena::granules(sizeof(uint32_t) * mb->sets.size());
     if (!host.alloc(staging, mb->host_off)) {
         release(mb.get());
@@ -374,6 +505,8 @@ void swih_server_s::retire(MicroBatch *mb, std::vector<swih_completion> &out)
         c.submit_ns = mb->queries[i].submit_ns;
         c.start_ns = mb->queries[i].start_ns;
         c.done_ns = t;
+        c.ih_reused = mb->reused[i];
+        c.reserved = 0;
         out.push_back(c);
     }
     if (mb->hostfn && !mb->fired) {
@@ -384,7 +517,33 @@ void swih_server_s::retire(MicroBatch *mb, std::vector<swih_completion> &out)
         return;
     }
     if (mb->ev) cudaEventDestroy(mb->ev);
+    // integral histograms built without error stay resident (keep_ih) until
+    // their memory is needed or their frame changes
+    for (auto &b : mb->built) {
+        const bool ok = mb->launch_status == SWIH_OK && !(mb->h_status[b.set] & kStatusTimeout);
+        if (!desc.keep_ih || !ok) {
+            dev.release(b.off, b.bytes);
+            continue;
+        }
+        const int id = cache.add_block(b.off, b.bytes);
+        for (int k = 0; k < (int)b.rects.size(); ++k) {
+            cache.add_entry(id, b.frames[k], b.rects[k], b.key, k);
+            resident_where[{id, k}] = mb->sets[b.set]->region_as_prebuilt(k);
+        }
+    }
+    uint64_t n_built = 0, n_reused = 0;
+    for (auto &b : mb->built) n_built += b.rects.size();
+    for (char r : mb->reused) n_reused += r ? 1 : 0;
+    mb->built.clear();
     release(mb);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        stats.queries += mb->queries.size();
+        stats.ih_reused += n_reused;
+        stats.regions_built += n_built;
+        stats.evictions = cache.evictions();
+        stats.resident_bytes = cache.resident_bytes();
+    }
     delete mb;
 }
 
@@ -409,7 +568,7 @@ void swih_server_s::run()
             return true;
         };
         const bool woke = cv.wait_for(lk, std::chrono::milliseconds(20), [&] {
-            return any_done() || (!mem_blocked && !queue.empty() && free_slot() >= 0) ||
+            return any_done() || (!mem_blocked && !queue.empty() && free_slot() >= 0) || !pending_invalidate.empty() ||
                    (stop && queue.empty() && idle());
         });
         if (stop && queue.empty() && idle()) break;
@@ -448,6 +607,22 @@ void swih_server_s::run()
             outstanding -= out.size();
             mem_blocked = false;
             cv_done.notify_all();
+        }
+        // frames whose pixels changed: their resident integral histograms go
+        // before anything newer is admitted
+        if (!pending_invalidate.empty()) {
+            std::vector<int> frames;
+            frames.swap(pending_invalidate);
+            lk.unlock();
+            for (int f : frames) {
+                std::vector<std::pair<uint64_t, uint64_t>> blocks;
+                std::vector<int> ids;
+                cache.invalidate_frame(f, blocks, &ids);
+                for (size_t k = 0; k < ids.size(); ++k) free_block(ids[k], blocks[k].first, blocks[k].second);
+            }
+            lk.lock();
+            stats.resident_bytes = cache.resident_bytes();
+            mem_blocked = false;
         }
         // admit, oldest first
         int si;
@@ -682,6 +857,26 @@ swih_status swih_server_cancel(swih_server_t S, uint64_t id)
         }
     }
     return sfail(SWIH_ERR_INVALID_ARG, "query " + std::to_string(id) + " is not waiting for admission");
+}
+
+swih_status swih_server_frame_changed(swih_server_t S, int32_t frame_id)
+{
+    if (!S) return sfail(SWIH_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (frame_id < 0 || frame_id >= (int)S->frames.size()) return sfail(SWIH_ERR_INVALID_ARG, "no such frame");
+        S->pending_invalidate.push_back(frame_id);
+    }
+    S->cv.notify_all();
+    return SWIH_OK;
+}
+
+swih_status swih_server_get_stats(swih_server_t S, swih_server_stats *out)
+{
+    if (!S || !out) return sfail(SWIH_ERR_INVALID_ARG, "server and out are required");
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    return SWIH_OK;
 }
 
 swih_status swih_server_drain(swih_server_t S)

@@ -158,6 +158,8 @@ class swih_server_desc(ctypes.Structure):
         ("gauss_degree", ctypes.c_int32),
         ("gauss_sigma_frac", ctypes.c_double),
         ("staging_bytes", ctypes.c_uint64),
+        ("keep_ih", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -200,6 +202,18 @@ class swih_completion(ctypes.Structure):
         ("submit_ns", ctypes.c_uint64),
         ("start_ns", ctypes.c_uint64),
         ("done_ns", ctypes.c_uint64),
+        ("ih_reused", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class swih_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("queries", ctypes.c_uint64),
+        ("ih_reused", ctypes.c_uint64),
+        ("regions_built", ctypes.c_uint64),
+        ("evictions", ctypes.c_uint64),
+        ("resident_bytes", ctypes.c_uint64),
     ]
 
 
@@ -280,6 +294,8 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.swih_server_drain.argtypes = [P]
     lib.swih_server_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.swih_server_frame_changed.argtypes = [P, ctypes.c_int32]
+    lib.swih_server_get_stats.argtypes = [P, ctypes.POINTER(swih_server_stats)]
     lib.swih_server_destroy.argtypes = [P]
     lib.swih_stream_plan.argtypes = [ctypes.POINTER(swih_plan_desc), ctypes.POINTER(swih_frame_job), I, P,
                                      ctypes.c_int32, ctypes.POINTER(P)]
@@ -295,7 +311,8 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = S
     for name in ("swih_server_create", "swih_server_add_frame", "swih_query_out_elems",
                  "swih_server_query_bytes", "swih_server_submit", "swih_server_poll",
-                 "swih_server_drain", "swih_server_destroy", "swih_server_cancel"):
+                 "swih_server_drain", "swih_server_destroy", "swih_server_cancel", "swih_server_frame_changed",
+                 "swih_server_get_stats"):
         getattr(lib, name).restype = S
     return lib
 
@@ -692,8 +709,10 @@ class Server:
     """Owning wrapper of swih_server_*; frames are device buffers kept alive here."""
 
     def __init__(self, hbm_budget_bytes, max_inflight=4, max_batch_queries=16, merge_regions=True,
-                 gauss_degree=0, gauss_sigma_frac=0.0, staging_bytes=0):
+                 gauss_degree=0, gauss_sigma_frac=0.0, staging_bytes=0, keep_ih=False):
         d = swih_server_desc()
+        d.keep_ih = 1 if keep_ih else 0
+        d.reserved = 0
         d.hbm_budget_bytes = int(hbm_budget_bytes)
         d.max_inflight = int(max_inflight)
         d.max_batch_queries = int(max_batch_queries)
@@ -741,6 +760,14 @@ class Server:
 
     def cancel(self, qid: int):
         _check(LIB.swih_server_cancel(self.handle, int(qid)))
+
+    def frame_changed(self, frame_id: int):
+        _check(LIB.swih_server_frame_changed(self.handle, int(frame_id)))
+
+    def stats(self) -> dict:
+        st = swih_server_stats()
+        _check(LIB.swih_server_get_stats(self.handle, ctypes.byref(st)))
+        return {name: int(getattr(st, name)) for name, _ in swih_server_stats._fields_}
 
     def close(self):
         if self.handle:

@@ -29,6 +29,7 @@ __all__ = [
     "config4",
     "config5_frames",
     "config5_queries",
+    "config5_repeat_queries",
     "odd_window",
 ]
 
@@ -273,6 +274,41 @@ def config5_queries(seed: int = 5, n: int = 1000, rate: float = 2000.0, n_frames
         targets /= targets.sum(1, keepdims=True)
         out.append(dict(t=t, frame=int(rng.integers(0, n_frames)), x0=x0, y0=y0, w=w, h=h, B=B,
                         kernel=kernel, windows=[(v, v) for v in wins], targets=targets.astype(np.float32)))
+    return out
+
+
+def config5_repeat_queries(seed: int = 6, n_frames: int = 16, size: int = 2048, regions_per_frame: int = 5,
+                           repeats: int = 5, rate: float = 2000.0, crop_range: tuple = (256, 512)) -> list:
+    """Tracking queries that come back to the same search regions: on each
+    frame, regions_per_frame search regions (side U{256..512} at a uniform
+    position, B from {16, 32}, kernel Manhattan or Euclidean), each queried
+    `repeats` times (a tracker asking again for other targets or scales of a
+    candidate region) at Poisson arrival times of mean rate `rate`, in a
+    seeded random order. Each query has 1-4 targets and 1-3 windows of
+    15/25/43/75/127 that fit the crop. Same dict layout as config5_queries."""
+    rng = np.random.default_rng(seed)
+    regions = []
+    for f in range(n_frames):
+        for _ in range(regions_per_frame):
+            w = int(rng.integers(crop_range[0], crop_range[1] + 1))
+            h = int(rng.integers(crop_range[0], crop_range[1] + 1))
+            regions.append((f, int(rng.integers(0, size - w + 1)), int(rng.integers(0, size - h + 1)), w, h,
+                            int(rng.choice([16, 32])), ("manhattan", "euclidean")[int(rng.integers(0, 2))]))
+    order = [r for r in range(len(regions)) for _ in range(repeats)]
+    rng.shuffle(order)
+    out = []
+    t = 0.0
+    for r in order:
+        f, x0, y0, w, h, B, kernel = regions[r]
+        t += float(rng.exponential(1.0 / rate))
+        nt = int(rng.integers(1, 5))
+        fit = [v for v in SERVE_WINDOWS if v <= min(w, h)]
+        ns = min(int(rng.integers(1, 4)), len(fit))
+        wins = sorted(int(v) for v in rng.choice(fit, ns, replace=False))
+        targets = rng.gamma(0.5, 1.0, size=(nt, B))
+        targets /= targets.sum(1, keepdims=True)
+        out.append(dict(t=t, frame=f, x0=x0, y0=y0, w=w, h=h, B=B, kernel=kernel,
+                        windows=[(v, v) for v in wins], targets=targets.astype(np.float32)))
     return out
 
 

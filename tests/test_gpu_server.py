@@ -279,3 +279,102 @@ def test_cancel_queued_queries():
     for i in (0, 1, 11, 29):
         if qids[i] not in cancelled:
             check_oracle(scene, specs[i], outs[i])
+
+
+# ---------------------------------------------------------------- resident integral histograms
+def one_query(srv, ids, sp):
+    out = sp.new_out()
+    n0 = S.swih_launch_count()
+    srv.submit(sp.query(ids, out))
+    srv.drain()
+    (c,) = srv.poll(max_n=4)
+    assert c.status == S.SWIH_OK
+    return out, c, S.swih_launch_count() - n0
+
+
+def test_a_crop_inside_a_resident_region_skips_quantise_and_scan():
+    scene = Scene(seed=21)
+    q = np.full((2, 16), 1.0 / 16)
+    big = QSpec(0, 40, 30, 300, 250, 16, "euclidean", [(15, 15), (25, 21)], q)
+    inner = QSpec(0, 90, 70, 120, 100, 16, "euclidean", [(9, 9), (25, 25)], q[:1])
+    other_bins = QSpec(0, 90, 70, 120, 100, 32, "euclidean", [(9, 9)], np.full((1, 32), 1.0 / 32))
+    with S.Server(hbm_budget_bytes=4 << 30, max_inflight=1, keep_ih=True) as srv:
+        ids = scene.register(srv)
+        _, c1, n1 = one_query(srv, ids, big)
+        assert c1.ih_reused == 0 and n1 >= 4  # quantise, scan, row map, gather
+        out, c2, n2 = one_query(srv, ids, inner)
+        assert c2.ih_reused == 1 and n2 == n1 - 3, (n1, n2)  # the gather alone
+        _, c3, n3 = one_query(srv, ids, other_bins)
+        assert c3.ih_reused == 0 and n3 == n1, "another bin count cannot read these integral histograms"
+        st = srv.stats()
+        assert st["queries"] == 3 and st["ih_reused"] == 1 and st["regions_built"] == 2
+        assert st["resident_bytes"] > 0
+    check_oracle(scene, inner, out)
+    with S.Server(hbm_budget_bytes=4 << 30, max_inflight=1) as srv:  # no residency: same maps
+        ids = scene.register(srv)
+        ref, c, _ = one_query(srv, ids, inner)
+        assert c.ih_reused == 0
+    assert torch.equal(ref, out)
+
+
+def test_resident_reuse_in_the_mix_equals_alone():
+    scene = Scene()
+    specs = make_specs(scene, 24, seed=7)
+    kw = dict(hbm_budget_bytes=8 << 30, max_inflight=4, max_batch_queries=16, merge_regions=True)
+    alone = run_alone(scene, specs, **kw)
+    outs = [sp.new_out() for sp in specs]
+    with S.Server(keep_ih=True, **kw) as srv:
+        ids = scene.register(srv)
+        for rep in range(2):  # the second pass finds every crop resident
+            for o in outs:
+                o.fill_(-1.0)
+            for i, (sp, o) in enumerate(zip(specs, outs)):
+                srv.submit(sp.query(ids, o, tag=i))
+            srv.drain()
+            comps = srv.poll(max_n=len(specs) + 8)
+            assert all(c.status == S.SWIH_OK for c in comps) and len(comps) == len(specs)
+            if rep == 1:
+                assert all(c.ih_reused == 1 for c in comps)
+            for sp, a, m in zip(specs, alone, outs):
+                assert torch.equal(a, m), (rep, sp.kernel)
+        st = srv.stats()
+        assert st["queries"] == 48 and st["ih_reused"] >= 24
+
+
+def test_resident_regions_are_evicted_under_a_tight_budget():
+    scene = Scene(seed=11)
+    specs = make_specs(scene, 16, seed=3, overlap=False)
+    with S.Server(hbm_budget_bytes=8 << 30) as probe:
+        ids = scene.register(probe)
+        need = [probe.query_bytes(sp.query(ids, 0)) for sp in specs]
+    alone = run_alone(scene, specs, hbm_budget_bytes=8 << 30)
+    outs = [sp.new_out() for sp in specs]
+    with S.Server(hbm_budget_bytes=int(max(need) * 1.6), max_inflight=2, max_batch_queries=4,
+                  keep_ih=True) as srv:
+        ids = scene.register(srv)
+        for i, (sp, o) in enumerate(zip(specs, outs)):
+            srv.submit(sp.query(ids, o, tag=i))
+        srv.drain()
+        comps = srv.poll(max_n=32)
+        assert all(c.status == S.SWIH_OK for c in comps) and len(comps) == len(specs)
+        assert srv.stats()["evictions"] > 0
+    for a, m in zip(alone, outs):
+        assert torch.equal(a, m)
+
+
+def test_frame_changed_drops_its_resident_regions():
+    scene = Scene(seed=5)
+    sp = QSpec(0, 20, 20, 200, 150, 16, "manhattan", [(15, 15)], np.full((1, 16), 1.0 / 16))
+    with S.Server(hbm_budget_bytes=2 << 30, max_inflight=1, keep_ih=True) as srv:
+        ids = scene.register(srv)
+        one_query(srv, ids, sp)
+        _, c, _ = one_query(srv, ids, sp)
+        assert c.ih_reused == 1
+        # new pixels in frame 0, announced to the server
+        new = synth.blob_scene(420, 560, 8, 99, n_blobs=8, margin=50).image
+        scene.dev[0].copy_(torch.from_numpy(new))
+        scene.frames[0] = (new, 8)
+        srv.frame_changed(ids[0])
+        out, c, _ = one_query(srv, ids, sp)
+        assert c.ih_reused == 0
+    check_oracle(scene, sp, out)

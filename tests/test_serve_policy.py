@@ -17,8 +17,10 @@ CSRC = os.path.join(ROOT, "paper_1705_03524_gb300", "csrc")
 
 HARNESS = r'''
 #include <cstdio>
+#include <map>
 #include <random>
 #include <set>
+#include <string>
 #include "serve_policy.h"
 using namespace swih;
 
@@ -94,7 +96,112 @@ int main() {
     std::vector<int> in = merge_crops({Rect{0, 0, 100, 100}, Rect{20, 30, 10, 10}}, reg, 8192);
     const bool inside_ok = reg.size() == 1 && reg[0].w == 100 && reg[0].h == 100 && in[1] == 0;
 
-    std::printf("{\"allocs\": %d, \"fails\": %d, \"overlap\": %d, \"oob\": %d, \"misaligned\": %d, "
+    // ---- resident integral histograms: random operations against a model
+    int cache_bad = 0, cache_ops = 0, evicted_in_use = 0, found_wrong = 0, freed_twice = 0, hits = 0;
+    {
+        ResidentCache c;
+        struct M { int frame; Rect r; std::string key; int block; };
+        std::vector<M> model;                 // live entries
+        std::map<int, int> users, entries;    // per live block
+        std::map<int, std::pair<uint64_t, uint64_t>> where;
+        std::set<int> gone;                   // blocks freed or evicted
+        uint64_t next_off = 0;
+        auto forget = [&](int id) {
+            if (gone.count(id)) ++freed_twice;
+            gone.insert(id);
+            users.erase(id);
+            entries.erase(id);
+            where.erase(id);
+        };
+        for (int it = 0; it < 20000; ++it) {
+            const int op = (int)(rng() % 6);
+            ++cache_ops;
+            if (op == 0) {  // a build becomes resident: a block with 1-3 entries
+                const uint64_t bytes = 256 * (1 + rng() % 64);
+                const int id = c.add_block(next_off, bytes);
+                where[id] = {next_off, bytes};
+                next_off += bytes;
+                users[id] = 0;
+                const int n = 1 + (int)(rng() % 3);
+                for (int k = 0; k < n; ++k) {
+                    M m{(int)(rng() % 4), Rect{(int)(rng() % 200), (int)(rng() % 200), 20 + (int)(rng() % 200),
+                                               20 + (int)(rng() % 200)}, (rng() % 2) ? "a" : "b", id};
+                    c.add_entry(id, m.frame, m.r, m.key, k);
+                    model.push_back(m);
+                    ++entries[id];
+                }
+            } else if (op == 1) {  // lookup: the answer holds the crop, and one exists iff the model has one
+                const int f = (int)(rng() % 4);
+                const std::string key = (rng() % 2) ? "a" : "b";
+                const Rect q{(int)(rng() % 300), (int)(rng() % 300), 3 + (int)(rng() % 60), 3 + (int)(rng() % 60)};
+                const int e = c.find(f, key, q);
+                bool any = false;
+                for (auto &m : model)
+                    any |= m.frame == f && m.key == key && q.x0 >= m.r.x0 && q.y0 >= m.r.y0 &&
+                           q.x0 + q.w <= m.r.x0 + m.r.w && q.y0 + q.h <= m.r.y0 + m.r.h;
+                if ((e >= 0) != any) ++found_wrong;
+                if (e >= 0) {
+                    ++hits;
+                    const auto &E = c.entry(e);
+                    if (E.frame != f || E.key != key || q.x0 < E.rect.x0 || q.y0 < E.rect.y0 ||
+                        q.x0 + q.w > E.rect.x0 + E.rect.w || q.y0 + q.h > E.rect.y0 + E.rect.h || gone.count(E.block))
+                        ++found_wrong;
+                    if (rng() % 2) {  // a micro-batch reads it
+                        c.acquire(E.block);
+                        ++users[E.block];
+                    }
+                }
+            } else if (op == 2 && !users.empty()) {  // a micro-batch that read a block retires
+                auto it2 = users.begin();
+                std::advance(it2, (long)(rng() % users.size()));
+                if (it2->second > 0) {
+                    const int id = it2->first;
+                    --it2->second;
+                    uint64_t off = 0, bytes = 0;
+                    const bool fr = c.release(id, off, bytes);
+                    const bool should = users[id] == 0 && entries[id] == 0;
+                    if (fr != should || (fr && where[id] != std::make_pair(off, bytes))) ++cache_bad;
+                    if (fr) forget(id);
+                }
+            } else if (op == 3) {  // evict one
+                uint64_t off = 0, bytes = 0;
+                int id = -1;
+                const bool ok = c.evict_one(off, bytes, &id);
+                bool idle = false;
+                for (auto &kv : users) idle |= kv.second == 0;
+                if (ok != idle) ++cache_bad;
+                if (ok) {
+                    if (users[id] != 0) ++evicted_in_use;
+                    if (where[id] != std::make_pair(off, bytes)) ++cache_bad;
+                    for (size_t i = 0; i < model.size();)
+                        if (model[i].block == id) model.erase(model.begin() + (long)i); else ++i;
+                    forget(id);
+                }
+            } else if (op == 4) {  // a frame's pixels change
+                const int f = (int)(rng() % 4);
+                std::vector<std::pair<uint64_t, uint64_t>> freed;
+                std::vector<int> ids;
+                c.invalidate_frame(f, freed, &ids);
+                for (size_t i = 0; i < model.size();)
+                    if (model[i].frame == f) { --entries[model[i].block]; model.erase(model.begin() + (long)i); } else ++i;
+                for (size_t k = 0; k < ids.size(); ++k) {
+                    if (users[ids[k]] != 0 || entries[ids[k]] != 0 || where[ids[k]] != freed[k]) ++cache_bad;
+                    forget(ids[k]);
+                }
+                for (auto &kv : entries)
+                    if (kv.second == 0 && users[kv.first] == 0 && !std::count(ids.begin(), ids.end(), kv.first)) ++cache_bad;
+            }
+            if (c.n_entries() != model.size()) ++cache_bad;
+            uint64_t live = 0;
+            for (auto &kv : where) live += kv.second.second;
+            if (c.resident_bytes() != live || c.n_blocks() != where.size()) ++cache_bad;
+        }
+    }
+
+    std::printf("{\"cache_ops\": %d, \"cache_bad\": %d, \"evicted_in_use\": %d, \"found_wrong\": %d, "
+                "\"freed_twice\": %d, \"hits\": %d, ", cache_ops, cache_bad, evicted_in_use, found_wrong,
+                freed_twice, hits);
+    std::printf("\"allocs\": %d, \"fails\": %d, \"overlap\": %d, \"oob\": %d, \"misaligned\": %d, "
                 "\"used_bad\": %d, \"whole\": %d, \"cases\": %d, \"merged_some\": %d, \"not_covered\": %d, "
                 "\"extra_pixels\": %d, \"too_wide\": %d, \"bad_index\": %d, \"same\": %d, \"apart\": %d, "
                 "\"inside\": %d}\n",
@@ -134,17 +241,29 @@ def test_crop_merging_invariants(policy_results):
     assert r["same"] == 1 and r["apart"] == 1 and r["inside"] == 1
 
 
+def test_resident_cache_against_a_model(policy_results):
+    """Resident integral histograms: lookups answer exactly when a live entry
+    of the frame and key holds the crop; a block in use is never evicted; a
+    block is freed once, when it has neither users nor entries; invalidating a
+    frame drops exactly its entries; the resident byte count stays exact."""
+    r = policy_results
+    assert r["cache_ops"] == 20000 and r["hits"] > 100
+    assert r["cache_bad"] == 0 and r["found_wrong"] == 0
+    assert r["evicted_in_use"] == 0 and r["freed_twice"] == 0
+
+
 def test_server_struct_layout_matches_header():
     src = r'''
 #include <stdio.h>
 #include <stddef.h>
 #include "swih.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(swih_server_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(swih_server_desc),
          offsetof(swih_server_desc, gauss_sigma_frac), offsetof(swih_server_desc, staging_bytes),
          sizeof(swih_frame_desc), offsetof(swih_frame_desc, pitch_bytes), sizeof(swih_query),
          offsetof(swih_query, d_targets), offsetof(swih_query, user_tag), sizeof(swih_completion),
-         offsetof(swih_completion, done_ns));
+         offsetof(swih_completion, done_ns), offsetof(swih_server_desc, keep_ih),
+         offsetof(swih_completion, ih_reused), sizeof(swih_server_stats));
   return 0;
 }
 '''
@@ -159,7 +278,9 @@ int main(void) {
                     S.swih_server_desc.staging_bytes.offset, ctypes.sizeof(S.swih_frame_desc),
                     S.swih_frame_desc.pitch_bytes.offset, ctypes.sizeof(S.swih_query),
                     S.swih_query.d_targets.offset, S.swih_query.user_tag.offset,
-                    ctypes.sizeof(S.swih_completion), S.swih_completion.done_ns.offset]
+                    ctypes.sizeof(S.swih_completion), S.swih_completion.done_ns.offset,
+                    S.swih_server_desc.keep_ih.offset, S.swih_completion.ih_reused.offset,
+                    ctypes.sizeof(S.swih_server_stats)]
 
 
 def test_query_out_elems_and_validation():
