@@ -1201,42 +1201,46 @@ def run_serving_repeats(S, synth, dev, frames, d_frames, stats_fn):
 
 
 # ----------------------------------------------------------------------------- Fig. 6
-def run_fig6(args):
+FIG6_KINDS = (("manhattan", 2), ("euclidean", 2), ("gaussian", 2), ("gaussian", 3), ("exponential", 2))
+FIG6_WINDOWS = (11, 21, 41, 61, 81, 121, 161, 201, 301, 401)
+
+
+def run_fig6(args, frames=((480, 640), (1024, 1024)), cpu=True, reps=10):
     """Time per likelihood map against window size (the experiment of Fig. 6):
     SWIH on the GPU (quantise + integral histograms + gather, CUDA events, and
-    the gather alone) and the brute-force oracle on the host cores (timed on a
-    sample of centres and scaled to the whole map), on 640x480 and 1024x1024
-    frames of the benchmark's scene generator, B = 32."""
+    the gather alone) for the Manhattan, Euclidean, Gaussian (degree 2 and 3)
+    and exponential kernels, and with cpu the brute-force oracle on the host
+    cores (timed on a sample of centres and scaled to the whole map), on
+    frames of the benchmark's scene generator, B = 32. Gaussian windows whose
+    exact moments pass 2^64 use the 128-bit ring and the any-degree gather."""
     import torch
 
-    from oracle import swih_oracle as O
     from paper_1705_03524_gb300 import swih as S
     from paper_1705_03524_gb300 import synth
 
-    O.build()
+    if cpu:
+        from oracle import swih_oracle as O
+        O.build()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     B = 32
     rows = []
-    for (H, W) in ((480, 640), (1024, 1024)):
+    for (H, W) in frames:
         sc = synth.blob_scene(H, W, 8, seed=2, n_blobs=8)
         img = sc.image
         d_img = torch.from_numpy(img).to(dev)
-        bins = O.quantize(img, 8, B)
-        for kind in ("manhattan", "euclidean", "gaussian", "exponential"):
-            wins = [w for w in (11, 21, 41, 61, 81, 121, 161, 201, 301, 401) if w < min(H, W)]
-            if kind == "gaussian":
-                wins = [w for w in wins if w <= 121]  # exact 64-bit moments: w h rx^4 ry^4 < 2^64
-            for w in wins:
-                desc = S.make_desc(H, W, bins=B, kernels=(kind,), max_win=(w, w))
+        bins = O.quantize(img, 8, B) if cpu else None
+        for kind, degree in FIG6_KINDS:
+            for w in (w for w in FIG6_WINDOWS if w < min(H, W)):
+                desc = S.make_desc(H, W, bins=B, kernels=(kind,), max_win=(w, w), gauss_degree=degree)
                 with S.Plan(desc) as p:
+                    elem = p.info().elem_bytes
                     q = torch.full((B,), 1.0 / B, device=dev)
                     m = torch.empty((H - w + 1, W - w + 1), device=dev)
                     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                     for _ in range(3):
                         p.build_ih(d_img, stream)
                         p.likelihood(kind, w, w, q, m, stream)
-                    reps = 10
                     t_all, t_g = 0.0, 0.0
                     for _ in range(reps):
                         ev[0].record(stream)
@@ -1248,25 +1252,27 @@ def run_fig6(args):
                         t_all += ev[0].elapsed_time(ev[2])
                         t_g += ev[1].elapsed_time(ev[2])
                     p.sync_status(stream)
-                K = O.kernel_weights(kind, w, w)
-                r = w // 2
                 n_c = (H - w + 1) * (W - w + 1)
-                rng = np.random.default_rng(w)
-                n_s = int(max(256, min(n_c, 2e8 / (w * w))))
-                cx = rng.integers(r, W - r, n_s)
-                cy = rng.integers(r, H - r, n_s)
-                t0 = time.perf_counter()
-                O.likelihood_at(bins, B, K, np.full(B, 1.0 / B), cx, cy)
-                t_cpu = (time.perf_counter() - t0) / n_s * n_c * 1e3
-                rows.append({"frame": f"{W}x{H}", "kernel": kind, "window": w, "centres": n_c,
-                             "swih_ms": t_all / reps, "swih_gather_ms": t_g / reps,
-                             "brute_force_cpu_ms": t_cpu, "cpu_threads": O.threads(),
-                             "cpu_sample_centres": n_s})
-                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                row = {"frame": f"{W}x{H}", "kernel": kind if kind != "gaussian" else f"gaussian_d{degree}",
+                       "window": w, "centres": n_c, "ring_bits": 8 * elem,
+                       "swih_ms": t_all / reps, "swih_gather_ms": t_g / reps}
+                if cpu:
+                    K = O.kernel_weights(kind, w, w, degree=degree)
+                    r = w // 2
+                    rng = np.random.default_rng(w)
+                    n_s = int(max(256, min(n_c, 2e8 / (w * w))))
+                    cx = rng.integers(r, W - r, n_s)
+                    cy = rng.integers(r, H - r, n_s)
+                    t0 = time.perf_counter()
+                    O.likelihood_at(bins, B, K, np.full(B, 1.0 / B), cx, cy)
+                    row.update({"brute_force_cpu_ms": (time.perf_counter() - t0) / n_s * n_c * 1e3,
+                                "cpu_threads": O.threads(), "cpu_sample_centres": n_s})
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
     return {"fig6": rows, "bins": B,
             "note": ("SWIH: GPU time per map (quantise + integral histograms + gather) and the gather "
-                     "alone; brute force: the FP64 oracle on the host cores, timed on a sample of "
-                     "centres and scaled to the map")}
+                     "alone" + ("; brute force: the FP64 oracle on the host cores, timed on a sample of "
+                                "centres and scaled to the map" if cpu else ""))}
 
 
 # ----------------------------------------------------------------------------- oracle
@@ -1479,7 +1485,8 @@ def main():
         for name, fn in (("small_frame", run_small_frame), ("dense_scene", run_dense_scene),
                          ("batched_regions", run_regions),
                          ("serving", lambda a, d: run_serving(a, d, n_queries=a.serve_queries)),
-                         ("large_frame", run_large_frame), ("exponential", run_exponential)):
+                         ("large_frame", run_large_frame), ("exponential", run_exponential),
+                         ("fig6", lambda a, d: run_fig6(a, frames=((1024, 1024),), cpu=False, reps=5))):
             t0 = time.perf_counter()
             line[name] = fn(args, dev)
             progress(f"{name}: {time.perf_counter() - t0:.1f} s")

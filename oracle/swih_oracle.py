@@ -114,10 +114,18 @@ def weighted_ih(bins: np.ndarray, b: int, p: int, q: int, bits: int = 64) -> np.
 
     i is the column and j the row, so the result is indexed [y, x]. The
     sums are taken modulo 2^bits (bits = 32 or 64): unsigned numpy
-    arithmetic wraps, which is exact arithmetic in that ring.
+    arithmetic wraps, which is exact arithmetic in that ring. bits = 128
+    uses Python integers (an object array, for small images) reduced mod 2^128.
     """
+    if bits == 128:
+        h, w = bins.shape
+        term = np.zeros((h, w), dtype=object)
+        for y in range(h):
+            for x in range(w):
+                term[y, x] = (x ** p) * (y ** q) if bins[y, x] == b else 0
+        return np.cumsum(np.cumsum(term, axis=0), axis=1) % (1 << 128)
     if bits not in (32, 64):
-        raise ValueError("bits must be 32 or 64")
+        raise ValueError("bits must be 32, 64 or 128")
     h, w = bins.shape
     xs = np.arange(w, dtype=np.uint64)
     ys = np.arange(h, dtype=np.uint64)

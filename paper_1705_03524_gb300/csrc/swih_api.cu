@@ -57,11 +57,13 @@ int gauss_axis_degree(int r, int D) { return std::max(0, std::min(D, r)); }
 bool gauss_fit(int r, double sigma, int D, double *c)
 {
     const int n = D + 1;
-    double A[3][4] = {};
+    double A[kWideMaxD + 1][kWideMaxD + 2] = {};
     for (int d = -r; d <= r; ++d) {
         const double t = (double)d * d / ((double)r * r);
         const double y = std::exp(-(double)d * d / (2.0 * sigma * sigma));
-        const double pw[3] = {1.0, t, t * t};
+        double pw[kWideMaxD + 1];
+        pw[0] = 1.0;
+        for (int i = 1; i < n; ++i) pw[i] = pw[i - 1] * t;
         for (int i = 0; i < n; ++i) {
             for (int j = 0; j < n; ++j) A[i][j] += pw[i] * pw[j];
             A[i][n] += pw[i] * y;
@@ -87,16 +89,23 @@ bool gauss_fit(int r, double sigma, int D, double *c)
     return true;
 }
 
+double binom(int n, int k)
+{
+    double v = 1.0;
+    for (int i = 1; i <= k; ++i) v = v * (n - k + i) / i;
+    return v;
+}
+
 struct GaussAxis {
     int D = 0;
-    double beta[3] = {0, 0, 0};  // Bernstein coefficients of the fitted polynomial
-    double mass = 0;             // sum over d = -r..r of P(d^2 / r^2)
+    double beta[kWideMaxD + 1] = {};  // Bernstein coefficients of the fitted polynomial
+    double mass = 0;                  // sum over d = -r..r of P(d^2 / r^2)
 };
 
 bool gauss_axis(int r, double sigma, int D_req, GaussAxis &g, std::string &why)
 {
     g.D = gauss_axis_degree(r, D_req);
-    double c[3] = {0, 0, 0};
+    double c[kWideMaxD + 1] = {};
     if (g.D < 1) {
         why = "Gaussian window half-size must be >= 1";
         return false;
@@ -106,13 +115,9 @@ bool gauss_axis(int r, double sigma, int D_req, GaussAxis &g, std::string &why)
         return false;
     }
     // power basis -> Bernstein basis: beta_i = sum_{k<=i} C(i,k)/C(D,k) c_k
-    if (g.D == 1) {
-        g.beta[0] = c[0];
-        g.beta[1] = c[0] + c[1];
-    } else {
-        g.beta[0] = c[0];
-        g.beta[1] = c[0] + 0.5 * c[1];
-        g.beta[2] = c[0] + c[1] + c[2];
+    for (int i = 0; i <= g.D; ++i) {
+        g.beta[i] = 0.0;
+        for (int k = 0; k <= i; ++k) g.beta[i] += binom(i, k) / binom(g.D, k) * c[k];
     }
     for (int i = 0; i <= g.D; ++i)
         if (!(g.beta[i] >= 0.0)) {
@@ -122,7 +127,9 @@ bool gauss_axis(int r, double sigma, int D_req, GaussAxis &g, std::string &why)
     g.mass = 0.0;
     for (int d = -r; d <= r; ++d) {
         const double t = (double)d * d / ((double)r * r);
-        g.mass += c[0] + t * (c[1] + t * c[2]);
+        double v = 0.0;
+        for (int i = g.D; i >= 0; --i) v = v * t + c[i];
+        g.mass += v;
     }
     return true;
 }
@@ -164,11 +171,11 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "max window sides must be odd and >= 3");
     if (d->max_win_w > d->width || d->max_win_h > d->height)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "max window larger than the image");
-    if (d->precision < SWIH_PREC_AUTO || d->precision > SWIH_PREC_RING64)
+    if (d->precision < SWIH_PREC_AUTO || d->precision > SWIH_PREC_RING128)
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "precision out of range");
     if (d->band_rows < 0) return fail(nullptr, SWIH_ERR_INVALID_ARG, "band_rows must be >= 0");
     const int D = d->gauss_degree == 0 ? 2 : d->gauss_degree;
-    if (D < 1 || D > 2) return fail(nullptr, SWIH_ERR_UNSUPPORTED, "gauss_degree must be 1 or 2");
+    if (D < 1 || D > kWideMaxD) return fail(nullptr, SWIH_ERR_UNSUPPORTED, "gauss_degree must be in [1, 4]");
     const double sf = d->gauss_sigma_frac == 0.0 ? 0.25 : d->gauss_sigma_frac;
     if (!(sf > 0.0) || !std::isfinite(sf))
         return fail(nullptr, SWIH_ERR_INVALID_ARG, "gauss_sigma_frac must be positive");
@@ -195,7 +202,7 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         pl->exp_E = d->width > 4096 ? 16 : (d->width > 2048 ? 8 : 4);
         pl->exp_threads = (int)round_up((d->width + pl->exp_E - 1) / pl->exp_E, 32);
     }
-    bool mark[5][5] = {};
+    bool mark[kMaxP][kMaxQ] = {};
     const bool want_man = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_MANHATTAN);
     const bool want_euc = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_EUCLIDEAN);
     const bool want_gau = d->kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_GAUSSIAN);
@@ -213,9 +220,9 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         for (int &v : row) v = -1;
     pl->n_terms = 0;
     pl->n_q = 0;
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < kMaxQ; ++q) {
         int cnt = 0;
-        for (int p = 0; p < 5; ++p) {
+        for (int p = 0; p < kMaxP; ++p) {
             if (!mark[p][q]) continue;
             pl->term_p[pl->n_terms] = p;
             pl->term_q[pl->n_terms] = q;
@@ -241,13 +248,29 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
     if (d->kernel_mask & (SWIH_KERNEL_BIT(SWIH_KERNEL_WEDDING) | SWIH_KERNEL_BIT(SWIH_KERNEL_EXPONENTIAL)))
         need = std::max(need, int_kernel_mass(SWIH_KERNEL_PLAIN, d->max_win_w, d->max_win_h));  // window counts
     const bool fits32 = !want_gau && need < 4294967296.0L;
-    if (want_gau && gauss_bound(d->max_win_w, d->max_win_h, D) >= 18446744073709551616.0L)
-        return fail(nullptr, SWIH_ERR_UNSUPPORTED,
-                    "Gaussian window too large for exact 64-bit moments (w*h*rx^2D*ry^2D >= 2^64)");
+    // Gaussian: the per-window Bernstein moments are below w h rx^2D ry^2D;
+    // past 2^64 they are kept in the ring mod 2^128 (Gaussian-only plans)
+    const long double gb = want_gau ? gauss_bound(d->max_win_w, d->max_win_h, D) : 0.0L;
+    const bool fits64 = gb < 18446744073709551616.0L;
+    const bool fits128 = gb < 340282366920938463463374607431768211456.0L;
+    const bool gau_only = d->kernel_mask == SWIH_KERNEL_BIT(SWIH_KERNEL_GAUSSIAN);
     if (d->precision == SWIH_PREC_RING32 && !fits32)
         return fail(nullptr, SWIH_ERR_UNSUPPORTED,
                     "RING32 is not exact for these kernels and windows; use AUTO or RING64");
-    pl->elem_bytes = (d->precision == SWIH_PREC_RING64 || !fits32) ? 8 : 4;
+    if (d->precision == SWIH_PREC_RING64 && !fits64)
+        return fail(nullptr, SWIH_ERR_UNSUPPORTED,
+                    "RING64 is not exact for this Gaussian window (w*h*rx^2D*ry^2D >= 2^64); use AUTO or RING128");
+    const bool want128 = d->precision == SWIH_PREC_RING128 || (want_gau && !fits64);
+    if (want128) {
+        if (!want_gau || !gau_only)
+            return fail(nullptr, SWIH_ERR_UNSUPPORTED, "the 128-bit ring serves plans of the Gaussian kernel alone");
+        if (!fits128)
+            return fail(nullptr, SWIH_ERR_UNSUPPORTED,
+                        "Gaussian window too large for exact 128-bit moments (w*h*rx^2D*ry^2D >= 2^128)");
+        if (d->width > 4096)
+            return fail(nullptr, SWIH_ERR_UNSUPPORTED, "the 128-bit ring serves images up to 4096 columns");
+    }
+    pl->elem_bytes = want128 ? 16 : (d->precision == SWIH_PREC_RING64 || !fits32) ? 8 : 4;
 
     // layout
     const int W = d->width, H = d->height;
@@ -374,6 +397,9 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
     g.want_stages = pl->cfg_stages[kernel];
     g.want_bb = pl->cfg_bb[kernel];
     if (kernel == SWIH_KERNEL_GAUSSIAN) {
+        if (gauss_is_wide(pl, w, h))
+            return fail(pl, SWIH_ERR_UNSUPPORTED,
+                        "a Gaussian of degree above 2 or in the 128-bit ring takes the any-degree gather");
         GaussAxis ax, ay;
         std::string why;
         if (!gauss_axis(g.rx, pl->sigma_frac * w, pl->gauss_degree, ax, why) ||
@@ -438,6 +464,68 @@ swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams 
         }
         g.nl = std::max(g.n_load_even, g.n_load_odd);
     }
+    return SWIH_OK;
+}
+
+// the Gaussian at this window needs the any-degree gather: a fitted degree
+// above 2 on either axis, or 16-byte ring elements
+bool gauss_is_wide(const swih_plan_s *pl, int w, int h)
+{
+    return pl->elem_bytes == 16 || gauss_axis_degree((w - 1) / 2, pl->gauss_degree) > 2 ||
+           gauss_axis_degree((h - 1) / 2, pl->gauss_degree) > 2;
+}
+
+// Integer coefficients of the Bernstein moments on one axis, as ring elements:
+// A_i(d) = C(D, i) d^2i (r^2 - d^2)^(D - i) = sum_k a[i][k] d^2k with
+// a[i][k] = C(D, i) C(D - i, k - i) (-1)^(k - i) r^(2 (D - k)) for i <= k <= D
+// (zero elsewhere), reduced mod 2^128 (the low word serves the 64-bit ring).
+static void bernstein_axis(int D, int r, unsigned long long (*lo)[kWideMaxD + 1],
+                           unsigned long long (*hi)[kWideMaxD + 1])
+{
+    for (int i = 0; i <= kWideMaxD; ++i)
+        for (int k = 0; k <= kWideMaxD; ++k) lo[i][k] = hi[i][k] = 0ull;
+    for (int i = 0; i <= D; ++i)
+        for (int k = i; k <= D; ++k) {
+            unsigned __int128 v = (unsigned __int128)(unsigned long long)(binom(D, i) * binom(D - i, k - i) + 0.5);
+            for (int e = 0; e < 2 * (D - k); ++e) v *= (unsigned __int128)(unsigned)r;
+            if ((k - i) & 1) v = (unsigned __int128)0 - v;
+            lo[i][k] = (unsigned long long)v;
+            hi[i][k] = (unsigned long long)(v >> 64);
+        }
+}
+
+swih_status make_gauss_wide(swih_plan_s *pl, int w, int h, GaussWideParams &g)
+{
+    std::memset(&g, 0, sizeof g);
+    g.ih = pl->d_mem + pl->off_ih;
+    g.row_map = (pl->sparse_rows && pl->d_mem) ? reinterpret_cast<const int *>(pl->d_mem + pl->off_row_map) : nullptr;
+    g.plane = pl->plane;
+    g.pitch = pl->ih_pitch;
+    g.B = pl->desc.bins;
+    g.H = pl->desc.height;
+    g.W = pl->desc.width;
+    g.rx = (w - 1) / 2;
+    g.ry = (h - 1) / 2;
+    GaussAxis ax, ay;
+    std::string why;
+    if (!gauss_axis(g.rx, pl->sigma_frac * w, pl->gauss_degree, ax, why) ||
+        !gauss_axis(g.ry, pl->sigma_frac * h, pl->gauss_degree, ay, why))
+        return fail(pl, SWIH_ERR_UNSUPPORTED, why);
+    g.dx = ax.D;
+    g.dy = ay.D;
+    for (int a = 0; a <= 2 * g.dx; ++a)
+        for (int b = 0; b <= 2 * g.dy; ++b) {
+            g.tg[a][b] = pl->term_index[a][b];
+            if (g.tg[a][b] < 0) return fail(pl, SWIH_ERR_UNSUPPORTED, "internal: a Gaussian term is missing");
+        }
+    bernstein_axis(g.dx, g.rx, g.ax_lo, g.ax_hi);
+    bernstein_axis(g.dy, g.ry, g.ay_lo, g.ay_hi);
+    const long double sx = powl((long double)g.rx, 2 * g.dx), sy = powl((long double)g.ry, 2 * g.dy);
+    const long double mass = (long double)ax.mass * ay.mass;
+    for (int i = 0; i <= g.dx; ++i)
+        for (int j = 0; j <= g.dy; ++j) g.gamma[i][j] = (double)(ax.beta[i] * (long double)ay.beta[j] / (sx * sy * mass));
+    g.n_targets = 1;
+    g.target_stride = g.B;
     return SWIH_OK;
 }
 
@@ -738,6 +826,19 @@ swih_status swih_local_hist(swih_plan_t pl, int kernel, int win_w, int win_h, in
         if (e != cudaSuccess) return cuda_fail(pl, "exponential gather launch", e);
         return SWIH_OK;
     }
+    if (kernel == SWIH_KERNEL_GAUSSIAN && gauss_is_wide(pl, win_w, win_h)) {
+        GaussWideParams gw;
+        st = make_gauss_wide(pl, win_w, win_h, gw);
+        if (st != SWIH_OK) return st;
+        gw.cx0 = cx0;
+        gw.cy0 = cy0;
+        gw.ncx = ncx;
+        gw.ncy = ncy;
+        gw.hist = d_hist;
+        const cudaError_t e = launch_gauss_wide(gw, pl->elem_bytes, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(pl, "Gaussian gather launch", e);
+        return SWIH_OK;
+    }
     GatherParams g;
     int kind = 0;
     st = make_gather(pl, kernel, win_w, win_h, g, kind);
@@ -764,6 +865,20 @@ swih_status swih_likelihood(swih_plan_t pl, int kernel, int win_w, int win_h, co
                                              pl->desc.width - win_w + 1, pl->desc.height - win_h + 1, d_target,
                                              d_map, nullptr, static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) return cuda_fail(pl, "exponential gather launch", e);
+        return SWIH_OK;
+    }
+    if (kernel == SWIH_KERNEL_GAUSSIAN && gauss_is_wide(pl, win_w, win_h)) {
+        GaussWideParams gw;
+        st = make_gauss_wide(pl, win_w, win_h, gw);
+        if (st != SWIH_OK) return st;
+        gw.cx0 = (win_w - 1) / 2;
+        gw.cy0 = (win_h - 1) / 2;
+        gw.ncx = pl->desc.width - win_w + 1;
+        gw.ncy = pl->desc.height - win_h + 1;
+        gw.target = d_target;
+        gw.map = d_map;
+        const cudaError_t e = launch_gauss_wide(gw, pl->elem_bytes, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(pl, "Gaussian gather launch", e);
         return SWIH_OK;
     }
     GatherParams g;
@@ -806,6 +921,9 @@ swih_status swih_likelihood_scales(swih_plan_t pl, int kernel, int n_windows, co
                             kernel == SWIH_KERNEL_EUCLIDEAN || kernel == SWIH_KERNEL_GAUSSIAN;
     if (n_windows == 1 || !tiled_kind || pl->gather_path == 1 || pl->desc.height > kTiledMaxRows)
         return one_by_one();
+    if (kernel == SWIH_KERNEL_GAUSSIAN)
+        for (int i = 0; i < n_windows; ++i)
+            if (gauss_is_wide(pl, win_w[i], win_h[i])) return one_by_one();
     GatherParams jobs[SWIH_MAX_SCALES];
     int kind = 0, max_w = 3;
     for (int i = 0; i < n_windows; ++i) {

@@ -138,6 +138,23 @@ swih_status swih_likelihood_channels(swih_plan_t pl, int kernel, int win_w, int 
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(pl, "channel target table launch", e);
+    if (kernel == SWIH_KERNEL_GAUSSIAN && gauss_is_wide(pl, win_w, win_h)) {
+        GaussWideParams gw;
+        st = make_gauss_wide(pl, win_w, win_h, gw);
+        if (st != SWIH_OK) return st;
+        gw.cx0 = (win_w - 1) / 2;
+        gw.cy0 = (win_h - 1) / 2;
+        gw.ncx = pl->desc.width - win_w + 1;
+        gw.ncy = pl->desc.height - win_h + 1;
+        gw.target = table;
+        gw.target_stride = B;
+        gw.n_targets = C;
+        gw.map = d_maps;
+        gw.map_stride = (int64_t)gw.ncx * gw.ncy;
+        e = launch_gauss_wide(gw, pl->elem_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(pl, "Gaussian gather launch", e);
+        return SWIH_OK;
+    }
     GatherParams g;
     int kind = 0;
     st = make_gather(pl, kernel, win_w, win_h, g, kind);

@@ -14,9 +14,9 @@ struct swih_plan_s {
     swih_plan_desc desc;
     int elem_bytes = 4;
     int n_terms = 0;
-    int term_p[swih::kMaxTerms];
-    int term_q[swih::kMaxTerms];
-    int term_index[5][5];  // [p][q] -> term or -1
+    int term_p[swih::kMaxPlanTerms];
+    int term_q[swih::kMaxPlanTerms];
+    int term_index[swih::kMaxP][swih::kMaxQ];  // [p][q] -> term or -1
     // scan chains: distinct q values and their p lists
     int n_q = 0;
     int q_val[swih::kMaxQ];
@@ -77,6 +77,10 @@ long double int_kernel_mass(int kernel, int w, int h);
 swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl);
 // gather parameters of one kernel and window over the plan's integral histograms
 swih_status make_gather(swih_plan_s *pl, int kernel, int w, int h, GatherParams &g, int &kind);
+// the Gaussian at a w x h window takes the any-degree gather (degree above 2
+// or the 128-bit ring), and its parameters
+bool gauss_is_wide(const swih_plan_s *pl, int w, int h);
+swih_status make_gauss_wide(swih_plan_s *pl, int w, int h, GaussWideParams &g);
 // allocate a laid-out plan's workspace on the current device and hand it out
 // (the plan is deleted on failure)
 swih_status allocate_plan(swih_plan_s *pl, swih_plan_t *out);

@@ -6,9 +6,10 @@
 
 namespace swih {
 
-constexpr int kMaxQ = 5;          // distinct y-exponents q (Gaussian D=2: 0..4)
-constexpr int kMaxP = 5;          // x-exponents p per q
-constexpr int kMaxTerms = 25;
+constexpr int kMaxQ = 9;          // distinct y-exponents q of a plan (Gaussian of degree D: 0..2D, D <= 4)
+constexpr int kMaxP = 9;          // x-exponents p per q
+constexpr int kMaxTerms = 25;     // terms a tiled or table gather reads (Gaussian D <= 2)
+constexpr int kMaxPlanTerms = 81; // terms of a plan (Gaussian D = 4: x^p y^q, p, q <= 8)
 constexpr int kMaxScanThreads = 512;
 
 // decoupled look-back tile states
@@ -86,9 +87,12 @@ struct ScanParams {
 // row is all zero), from the occupancy words of a sparse-row scan
 cudaError_t launch_row_map(const unsigned long long *occ, int *row_map, int B, int H, int band_rows, int n_bands,
                            cudaStream_t s);
-// E = columns per thread, threads = ceil(W/E) rounded to a warp multiple
+// E = columns per thread, threads = ceil(W/E) rounded to a warp multiple;
+// elem_bytes 4, 8 or 16 (the 128-bit ring: E <= 8)
 cudaError_t launch_ih_scan(const ScanParams &p, int elem_bytes, int E, int threads,
                            cudaStream_t s);
+// the same for chains of more than 5 x-exponents or 16-byte elements (one plan)
+cudaError_t launch_ih_scan_wide(const ScanParams &p, int elem_bytes, int E, int threads, cudaStream_t s);
 
 // The per-region fields of a scan (one entry per image region of a batch).
 struct ScanRoi {
@@ -207,6 +211,34 @@ struct GatherParams {
 };
 cudaError_t launch_gather(const GatherParams &p, int kind, int elem_bytes, cudaStream_t s);
 
+// Gaussian approximant of any fitted degree (1..4 per axis) in the 64- or
+// 128-bit ring: one thread per centre, corner reads from global memory (the
+// term planes of degrees above 2 do not fit the tiled gather's shared memory).
+// Per bin: the exact window count (x^0 y^0 plane) gates the bin; the window's
+// raw moments sum x^a y^b are translated to the centre (a Taylor shift in x per
+// y-power, binomial sums in y), combined into the Bernstein moments
+// F_ij = sum A_i(dx) B_j(dy), A_i(d) = sum_k ax[i][k] d^2k, exact in the ring,
+// and U = sum_ij gamma_ij F_ij in double from the non-negative F_ij.
+constexpr int kWideMaxD = 4;
+struct GaussWideParams {
+    const void *ih;
+    const int *row_map;          // [b][H] (-1: zero row), or NULL
+    int64_t plane, pitch;        // elements
+    int B, H, W, rx, ry;
+    int cx0, cy0, ncx, ncy;
+    int dx, dy;                  // fitted degree per axis
+    int tg[2 * kWideMaxD + 1][2 * kWideMaxD + 1];  // term index of x^a y^b
+    unsigned long long ax_lo[kWideMaxD + 1][kWideMaxD + 1], ax_hi[kWideMaxD + 1][kWideMaxD + 1];
+    unsigned long long ay_lo[kWideMaxD + 1][kWideMaxD + 1], ay_hi[kWideMaxD + 1][kWideMaxD + 1];
+    double gamma[kWideMaxD + 1][kWideMaxD + 1];  // beta_x[i] beta_y[j] / (rx^2dx ry^2dy M)
+    const float *target;         // [n_targets][target_stride] or NULL
+    float *map;                  // n_targets maps [ncy][ncx], map_stride apart, or NULL
+    float *hist;                 // [ncy][ncx][B] or NULL
+    int n_targets;
+    int64_t target_stride, map_stride;
+};
+cudaError_t launch_gauss_wide(const GaussWideParams &p, int elem_bytes, cudaStream_t s);
+
 // kernels this library has enqueued in the process (host count, for reporting)
 void count_launches(unsigned n);
 
@@ -250,7 +282,7 @@ cudaError_t launch_gather_table(const GatherParams *d_jobs, const int *d_item_st
 // allocating anything.
 struct PlanLayout {
     int elem_bytes, n_terms;
-    int term_p[kMaxTerms], term_q[kMaxTerms];
+    int term_p[kMaxPlanTerms], term_q[kMaxPlanTerms];
     int n_q;
     int q_val[kMaxQ], p_count[kMaxQ], p_val[kMaxQ][kMaxP], term[kMaxQ][kMaxP];
     int64_t bins_pitch, ih_pitch, plane;

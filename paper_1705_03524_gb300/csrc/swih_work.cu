@@ -108,6 +108,10 @@ swih_status WorkSet::plan(const WorkSpec &spec, const std::vector<WorkRegion> &r
     tmpl_ = swih_plan_s();
     const swih_status st = build_layout(&pd, &tmpl_);
     if (st != SWIH_OK) return bad(st, thread_error());
+    if (tmpl_.elem_bytes > 8 || (tmpl_.desc.kernel_mask & SWIH_KERNEL_BIT(SWIH_KERNEL_GAUSSIAN) &&
+                                 (gauss_is_wide(&tmpl_, pd.max_win_w, pd.max_win_h))))
+        return bad(SWIH_ERR_UNSUPPORTED, "batches, the server and streamed frames serve the Gaussian up to degree 2 "
+                                         "in the 64-bit ring (use a plan for larger windows or degrees)");
     scan_E_ = tmpl_.scan_E;
     scan_threads_ = tmpl_.scan_threads;
     band_rows_ = spec.band_rows > 0 ? spec.band_rows : 32;

@@ -39,6 +39,7 @@ SWIH_KERNEL_EXPONENTIAL = 5
 SWIH_PREC_AUTO = 0
 SWIH_PREC_RING32 = 1
 SWIH_PREC_RING64 = 2
+SWIH_PREC_RING128 = 3
 
 KERNELS = {"plain": SWIH_KERNEL_PLAIN, "manhattan": SWIH_KERNEL_MANHATTAN,
            "euclidean": SWIH_KERNEL_EUCLIDEAN, "gaussian": SWIH_KERNEL_GAUSSIAN,
@@ -83,8 +84,8 @@ class swih_plan_info(ctypes.Structure):
         ("bins", ctypes.c_int32),
         ("elem_bytes", ctypes.c_int32),
         ("n_terms", ctypes.c_int32),
-        ("term_p", ctypes.c_int32 * 32),
-        ("term_q", ctypes.c_int32 * 32),
+        ("term_p", ctypes.c_int32 * 96),
+        ("term_q", ctypes.c_int32 * 96),
         ("d_bins", ctypes.c_void_p),
         ("bins_pitch", ctypes.c_int64),
         ("d_ih", ctypes.c_void_p),

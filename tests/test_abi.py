@@ -74,9 +74,12 @@ def _desc(**kw):
     (dict(kernels=()), S.SWIH_ERR_INVALID_ARG),
     (dict(pitch_bytes=100), S.SWIH_ERR_INVALID_ARG),
     (dict(bitdepth=9), S.SWIH_ERR_INVALID_ARG),
-    (dict(gauss_degree=3, kernels=("gaussian",)), S.SWIH_ERR_UNSUPPORTED),
+    (dict(gauss_degree=5, kernels=("gaussian",)), S.SWIH_ERR_UNSUPPORTED),
     (dict(precision=S.SWIH_PREC_RING32, kernels=("gaussian",)), S.SWIH_ERR_UNSUPPORTED),
-    (dict(height=1024, width=1024, kernels=("gaussian",), max_win=(255, 255)), S.SWIH_ERR_UNSUPPORTED),
+    (dict(height=1024, width=1024, kernels=("gaussian",), max_win=(255, 255), precision=S.SWIH_PREC_RING64),
+     S.SWIH_ERR_UNSUPPORTED),
+    (dict(height=1024, width=1024, kernels=("gaussian",), max_win=(301, 301), gauss_degree=4),
+     S.SWIH_ERR_UNSUPPORTED),
     (dict(hbm_budget_bytes=1000), S.SWIH_ERR_BUDGET),
     (dict(kernels=("exponential",), exp_lambda=20.0), S.SWIH_ERR_INVALID_ARG),
     (dict(kernels=("exponential",), exp_lambda=1e-4), S.SWIH_ERR_INVALID_ARG),
@@ -258,3 +261,32 @@ def test_channel_plan_refusals_on_the_host():
         with pytest.raises(S.SwihError) as ei:
             S.ChannelPlan(desc, chans)
         assert ei.value.status == S.SWIH_ERR_INVALID_ARG
+
+
+def test_gaussian_ring_choice_and_refusals():
+    # the ring follows the largest Bernstein moment w h rx^2D ry^2D
+    def ws(**kw):
+        return S.swih_plan_workspace_bytes(_desc(kernels=("gaussian",), **kw))
+    small = ws(width=1024, height=1024, max_win=(81, 81))                       # D = 2: 64-bit ring
+    big = ws(width=1024, height=1024, max_win=(401, 401))                      # D = 2: 128-bit ring
+    assert big > 1.9 * small
+    ws(width=1024, height=1024, max_win=(401, 401), gauss_degree=3)            # 49 terms, 128-bit
+    for kw, status in ((dict(max_win=(301, 301), gauss_degree=4, width=1024, height=1024), S.SWIH_ERR_UNSUPPORTED),
+                       (dict(max_win=(401, 401), width=5000, height=600), S.SWIH_ERR_UNSUPPORTED),
+                       (dict(gauss_degree=5), S.SWIH_ERR_UNSUPPORTED),
+                       (dict(max_win=(201, 201), width=1024, height=1024, precision=S.SWIH_PREC_RING64),
+                        S.SWIH_ERR_UNSUPPORTED)):
+        with pytest.raises(S.SwihError) as ei:
+            ws(**kw)
+        assert ei.value.status == status, kw
+    # the 128-bit ring serves plans of the Gaussian kernel alone
+    with pytest.raises(S.SwihError) as ei:
+        S.swih_plan_workspace_bytes(_desc(width=1024, height=1024, kernels=("gaussian", "manhattan"),
+                                          max_win=(401, 401)))
+    assert ei.value.status == S.SWIH_ERR_UNSUPPORTED
+    # batches stay within degree 2 and the 64-bit ring
+    with pytest.raises(S.SwihError) as ei:
+        desc = S.make_batch_desc(1024, 1024, bins=16, kernels=("gaussian",), gauss_degree=3)
+        roi = S.make_roi(0, 0, 300, 300, "gaussian", [(41, 41)], 256, [256])
+        S.swih_batch_workspace_bytes(desc, [roi])
+    assert ei.value.status == S.SWIH_ERR_UNSUPPORTED

@@ -100,8 +100,8 @@ def test_plain_ih_matches_counts():
         assert np.array_equal(O.weighted_ih(bins, b, 0, 0, 64).astype(np.int64), ih[b])
 
 
-@pytest.mark.parametrize("bits", [32, 64])
-@pytest.mark.parametrize("p,q", [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (4, 4), (3, 2)])
+@pytest.mark.parametrize("bits", [32, 64, 128])
+@pytest.mark.parametrize("p,q", [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (4, 4), (3, 2), (8, 8), (7, 6)])
 def test_weighted_ih_exact_in_ring(bits, p, q):
     rng = np.random.default_rng(11 + p + 7 * q)
     bins = rng.integers(0, 3, size=(6, 8)).astype(np.uint8)
@@ -112,6 +112,22 @@ def test_weighted_ih_exact_in_ring(bits, p, q):
         for y in range(6):
             for x in range(8):
                 assert int(got[y, x]) == ref[y][x] % mod
+
+
+def test_weighted_ih_128_wraps_exactly_on_large_coordinates():
+    # x^8 y^8 prefix sums pass 2^128 at these coordinates; the oracle keeps
+    # them mod 2^128, and its 64-bit ring is the same values mod 2^64
+    rng = np.random.default_rng(13)
+    H, W = 40, 3000
+    bins = rng.integers(0, 2, size=(H, W)).astype(np.uint8)
+    got = O.weighted_ih(bins, 1, 8, 8, 128)
+    ys, xs = np.nonzero(bins == 1)
+    exact = sum(int(a) ** 8 * int(c) ** 8 for a, c in zip(xs, ys))
+    assert exact >= 1 << 128
+    assert int(got[H - 1, W - 1]) == exact % (1 << 128)
+    got64 = O.weighted_ih(bins, 1, 3, 2, 64)
+    got128 = O.weighted_ih(bins, 1, 3, 2, 128)
+    assert all(int(got128[y, x]) % (1 << 64) == int(got64[y, x]) for y in (0, 11, 39) for x in (0, 100, 2999))
 
 
 def test_weighted_ih_wraps_exactly_on_large_coordinates():
