@@ -1018,6 +1018,33 @@ def run_exp_profile():
     print(json.dumps({"exp_profile": "ok", "bins": B}), flush=True)
 
 
+def run_wide_profile(degree=3, w=151):
+    """A small run of the any-degree Gaussian gather to capture under ncu: the
+    benchmark frame with B = 8, a degree-3 plan at a 151 px window (128-bit
+    ring), two builds and two maps."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    img = synth.config2()["image"]
+    H, W = img.shape
+    B = 8
+    d_img = torch.from_numpy(img).to(dev)
+    q = torch.full((B,), 1.0 / B, device=dev)
+    m = torch.empty((H - w + 1, W - w + 1), device=dev)
+    desc = S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(w, w), gauss_degree=degree)
+    with S.Plan(desc) as p:
+        for _ in range(2):
+            p.build_ih(d_img)
+            p.likelihood("gaussian", w, w, q, m)
+        p.sync_status()
+        elem = p.info().elem_bytes
+    print(json.dumps({"wide_profile": "ok", "bins": B, "degree": degree, "window": w, "ring_bits": 8 * elem}),
+          flush=True)
+
+
 # ----------------------------------------------------------------------------- serving
 def run_serving(args, dev, n_queries=400, rate=2000.0):
     """A Poisson stream of tracking queries against 16 resident 2048x2048
@@ -1438,6 +1465,8 @@ def main():
                     help="time per map against window size (SWIH on the GPU vs the brute-force oracle)")
     ap.add_argument("--exp-profile", action="store_true",
                     help="small exponential-kernel run for ncu captures: B = 8, two builds and two w = 41 maps")
+    ap.add_argument("--wide-profile", action="store_true",
+                    help="small any-degree Gaussian run for ncu captures: B = 8, degree 3, 151 px window")
     ap.add_argument("--regions-only", action="store_true",
                     help="only the batched search-regions measurement (for launch lists of the batch)")
     args = ap.parse_args()
@@ -1452,6 +1481,9 @@ def main():
         return
     if args.exp_profile:
         run_exp_profile()
+        return
+    if args.wide_profile:
+        run_wide_profile()
         return
     if args.regions_only:
         import torch

@@ -181,9 +181,13 @@ swih_status swih_likelihood(swih_plan_t plan, int kernel, int win_w, int win_h,
  * d_targets[i] (float32 [B]) into d_maps[i] (float32 [H-win_h[i]+1][W-win_w[i]+1]).
  * win_w, win_h, d_targets and d_maps are host arrays (of device pointers for
  * the last two). The windows of the tiled kernels run as one launch over a job
- * table in the plan (the launch's last wave is a small part of it), which is
- * uploaded with cudaMemcpyAsync on the stream from host memory, so this call
- * cannot be captured into a CUDA graph; the wedding cake, the exponential
+ * table in the plan (the launch's last wave is a small part of it). The plan
+ * keeps the last 8 distinct tables in slots: a call whose table (kernel,
+ * windows, targets and maps) equals a slot's enqueues no copy; otherwise the
+ * least recently used slot is uploaded with cudaMemcpyAsync on the stream from
+ * host memory. So a call can be captured into a CUDA graph once the same call
+ * has run uncaptured, and the graph stays valid while the plan's later
+ * multi-window calls use at most 7 other distinct tables. The wedding cake, the exponential
  * kernel and Gaussian windows of different fitted degrees run one launch per
  * window. Results equal those of n_windows calls of swih_likelihood up to
  * float rounding (a single-window call may split its bins over CTA groups and
@@ -456,8 +460,11 @@ swih_status swih_debug_inject(swih_plan_t plan, int what);
  * its rows plus a halo of (tallest window - 1) rows, are built, gathered for
  * every job's centres in the band and then overwritten by the next band's.
  * Results equal those of one plan over the whole frame (integer integral
- * histograms are exact at any origin). The pass over all bands is captured
- * into a CUDA graph at the first run. */
+ * histograms are exact at any origin). Frames wider than 8192 columns are
+ * also cut into column tiles of at most 8192 columns (a halo of the widest
+ * window - 1 columns); each piece's maps are computed into a scratch area of
+ * the workspace and copied into the frame-sized maps. The pass over all
+ * pieces is captured into a CUDA graph at the first run. */
 typedef struct swih_frame_job {
     int32_t kernel;             /* swih_kernel, in the desc's kernel_mask */
     int32_t win_w, win_h;       /* odd, >= 3 */

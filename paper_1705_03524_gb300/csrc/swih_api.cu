@@ -19,6 +19,10 @@ namespace swih {
 
 thread_local std::string g_err;
 
+// bytes of one job-table slot of swih_likelihood_scales (256-byte multiple)
+constexpr uint64_t kJobSlotBytes =
+    (sizeof(GatherParams) * SWIH_MAX_SCALES + sizeof(int) * (SWIH_MAX_SCALES + 1) + 255) / 256 * 256;
+
 std::string &thread_error() { return g_err; }
 
 swih_status fail(swih_plan_s *plan, swih_status st, const std::string &msg)
@@ -313,7 +317,7 @@ swih_status build_layout(const swih_plan_desc *d, swih_plan_s *pl)
         pl->off_exp_carry = take((uint64_t)2 * d->bins * pl->n_bands * pl->ih_pitch * sizeof(unsigned long long));
         pl->off_exp_rows = take((uint64_t)2 * d->bins * pl->n_bands * sizeof(unsigned long long));
     }
-    pl->off_jobs = take(sizeof(GatherParams) * SWIH_MAX_SCALES + sizeof(int) * (SWIH_MAX_SCALES + 1));
+    pl->off_jobs = take((uint64_t)swih_plan_s::kJobSlots * kJobSlotBytes);
     take(sizeof(uint32_t) * 64);  // status word
     pl->total = off;
     if (d->hbm_budget_bytes && pl->total > d->hbm_budget_bytes) {
@@ -955,13 +959,30 @@ swih_status swih_likelihood_scales(swih_plan_t pl, int kernel, int n_windows, co
         if (total > 0x7fffffffLL) return one_by_one();
     }
     start[n_windows] = (int)total;
-    // job table, then the item starts, uploaded on the stream (stream-ordered)
-    unsigned char host[sizeof(GatherParams) * SWIH_MAX_SCALES + sizeof(int) * (SWIH_MAX_SCALES + 1)];
-    std::memcpy(host, jobs, sizeof(GatherParams) * n_windows);
-    std::memcpy(host + sizeof(GatherParams) * SWIH_MAX_SCALES, start, sizeof(int) * (n_windows + 1));
-    char *d_tab = pl->d_mem + pl->off_jobs;
-    cudaError_t e = cudaMemcpyAsync(d_tab, host, sizeof host, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(pl, "cudaMemcpyAsync(job table)", e);
+    // job table, then the item starts: a slot already holding this table is
+    // reused as it is; otherwise the least recently used slot is uploaded on
+    // the stream (stream-ordered)
+    std::vector<unsigned char> host(kJobSlotBytes, 0);
+    std::memcpy(host.data(), jobs, sizeof(GatherParams) * n_windows);
+    std::memcpy(host.data() + sizeof(GatherParams) * SWIH_MAX_SCALES, start, sizeof(int) * (n_windows + 1));
+    int slot = -1, lru = 0;
+    for (int k = 0; k < swih_plan_s::kJobSlots; ++k) {
+        if (pl->job_slot[k] == host) slot = k;
+        if (pl->job_slot_use[k] < pl->job_slot_use[lru]) lru = k;
+    }
+    const bool upload = slot < 0;
+    if (upload) slot = lru;
+    pl->job_slot_use[slot] = ++pl->job_clock;
+    char *d_tab = pl->d_mem + pl->off_jobs + (uint64_t)slot * kJobSlotBytes;
+    cudaError_t e = cudaSuccess;
+    if (upload) {
+        pl->job_slot[slot] = host;
+        e = cudaMemcpyAsync(d_tab, pl->job_slot[slot].data(), kJobSlotBytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            pl->job_slot[slot].clear();
+            return cuda_fail(pl, "cudaMemcpyAsync(job table)", e);
+        }
+    }
     e = launch_gather_table(reinterpret_cast<const GatherParams *>(d_tab),
                             reinterpret_cast<const int *>(d_tab + sizeof(GatherParams) * SWIH_MAX_SCALES), n_windows,
                             (int)total, jobs[0], kind, pl->elem_bytes, jobs[0].gdx, jobs[0].gdy, sh, s);

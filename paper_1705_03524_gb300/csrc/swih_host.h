@@ -35,7 +35,14 @@ struct swih_plan_s {
     // (bin, row)'s last stored row
     bool sparse_rows = false;
     uint64_t off_occ = 0, off_row_map = 0;
-    uint64_t off_jobs = 0;  // job table of swih_likelihood_scales (SWIH_MAX_SCALES jobs + item starts)
+    uint64_t off_jobs = 0;  // job tables of swih_likelihood_scales: kJobSlots slots of
+                            // SWIH_MAX_SCALES jobs + item starts
+    // host copies of the slots' contents and their last use: a call whose table
+    // equals a slot's reuses it without an upload
+    static constexpr int kJobSlots = 8;
+    std::vector<unsigned char> job_slot[kJobSlots];
+    uint64_t job_slot_use[kJobSlots] = {};
+    uint64_t job_clock = 0;
     // exponential kernel: decay per pixel, fixed-point fraction bits, the four
     // directional integral histograms and the scan's band carries
     bool has_exp = false;

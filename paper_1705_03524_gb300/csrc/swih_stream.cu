@@ -19,12 +19,28 @@
 
 using namespace swih;
 
+// a map piece computed into scratch and copied into the frame-sized map
+struct MapCopy {
+    float *dst;
+    int64_t dpitch;  // bytes
+    const float *src;
+    int64_t spitch;  // bytes
+    int64_t width;   // bytes
+    int height;
+};
+
 struct swih_stream_s {
     swih_plan_desc desc;
     std::vector<swih_frame_job> jobs;
     const void *image = nullptr;
     int band_h = 0, n_bands = 0, R = 0;
-    std::vector<std::unique_ptr<WorkSet>> bands;
+    // column tiles (frames wider than one region): tile t owns the centre
+    // columns [Rx + t Tw, Rx + (t+1) Tw) (the first from 0, the last to W)
+    int Rx = 0, tile_w = 0, n_tiles = 1;
+    std::vector<std::unique_ptr<WorkSet>> bands;  // (band, tile) pieces, band-major
+    std::vector<std::vector<MapCopy>> copies;     // per piece: maps placed after its gathers
+    std::vector<uint64_t> scratch_off;            // per job: its map piece in the scratch
+    uint64_t scratch_bytes = 0;
     char *d_mem = nullptr;
     uint64_t bytes = 0;
     char *h_tables = nullptr;  // pinned copies of every band's tables
@@ -56,41 +72,68 @@ WorkSpec spec_of(const swih_plan_desc &d)
     return sp;
 }
 
-// Lay out band k of a pass with band height Hb (host only).
-swih_status plan_band(const swih_stream_s &S, int Hb, int n_bands, int k, WorkSet &ws, std::string &err)
+constexpr int kMaxRegionW = 8192;  // the widest region one work set holds
+
+// Lay out the piece (band k, column tile t) of a pass with band height Hb
+// (host only). With one tile the jobs write straight into the frame maps;
+// with several, each job writes its piece into the scratch (at scratch + the
+// job's offset; scratch NULL: layout only) and `copies` receives the copies
+// into the frame maps.
+swih_status plan_band(const swih_stream_s &S, int Hb, int n_bands, int k, int t, WorkSet &ws, std::string &err,
+                      const char *scratch = nullptr, std::vector<MapCopy> *copies = nullptr,
+                      std::vector<uint64_t> *piece_floats = nullptr)
 {
-    const int H = S.desc.height, W = S.desc.width, R = S.R;
+    const int H = S.desc.height, W = S.desc.width, R = S.R, Rx = S.Rx, Tw = S.tile_w, nt = S.n_tiles;
     const int y0 = k * Hb;
     const int y1 = k == n_bands - 1 ? H : std::min(H, (k + 1) * Hb + 2 * R);
     const int lo = k == 0 ? 0 : R + k * Hb;
     const int hi = k == n_bands - 1 ? H : R + (k + 1) * Hb;
+    const int x0 = t * Tw;
+    const int x1 = t == nt - 1 ? W : std::min(W, (t + 1) * Tw + 2 * Rx);
+    const int lox = t == 0 ? 0 : Rx + t * Tw;
+    const int hix = t == nt - 1 ? W : Rx + (t + 1) * Tw;
+    const int pb = S.desc.pixel_type == SWIH_PIXEL_U16 ? 2 : 1;
     WorkRegion reg;
-    reg.image = static_cast<const uint8_t *>(S.image) + (int64_t)y0 * S.desc.pitch_bytes;
+    reg.image = static_cast<const uint8_t *>(S.image) + (int64_t)y0 * S.desc.pitch_bytes + (int64_t)x0 * pb;
     reg.pitch = S.desc.pitch_bytes;
     reg.H = y1 - y0;
-    reg.W = W;
+    reg.W = x1 - x0;
     std::vector<WorkJob> jobs;
-    for (const swih_frame_job &fj : S.jobs) {
+    if (piece_floats) piece_floats->assign(S.jobs.size(), 0);
+    for (size_t j = 0; j < S.jobs.size(); ++j) {
+        const swih_frame_job &fj = S.jobs[j];
         const int rx = (fj.win_w - 1) / 2, ry = (fj.win_h - 1) / 2;
         const int c_lo = std::max(lo, ry), c_hi = std::min(hi, H - ry);
-        if (c_hi <= c_lo) continue;
+        const int cx_lo = std::max(lox, rx), cx_hi = std::min(hix, W - rx);
+        if (c_hi <= c_lo || cx_hi <= cx_lo) continue;
         WorkJob jb;
         jb.region = 0;
         jb.kernel = fj.kernel;
         jb.w = fj.win_w;
         jb.h = fj.win_h;
-        jb.cx0 = rx;
-        jb.ncx = W - fj.win_w + 1;
+        jb.cx0 = cx_lo - x0;
+        jb.ncx = cx_hi - cx_lo;
         jb.cy0 = c_lo - y0;
         jb.ncy = c_hi - c_lo;
         jb.target = fj.d_target;
-        jb.map = fj.d_map + (int64_t)(c_lo - ry) * jb.ncx;
+        const int64_t frame_nx = W - fj.win_w + 1;
+        float *dst = fj.d_map + (int64_t)(c_lo - ry) * frame_nx + (cx_lo - rx);
+        if (nt == 1) {
+            jb.map = dst;
+        } else {
+            jb.map = scratch ? reinterpret_cast<float *>(const_cast<char *>(scratch) + S.scratch_off[j])
+                             : reinterpret_cast<float *>(256);  // layout only
+            if (copies)
+                copies->push_back(MapCopy{dst, frame_nx * 4, jb.map, (int64_t)jb.ncx * 4, (int64_t)jb.ncx * 4,
+                                          jb.ncy});
+            if (piece_floats) (*piece_floats)[j] = (uint64_t)jb.ncx * jb.ncy;
+        }
         jobs.push_back(jb);
     }
     return ws.plan(spec_of(S.desc), {reg}, jobs, err);
 }
 
-// Every band for band height Hb; bytes = the largest band's memory.
+// Every piece for band height Hb; bytes = the largest piece's memory.
 swih_status plan_bands(swih_stream_s &S, int Hb, std::vector<std::unique_ptr<WorkSet>> &out, uint64_t &bytes,
                        std::string &err)
 {
@@ -98,14 +141,27 @@ swih_status plan_bands(swih_stream_s &S, int Hb, std::vector<std::unique_ptr<Wor
     const int n = std::max(1, (rows + Hb - 1) / Hb);
     out.clear();
     bytes = 0;
-    for (int k = 0; k < n; ++k) {
-        std::unique_ptr<WorkSet> ws(new WorkSet());
-        const swih_status st = plan_band(S, Hb, n, k, *ws, err);
-        if (st != SWIH_OK) return st;
-        bytes = std::max(bytes, ws->bytes());
-        out.push_back(std::move(ws));
-    }
+    for (int k = 0; k < n; ++k)
+        for (int t = 0; t < S.n_tiles; ++t) {
+            std::unique_ptr<WorkSet> ws(new WorkSet());
+            const swih_status st = plan_band(S, Hb, n, k, t, *ws, err);
+            if (st != SWIH_OK) return st;
+            bytes = std::max(bytes, ws->bytes());
+            out.push_back(std::move(ws));
+        }
     return SWIH_OK;
+}
+
+// the map pieces of piece k into the frame maps (several column tiles only)
+cudaError_t enqueue_copies(const swih_stream_s &S, size_t k, cudaStream_t s)
+{
+    if (k >= S.copies.size()) return cudaSuccess;
+    for (const MapCopy &c : S.copies[k]) {
+        const cudaError_t e = cudaMemcpy2DAsync(c.dst, (size_t)c.dpitch, c.src, (size_t)c.spitch, (size_t)c.width,
+                                                (size_t)c.height, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 swih_status capture(swih_stream_s *S)
@@ -118,6 +174,7 @@ swih_status capture(swih_stream_s *S)
         le = cudaMemcpyAsync(ws.tables_device(), S->h_tables + S->tab_off[k], ws.tables_bytes(),
                              cudaMemcpyHostToDevice, S->cap);
         if (le == cudaSuccess) le = ws.enqueue(S->cap, false);
+        if (le == cudaSuccess) le = enqueue_copies(*S, k, S->cap);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(S->cap, &g);
@@ -151,15 +208,26 @@ swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *j
     S->desc = *desc;
     S->jobs.assign(jobs, jobs + n_jobs);
     S->image = d_image;
-    int hmax = 3;
+    int hmax = 3, wmax = 3;
     for (int j = 0; j < n_jobs; ++j) {
         const swih_frame_job &fj = jobs[j];
         if (!odd_window(fj.win_w) || !odd_window(fj.win_h) || fj.win_w > desc->width || fj.win_h > desc->height)
             return tfail(SWIH_ERR_INVALID_ARG, "job " + std::to_string(j) + ": window must be odd, >= 3, inside the frame");
         if (!fj.d_target || !fj.d_map) return tfail(SWIH_ERR_INVALID_ARG, "job " + std::to_string(j) + ": NULL target or map");
         hmax = std::max(hmax, fj.win_h);
+        wmax = std::max(wmax, fj.win_w);
     }
     S->R = (hmax - 1) / 2;
+    S->Rx = (wmax - 1) / 2;
+    if (desc->width <= kMaxRegionW) {
+        S->n_tiles = 1;
+        S->tile_w = std::max(1, desc->width - 2 * S->Rx);
+    } else {
+        // column tiles of at most kMaxRegionW columns, halo 2 Rx
+        S->tile_w = kMaxRegionW - 2 * S->Rx;
+        if (S->tile_w < 256) return tfail(SWIH_ERR_UNSUPPORTED, "windows too wide for column tiles");
+        S->n_tiles = (desc->width - 2 * S->Rx + S->tile_w - 1) / S->tile_w;
+    }
     const int rows = desc->height - 2 * S->R;
     std::string err;
     uint64_t bytes = 0;
@@ -171,10 +239,10 @@ swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *j
             const int mid = lo + (hi - lo) / 2;
             std::unique_ptr<WorkSet> ws(new WorkSet());
             const int n = std::max(1, (rows + mid - 1) / mid);
-            swih_status st = plan_band(*S, mid, n, n > 1 ? 1 : 0, *ws, err);
+            swih_status st = plan_band(*S, mid, n, n > 1 ? 1 : 0, 0, *ws, err);
             if (st == SWIH_OK && n > 1) {  // the first band can be the tallest region too
                 std::unique_ptr<WorkSet> w0(new WorkSet());
-                st = plan_band(*S, mid, n, 0, *w0, err);
+                st = plan_band(*S, mid, n, 0, 0, *w0, err);
                 if (st == SWIH_OK && w0->bytes() > ws->bytes()) ws = std::move(w0);
             }
             if (st != SWIH_OK) return tfail(st, err);
@@ -196,12 +264,47 @@ swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *j
         Hb = std::max(1, Hb - std::max(1, Hb / 16));  // a last band taller than the probe: shrink
     }
     S->band_h = Hb;
-    S->n_bands = (int)S->bands.size();
-    S->bytes = bytes;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->d_mem), bytes);
+    const int n_bands = (int)S->bands.size() / S->n_tiles;
+    S->n_bands = n_bands;
+    // column tiles: each job's largest piece in a scratch after the work memory
+    S->scratch_off.assign(S->jobs.size(), 0);
+    if (S->n_tiles > 1) {
+        std::vector<uint64_t> most(S->jobs.size(), 0), piece;
+        for (int k = 0; k < n_bands; ++k)
+            for (int t = 0; t < S->n_tiles; ++t) {
+                WorkSet probe;
+                const swih_status st = plan_band(*S, Hb, n_bands, k, t, probe, err, nullptr, nullptr, &piece);
+                if (st != SWIH_OK) return tfail(st, err);
+                for (size_t j = 0; j < piece.size(); ++j) most[j] = std::max(most[j], piece[j]);
+            }
+        uint64_t off = (bytes + 255) / 256 * 256;
+        for (size_t j = 0; j < most.size(); ++j) {
+            S->scratch_off[j] = off;
+            off += (most[j] * sizeof(float) + 255) / 256 * 256;
+        }
+        S->scratch_bytes = off - bytes;
+        if (desc->hbm_budget_bytes && off > desc->hbm_budget_bytes)
+            return tfail(SWIH_ERR_BUDGET, "the maps' tile pieces do not fit hbm_budget_bytes with this band height");
+    }
+    S->bytes = bytes + S->scratch_bytes;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->d_mem), S->bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(nullptr, "cudaMalloc(stream workspace)", e);
+    }
+    if (S->n_tiles > 1) {
+        // the pieces again, now writing their maps into the scratch, with the copies
+        S->copies.assign(S->bands.size(), {});
+        for (int k = 0; k < n_bands; ++k)
+            for (int t = 0; t < S->n_tiles; ++t) {
+                const size_t i = (size_t)k * S->n_tiles + t;
+                S->bands[i].reset(new WorkSet());
+                const swih_status st = plan_band(*S, Hb, n_bands, k, t, *S->bands[i], err, S->d_mem, &S->copies[i]);
+                if (st != SWIH_OK) {
+                    cudaFree(S->d_mem);
+                    return tfail(st, err);
+                }
+            }
     }
     uint64_t tab_total = 0;
     for (auto &ws : S->bands) {
@@ -260,6 +363,7 @@ swih_status swih_stream_run_timed(swih_stream_t S, void *stream, float *stage_ms
             e = cudaMemcpyAsync(ws.tables_device(), S->h_tables + S->tab_off[k], ws.tables_bytes(),
                                 cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = ws.enqueue(s, false, ev[k].data() + 1);
+        if (e == cudaSuccess) e = enqueue_copies(*S, k, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     for (size_t k = 0; k < S->bands.size() && e == cudaSuccess; ++k) {

@@ -547,3 +547,32 @@ def test_every_gather_shape_gives_the_same_maps():
                         err = np.abs(single.cpu().numpy().astype(np.float64) - refs[kind, *windows[0]][1]).max()
                         assert err <= TOL, (kind, tile_cols, stages, bps, "single", err)
             S.swih_set_gather_config(plan.handle, k, 0, 0, 0)
+
+
+def test_multi_window_call_is_captured_after_a_first_run():
+    """swih_likelihood_scales reuses a job-table slot when its arguments repeat,
+    enqueuing no copy: after one uncaptured call the same call is captured into
+    a CUDA graph, and replays write the maps of the uncaptured call."""
+    H, W, B = 300, 400, 16
+    img = synth.blob_scene(H, W, 8, 41, n_blobs=5, margin=40).image
+    d = torch.from_numpy(img).to(DEV)
+    wins = [(21, 21), (41, 31), (61, 61)]
+    q = [torch.full((B,), 1.0 / B, device=DEV) for _ in wins]
+    s = torch.cuda.Stream()
+    with S.Plan(S.make_desc(H, W, bins=B, kernels=("manhattan", "euclidean"), max_win=(61, 61))) as p:
+        p.build_ih(d, s)
+        for kernel in ("manhattan", "euclidean"):
+            maps = [torch.empty((H - h + 1, W - w + 1), device=DEV) for w, h in wins]
+            p.likelihood_scales(kernel, wins, q, maps, s)
+            s.synchronize()
+            ref = [m.clone() for m in maps]
+            for m in maps:
+                m.fill_(-1.0)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                p.likelihood_scales(kernel, wins, q, maps, s)
+            g.replay()
+            torch.cuda.synchronize()
+            for a, b in zip(ref, maps):
+                assert torch.equal(a, b), kernel
+        p.sync_status(s)

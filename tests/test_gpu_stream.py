@@ -181,3 +181,46 @@ def test_timed_pass_equals_the_graph_pass_and_counts_loaded_bytes():
         two = st.load_bytes(reset=True)
         assert two == {k: 2 * v for k, v in one.items()}, (one, two)
         assert all(v == 0 for v in st.load_bytes().values())
+
+
+def test_frames_wider_than_8192_columns_in_column_tiles():
+    """A 12000-column frame runs as column tiles of at most 8192 columns (plus
+    row bands): the maps equal those of plans over the left and right 8192
+    columns bit for bit, and the oracle at centres on both sides of the tile
+    boundary."""
+    H, W, bd, B = 420, 12000, 12, 8
+    img = synth.blob_scene(H, W, 16, 31, n_blobs=40, margin=60).image
+    d = torch.from_numpy(img.view(np.int16)).to(DEV)
+    jobs_spec = [("manhattan", 9, 9), ("euclidean", 43, 21), ("gaussian", 41, 41), ("gaussian", 25, 25)]
+    bins, jobs = make_jobs(img, bd, B, jobs_spec)
+    desc = S.make_desc(H, W, pixel_type=S.SWIH_PIXEL_U16, bitdepth=bd, bins=B,
+                       kernels=("manhattan", "euclidean", "gaussian"), max_win=(43, 41))
+    fj = [S.make_frame_job(j["kernel"], j["w"], j["h"], j["target"], j["map"]) for j in jobs]
+    with S.Stream(desc, fj, d, band_height=150) as st:
+        st.run()
+        st.sync_status()
+        info = st.info()
+    assert info["n_bands"] == 3
+    for j in jobs:
+        assert (j["map"] >= 0).all(), "a centre was not written"
+    # plans over the left and right 8192 columns (frame pitch): every centre of
+    # the frame lies in one of them
+    for x0 in (0, W - 8192):
+        pd = S.make_desc(H, 8192, pitch_bytes=W * 2, pixel_type=S.SWIH_PIXEL_U16, bitdepth=bd, bins=B,
+                         kernels=("manhattan", "euclidean", "gaussian"), max_win=(43, 41))
+        with S.Plan(pd) as p:
+            p.build_ih(d.data_ptr() + 2 * x0)
+            for j in jobs:
+                m = torch.empty((H - j["h"] + 1, 8192 - j["w"] + 1), device=DEV)
+                p.likelihood(j["kernel"], j["w"], j["h"], j["target"], m)
+                p.sync_status()
+                assert torch.equal(m, j["map"][:, x0: x0 + m.shape[1]]), (x0, j["kernel"], j["w"])
+    # the oracle across the tile boundary (tile 0 owns centre columns below 21 + 8150)
+    rng = np.random.default_rng(3)
+    for j in jobs:
+        rx, ry = (j["w"] - 1) // 2, (j["h"] - 1) // 2
+        cx = rng.integers(8150, 8195, 400)
+        cy = rng.integers(ry, H - ry, 400)
+        ref = O.likelihood_at(bins, B, j["K"], j["q"], cx, cy)
+        got = j["map"].cpu().numpy()[cy - ry, cx - rx]
+        assert np.abs(got - ref).max() <= TOL, j["kernel"]
