@@ -193,7 +193,14 @@ __global__ void __launch_bounds__(kWThreads) gauss_wide_kernel(const __grid_cons
         const int t = i / p.B, b = i - t * p.B;
         s_sq[i] = sqrtf(fmaxf(p.target[(int64_t)t * p.target_stride + b], 0.f));
     }
-    for (int iy = blockIdx.y; iy < p.ncy; iy += gridDim.y) {
+    // centre rows in the order 0, h, 2h, ..., 1, 1 + h, ...: the bottom corner
+    // row of a window is the top corner row of the window h rows below, so
+    // blocks that run one after the other read shared rows from L2
+    const int h = 2 * p.ry + 1;
+    const int m = (p.ncy + h - 1) / h;
+    for (int j = blockIdx.y; j < m * h; j += gridDim.y) {
+        const int iy = (j % m) * h + j / m;
+        if (iy >= p.ncy) continue;  // uniform over the block
         const int cy = p.cy0 + iy;
         __syncthreads();  // the previous row's coefficients are no longer read
         if (threadIdx.x == 0) {
@@ -217,7 +224,8 @@ __global__ void __launch_bounds__(kWThreads) gauss_wide_kernel(const __grid_cons
 template <typename T, int DM>
 cudaError_t launch_dm(const GaussWideParams &p, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((p.ncx + kWThreads - 1) / kWThreads), (unsigned)(p.ncy < 65535 ? p.ncy : 65535));
+    const long long rows = (long long)((p.ncy + 2 * p.ry) / (2 * p.ry + 1)) * (2 * p.ry + 1);
+    const dim3 grid((unsigned)((p.ncx + kWThreads - 1) / kWThreads), (unsigned)(rows < 65535 ? rows : 65535));
     const size_t smem = p.target ? sizeof(float) * (size_t)p.n_targets * p.B : 0;
     gauss_wide_kernel<T, DM><<<grid, kWThreads, smem, s>>>(p);
     count_launches(1);
