@@ -401,7 +401,7 @@ def run_swih(args, rank, world, local_rank):
     dom_ms = float(np.mean([seg_ms[k] for k in dom_keys]))
     peak, peak_kind = read_peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    src = "k2_ih_scan.cu" if dom.startswith("ih_scan") else "k3_tiled_kernels.cuh"
+    src = "k2_ih_scan.cuh" if dom.startswith("ih_scan") else "k3_tiled_kernels.cuh"
     prof = "ih_scan_gaussian_1024" if dom.startswith("ih_scan (G") else (
         "gather_gaussian_1024" if dom == "gather Gaussian" else None)
     if H != 1024 or B != 32:
@@ -1018,7 +1018,7 @@ def run_exp_profile():
     print(json.dumps({"exp_profile": "ok", "bins": B}), flush=True)
 
 
-def run_wide_profile(degree=3, w=151):
+def run_wide_profile(degree=3, w=151, timed=False):
     """A small run of the any-degree Gaussian gather to capture under ncu: the
     benchmark frame with B = 8, a degree-3 plan at a 151 px window (128-bit
     ring), two builds and two maps."""
@@ -1035,14 +1035,23 @@ def run_wide_profile(degree=3, w=151):
     q = torch.full((B,), 1.0 / B, device=dev)
     m = torch.empty((H - w + 1, W - w + 1), device=dev)
     desc = S.make_desc(H, W, bins=B, kernels=("gaussian",), max_win=(w, w), gauss_degree=degree)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with S.Plan(desc) as p:
         for _ in range(2):
             p.build_ih(d_img)
             p.likelihood("gaussian", w, w, q, m)
         p.sync_status()
         elem = p.info().elem_bytes
-    print(json.dumps({"wide_profile": "ok", "bins": B, "degree": degree, "window": w, "ring_bits": 8 * elem}),
-          flush=True)
+        if timed:
+            e0.record()
+            for _ in range(5):
+                p.likelihood("gaussian", w, w, q, m)
+            e1.record()
+            p.sync_status()
+    out = {"wide_profile": "ok", "bins": B, "degree": degree, "window": w, "ring_bits": 8 * elem}
+    if timed:
+        out["gather_ms"] = e0.elapsed_time(e1) / 5
+    print(json.dumps(out), flush=True)
 
 
 # ----------------------------------------------------------------------------- serving
@@ -1467,6 +1476,7 @@ def main():
                     help="small exponential-kernel run for ncu captures: B = 8, two builds and two w = 41 maps")
     ap.add_argument("--wide-profile", action="store_true",
                     help="small any-degree Gaussian run for ncu captures: B = 8, degree 3, 151 px window")
+    ap.add_argument("--timed", action="store_true", help="with --wide-profile: time five maps with CUDA events")
     ap.add_argument("--regions-only", action="store_true",
                     help="only the batched search-regions measurement (for launch lists of the batch)")
     args = ap.parse_args()
@@ -1483,7 +1493,7 @@ def main():
         run_exp_profile()
         return
     if args.wide_profile:
-        run_wide_profile()
+        run_wide_profile(timed=args.timed)
         return
     if args.regions_only:
         import torch

@@ -66,23 +66,37 @@ __device__ __forceinline__ double to_double(T a)
     }
 }
 
+// a read-only load of one ring element (two 64-bit halves for the 128-bit ring)
+template <typename T>
+__device__ __forceinline__ T ld_ro(const T *p)
+{
+    if constexpr (sizeof(T) == 16) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+        return T(v.x, v.y);
+    } else {
+        return __ldg(p);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T select(bool c, T a)
+{
+    return c ? a : T(0);
+}
+
 // sum over columns (xa, xb] and rows (ra, rb] of one plane; ra, rb are stored
-// rows (-1: above the image or an all-zero row), xa = -1 is left of the image
+// rows (-1: above the image or an all-zero row), xa = -1 is left of the image.
+// The four loads are unconditional (clamped to row or column 0 and masked
+// afterwards), so a thread's loads of several planes can all be in flight.
 template <typename T>
 __device__ __forceinline__ T rect_sum(const T *__restrict__ plane, int64_t pitch, int ra, int rb, int xa, int xb)
 {
-    T v = 0;
-    if (rb >= 0) {
-        const T *row = plane + (int64_t)rb * pitch;
-        v = row[xb];
-        if (xa >= 0) v = v - row[xa];
-    }
-    if (ra >= 0) {
-        const T *row = plane + (int64_t)ra * pitch;
-        v = v - row[xb];
-        if (xa >= 0) v = v + row[xa];
-    }
-    return v;
+    const bool va = ra >= 0, vb = rb >= 0, vx = xa >= 0;
+    const T *row_a = plane + (int64_t)(va ? ra : 0) * pitch;
+    const T *row_b = plane + (int64_t)(vb ? rb : 0) * pitch;
+    const int xc = vx ? xa : 0;
+    const T b1 = ld_ro(row_b + xb), b0 = ld_ro(row_b + xc), a1 = ld_ro(row_a + xb), a0 = ld_ro(row_a + xc);
+    return select(vb, b1 - select(vx, b0)) - select(va, a1 - select(vx, a0));
 }
 
 __device__ __forceinline__ int binom_small(int n, int k)

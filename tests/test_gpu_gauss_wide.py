@@ -77,7 +77,8 @@ def test_integral_histograms_bit_exact_in_the_128_bit_ring():
             assert (got == ref).all(), (pp, qq, b)
 
 
-@pytest.mark.parametrize("degree,w,h", [(3, 9, 9), (3, 15, 11), (4, 15, 15), (4, 9, 21), (3, 41, 41)])
+@pytest.mark.parametrize("degree,w,h", [(3, 9, 9), (3, 15, 11), (4, 15, 15), (4, 9, 21), (3, 41, 41),
+                                        (3, 5, 41), (4, 3, 9)])  # the last two fit lower degrees on one axis
 def test_degree_3_and_4_full_maps(degree, w, h):
     H, W, B = 140, 190, 16
     img = scene(H, W, 7 + degree)
