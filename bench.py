@@ -1477,6 +1477,8 @@ def main():
     ap.add_argument("--wide-profile", action="store_true",
                     help="small any-degree Gaussian run for ncu captures: B = 8, degree 3, 151 px window")
     ap.add_argument("--timed", action="store_true", help="with --wide-profile: time five maps with CUDA events")
+    ap.add_argument("--wide-degree", type=int, default=3, help="with --wide-profile: the Gaussian's degree")
+    ap.add_argument("--wide-window", type=int, default=151, help="with --wide-profile: the window side")
     ap.add_argument("--regions-only", action="store_true",
                     help="only the batched search-regions measurement (for launch lists of the batch)")
     args = ap.parse_args()
@@ -1493,7 +1495,7 @@ def main():
         run_exp_profile()
         return
     if args.wide_profile:
-        run_wide_profile(timed=args.timed)
+        run_wide_profile(degree=args.wide_degree, w=args.wide_window, timed=args.timed)
         return
     if args.regions_only:
         import torch

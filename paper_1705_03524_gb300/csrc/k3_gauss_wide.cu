@@ -196,7 +196,7 @@ __device__ __forceinline__ void centre(const GaussWideParams &p, const T (*s_cy)
 }
 
 template <typename T, int DM>
-__global__ void __launch_bounds__(kWThreads) gauss_wide_kernel(const __grid_constant__ GaussWideParams p)
+__global__ void __launch_bounds__(kWThreads, (sizeof(T) == 16 && DM == 4) ? 3 : 4) gauss_wide_kernel(const __grid_constant__ GaussWideParams p)
 {
     constexpr int NA = 2 * DM + 1;
     __shared__ T s_cy[DM + 1][NA];  // C(2l, b) (-yc)^(2l-b) for b <= 2l
