@@ -433,7 +433,24 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
 }
 
 template <typename T, int E, int NP, bool SPARSE>
+__device__ __forceinline__ void plan_scan(const ScanParams &p);
+
+template <typename T, int E, int NP, bool SPARSE>
 __global__ void __launch_bounds__(kMaxScanThreads) ih_scan_kernel(const __grid_constant__ ScanParams p)
+{
+    plan_scan<T, E, NP, SPARSE>(p);
+}
+
+// The same for 256-thread blocks, compiled for 5 resident blocks per SM (at
+// most 51 registers): the Gaussian plan's scan of images up to 1024 columns
+template <typename T, int E, int NP, bool SPARSE>
+__global__ void __launch_bounds__(256, 5) ih_scan_kernel_256x5(const __grid_constant__ ScanParams p)
+{
+    plan_scan<T, E, NP, SPARSE>(p);
+}
+
+template <typename T, int E, int NP, bool SPARSE>
+__device__ __forceinline__ void plan_scan(const ScanParams &p)
 {
     __shared__ int s_ticket;
     if (threadIdx.x == 0) s_ticket = atomicAdd(p.ticket, 1);
@@ -520,6 +537,20 @@ cudaError_t launch_typed(const ScanParams &p_in, int threads, const ScanRoi *tab
         }
     } else if (p.occ) {
         if (p.band_rows > 64) return cudaErrorInvalidValue;  // the occupancy word covers 64 rows
+        if constexpr (sizeof(T) == 8 && NP == 5 && E == 4) {
+            if (threads == 256) {
+                // the Gaussian plan's scan: 5 resident blocks need the full shared-memory carve-out
+                e = allow_smem(ih_scan_kernel_256x5<T, E, NP, true>, smem);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(ih_scan_kernel_256x5<T, E, NP, true>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+                if (e != cudaSuccess) return e;
+                ih_scan_kernel_256x5<T, E, NP, true>
+                    <<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, smem, s>>>(p);
+                count_launches(1);
+                return cudaGetLastError();
+            }
+        }
         e = allow_smem(ih_scan_kernel<T, E, NP, true>, smem);
         if (e != cudaSuccess) return e;
         ih_scan_kernel<T, E, NP, true><<<(unsigned)((long long)p.B * p.n_q * p.n_bands), threads, smem, s>>>(p);
