@@ -51,12 +51,11 @@ cudaError_t tiled_shape(int kind, int elem_bytes, int gdx, int gdy, int max_w, i
     }
     for (int i = 0; i < ntx; ++i) {
         const int tx = txs[i];
-        // bins per pipeline step. Steps of 2 bins exist for the 256-column 32-bit
-        // kernels only; by default the Euclidean takes them there (its 5 planes
-        // per bin make a 4-bin stage too large for 4 resident CTAs)
+        // bins per pipeline step (4 by default). Steps of 2 bins exist for the
+        // 256-column 32-bit kernels only, on request (they keep 4 Euclidean CTAs
+        // resident, which measured slower than 4-bin steps)
         int bb = gau ? 1 : (want_bb == 8 ? 8 : 4);
-        if (!gau && tx == 256 && elem_bytes == 4 && (want_bb == 2 || (want_bb == 0 && kind == kGatherEuclidean)))
-            bb = 2;
+        if (!gau && tx == 256 && elem_bytes == 4 && want_bb == 2) bb = 2;
         GatherShape sh;
         sh.tx = tx;
         sh.bb = bb;
