@@ -312,10 +312,11 @@ swih_status swih_plan_load_bytes(swih_plan_t plan, uint64_t *bytes, int reset);
 
 /* ---------------------------------------------------------------- batches
  * Many regions of interest (ROIs) of one frame, each with its own size,
- * kernel, windows (scales) and target histogram, processed by a fixed set of
- * launches: one quantisation over all ROIs, one integral-histogram scan over
- * all ROIs, and one window-gather launch per group of jobs that share a kernel
- * and fitted degree (a job = one ROI at one window). The sequence is captured
+ * kernel, windows (scales), bin count and target histogram, processed by a
+ * fixed set of launches per bin count among the ROIs: one quantisation over
+ * its ROIs, one integral-histogram scan over them, and one window-gather
+ * launch per group of jobs that share a kernel and fitted degree (a job = one
+ * ROI at one window). The sequence is captured
  * into a CUDA graph once and replayed by swih_batch_run. This is the paper's
  * search problem (Sec. 1, Sec. 4: likelihood maps for many candidate regions)
  * run for many targets at once; the paper itself processes one region at a
@@ -326,7 +327,7 @@ typedef struct swih_batch_desc {
     int64_t pitch_bytes;       /* frame row stride in bytes */
     int32_t pixel_type;        /* swih_pixel_type */
     int32_t bitdepth;
-    int32_t bins;              /* B, shared by every ROI */
+    int32_t bins;              /* B of every ROI that does not set its own */
     uint32_t kernel_mask;      /* kernels any ROI may use */
     int32_t gauss_degree;      /* as in swih_plan_desc */
     double gauss_sigma_frac;
@@ -343,6 +344,9 @@ typedef struct swih_roi_desc {
     int32_t win_w[SWIH_MAX_SCALES], win_h[SWIH_MAX_SCALES];  /* odd, >= 3, <= ROI size */
     const float *d_target;     /* device float32 [bins], q(b) >= 0 summing to 1 */
     float *d_map[SWIH_MAX_SCALES]; /* device float32 [height-win_h+1][width-win_w+1] each */
+    int32_t bins;              /* B of this ROI, 1..256 (0: the batch's bins); ROIs of each
+                                  bin count form one work set (its own three launches) */
+    int32_t reserved;          /* 0 */
 } swih_roi_desc;
 
 typedef struct swih_batch_s *swih_batch_t;

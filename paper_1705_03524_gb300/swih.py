@@ -144,6 +144,8 @@ class swih_roi_desc(ctypes.Structure):
         ("win_h", ctypes.c_int32 * SWIH_MAX_SCALES),
         ("d_target", ctypes.c_void_p),
         ("d_map", ctypes.c_void_p * SWIH_MAX_SCALES),
+        ("bins", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -578,8 +580,9 @@ def make_batch_desc(height, width, *, pitch_bytes=None, pixel_type=SWIH_PIXEL_U8
     return d
 
 
-def make_roi(x0, y0, width, height, kernel, windows, target, maps) -> swih_roi_desc:
-    """windows: [(w, h), ...] (at most SWIH_MAX_SCALES); maps: one device buffer per window."""
+def make_roi(x0, y0, width, height, kernel, windows, target, maps, bins=0) -> swih_roi_desc:
+    """windows: [(w, h), ...] (at most SWIH_MAX_SCALES); maps: one device buffer per window;
+    bins: this ROI's bin count (0: the batch's)."""
     if len(windows) != len(maps) or not 1 <= len(windows) <= SWIH_MAX_SCALES:
         raise ValueError("need 1..SWIH_MAX_SCALES windows, one map each")
     r = swih_roi_desc()
@@ -590,6 +593,8 @@ def make_roi(x0, y0, width, height, kernel, windows, target, maps) -> swih_roi_d
         r.win_w[k], r.win_h[k] = int(w), int(h)
         r.d_map[k] = _ptr(maps[k])
     r.d_target = _ptr(target)
+    r.bins = int(bins)
+    r.reserved = 0
     return r
 
 

@@ -301,3 +301,41 @@ def test_every_binary_4x4_image_in_one_batch(kernel):
             ref = O.likelihood_at(bins, B, K, q, 4 * tx + 1 + dx, 4 * ty + 1 + dy)
             err = np.abs(got[:, dy, dx] - ref).max()
             assert err <= TOL, (kernel, dx, dy, err)
+
+
+def test_regions_with_their_own_bin_counts():
+    """ROIs of one batch with different bin counts (one work set per count,
+    all in the one graph) match the oracle at their own B, survive autotuning,
+    and the sync status covers every set."""
+    img = synth.blob_scene(260, 420, 8, seed=15, n_blobs=6, margin=30).image
+    rows = [(0, 0, 120, 90, "manhattan", [(21, 21)], 8), (100, 40, 200, 150, "gaussian", [(25, 25), (41, 31)], 32),
+            (250, 120, 160, 130, "euclidean", [(15, 15)], 64), (30, 150, 90, 100, "gaussian", [(9, 9)], 8),
+            (300, 10, 100, 80, "plain", [(7, 7)], 0)]  # 0: the batch's own bin count
+    B_default = 16
+    specs, bs = [], []
+    for (x0, y0, w, h, k, wins, B) in rows:
+        sp = Spec(x0, y0, w, h, k, wins)
+        Bi = B or B_default
+        sp.set_target(oracle_bins(sp.crop(img), 8, Bi), Bi, seed=x0 + y0)
+        specs.append(sp)
+        bs.append(B)
+    buf, ptr, pitch = upload(img)
+    desc = S.make_batch_desc(img.shape[0], img.shape[1], pitch_bytes=pitch, bins=B_default,
+                             kernels=("plain", "manhattan", "euclidean", "gaussian"))
+    rois = [S.make_roi(sp.x0, sp.y0, sp.w, sp.h, sp.kernel, sp.windows, sp.target, sp.maps, bins=B)
+            for sp, B in zip(specs, bs)]
+    keep = [buf] + [sp.target for sp in specs] + [m for sp in specs for m in sp.maps]
+    with S.Batch(desc, rois, ptr, keep=keep) as batch:
+        batch.run()
+        batch.sync_status()
+        first = [m.clone() for sp in specs for m in sp.maps]
+        batch.autotune()
+        for sp in specs:
+            for m in sp.maps:
+                m.fill_(-1.0)
+        batch.run()
+        batch.sync_status()
+    for a, m in zip(first, [m for sp in specs for m in sp.maps]):
+        assert torch.equal(a, m)
+    for sp, B in zip(specs, bs):
+        check_against_oracle(img, 8, B or B_default, [sp])
