@@ -196,9 +196,14 @@ class FrameStep:
     """One benchmark step over a frame: the Manhattan+Euclidean plan's and the
     Gaussian plan's integral histograms, then each kernel's windows in one
     multi-window launch (swih_likelihood_scales). Targets are the window of
-    each kernel and size centred on (tx, ty), set up untimed."""
+    each kernel and size centred on (tx, ty), set up untimed.
 
-    def __init__(self, S, dev, img, B, kernels, tx, ty, stream, windows=WINDOWS):
+    With two streams (the default) the two plans, which share only the frame,
+    run side by side: the Gaussian plan's build and gather on `stream`, the
+    Manhattan+Euclidean plan's build and gathers on a second stream forked from
+    it and joined back at the end of the step."""
+
+    def __init__(self, S, dev, img, B, kernels, tx, ty, stream, windows=WINDOWS, streams=2):
         import torch
 
         H, W = img.shape
@@ -226,27 +231,65 @@ class FrameStep:
         for pl in self.plans:
             pl.sync_status(stream)
         self.windows_per_step = sum(m.numel() for m in self.maps)
+        # the Manhattan+Euclidean plan's stream (the main one with streams=1)
+        self.side = torch.cuda.Stream(device=dev) if streams > 1 and self.plan_me and self.plan_g else stream
+        self.fork = torch.cuda.Event()
+        self.join = torch.cuda.Event()
+        self.stages = ([s for s, pl in (("build_me", self.plan_me), ("build_g", self.plan_g)) if pl]
+                       + [f"gather_{k}" for k in kernels])
+
+    def stream_of(self, stage):
+        return self.stream if stage in ("build_g", "gather_gaussian") else self.side
+
+    def new_events(self):
+        """Begin and end events of every stage of one step."""
+        import torch
+
+        return {st: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for st in self.stages}
+
+    def run_maps(self, d_img, targets, maps, s, side, ev=None, on_map=None):
+        """Enqueue one step on d_img: builds and gathers of both plans, the
+        Manhattan+Euclidean ones on `side` (forked from and joined back to s).
+        on_map(job, stream) runs after each kernel's gather launch."""
+        def mark(stage, i, st):
+            if ev is not None:
+                ev[stage][i].record(st)
+
+        if side is not s:
+            self.fork.record(s)
+            side.wait_event(self.fork)
+        for st, pl, name in ((side, self.plan_me, "build_me"), (s, self.plan_g, "build_g")):
+            if pl:
+                mark(name, 0, st)
+                pl.build_ih(d_img, st)
+                mark(name, 1, st)
+        for k in self.kernels:  # the kernel's windows in one launch (multi-scale search)
+            st = s if k == "gaussian" else side
+            js = self.job_of[k]
+            mark(f"gather_{k}", 0, st)
+            self.plan_of[k].likelihood_scales(k, [(self.jobs[j][1], self.jobs[j][1]) for j in js],
+                                              [targets[j] for j in js], [maps[j] for j in js], st)
+            mark(f"gather_{k}", 1, st)
+            if on_map is not None:
+                for j in js:
+                    on_map(j, st)
+        if side is not s:
+            self.join.record(side)
+            s.wait_event(self.join)
 
     def step(self, ev=None):
-        """ev (optional): 3 + len(kernels) events, recorded before the builds,
-        after each build and after each kernel's gather launch."""
-        s = self.stream
-        if ev is not None:
-            ev[0].record(s)
-        if self.plan_me:
-            self.plan_me.build_ih(self.d_img, s)
-        if ev is not None:
-            ev[1].record(s)
-        if self.plan_g:
-            self.plan_g.build_ih(self.d_img, s)
-        if ev is not None:
-            ev[2].record(s)
-        for ki, k in enumerate(self.kernels):  # the kernel's windows in one launch (multi-scale search)
-            js = self.job_of[k]
-            self.plan_of[k].likelihood_scales(k, [(self.jobs[j][1], self.jobs[j][1]) for j in js],
-                                              [self.targets[j] for j in js], [self.maps[j] for j in js], s)
-            if ev is not None:
-                ev[3 + ki].record(s)
+        """ev (optional): new_events() of this step."""
+        self.run_maps(self.d_img, self.targets, self.maps, self.stream, self.side, ev)
+
+    @staticmethod
+    def stage_ms(events):
+        """Mean duration of each stage over the steps' events."""
+        out = {}
+        for ev in events:
+            for st, (e0, e1) in ev.items():
+                out.setdefault(st, []).append(e0.elapsed_time(e1))
+        return {k: float(np.mean(v)) for k, v in out.items()}
 
     def timed(self, steps, clocks=None):
         """Time `steps` steps with CUDA events (after a synchronize); returns
@@ -254,8 +297,7 @@ class FrameStep:
         Gaussian gathers loaded per launch, clock summary or None)."""
         import torch
 
-        n_ev = 3 + len(self.kernels)
-        events = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(steps)]
+        events = [self.new_events() for _ in range(steps)]
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         if clocks is not None:
@@ -274,18 +316,12 @@ class FrameStep:
         for pl in self.plans:
             pl.sync_status(self.stream)
         loaded_g = self.plan_g.load_bytes() / steps if self.plan_g else 0.0
-        seg = {"build_me": [], "build_g": []}
-        for i in range(steps):
-            ev = events[i]
-            seg["build_me"].append(ev[0].elapsed_time(ev[1]))
-            seg["build_g"].append(ev[1].elapsed_time(ev[2]))
-            for ki, k in enumerate(self.kernels):
-                seg.setdefault(f"gather_{k}", []).append(ev[2 + ki].elapsed_time(ev[3 + ki]))
-        return t0.elapsed_time(t1), {k: float(np.mean(v)) for k, v in seg.items()}, loaded_g, clk
+        return t0.elapsed_time(t1), self.stage_ms(events), loaded_g, clk
 
     def close(self):
         for pl in self.plans:
             pl.close()
+
 
 # inputs and final maps of the benchmark run, for the oracle comparison
 _ORACLE_CHECK = []
@@ -309,14 +345,13 @@ def run_swih(args, rank, world, local_rank):
     kernels = tuple(k for k in KERNELS if k in args.kernels.split(","))
     tx, ty = cfg["target_centre"]
     stream = torch.cuda.Stream(device=dev)
-    fr = FrameStep(S, dev, img, B, kernels, tx, ty, stream)
+    fr = FrameStep(S, dev, img, B, kernels, tx, ty, stream, streams=args.streams)
     d_img = fr.d_img
     plan_me, plan_g, plans, plan_of = fr.plan_me, fr.plan_g, fr.plans, fr.plan_of
     info_me, info_g = fr.info_me, fr.info_g
     jobs, job_of, targets, maps = fr.jobs, fr.job_of, fr.targets, fr.maps
     step = fr.step
 
-    n_ev = 3 + len(kernels)
     for _ in range(args.warmup):
         step()
     for pl in plans:
@@ -325,7 +360,7 @@ def run_swih(args, rank, world, local_rank):
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    events = [fr.new_events() for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local_rank)
@@ -353,17 +388,22 @@ def run_swih(args, rank, world, local_rank):
         pl.sync_status(stream)
     loaded_g = plan_g.load_bytes() if plan_g else 0
 
-    # per-launch durations inside the timed region
-    seg = {"build_me": [], "build_g": []}
-    for k in kernels:
-        seg[f"gather_{k}"] = []  # one launch: the kernel's three windows
-    for s in range(args.steps):
-        ev = events[s]
-        seg["build_me"].append(ev[0].elapsed_time(ev[1]))
-        seg["build_g"].append(ev[1].elapsed_time(ev[2]))
-        for ki, k in enumerate(kernels):
-            seg[f"gather_{k}"].append(ev[2 + ki].elapsed_time(ev[3 + ki]))
-    seg_ms = {k: float(np.mean(v)) for k, v in seg.items()}
+    # per-launch durations inside the timed region (each gather stage is one
+    # launch: the kernel's three windows), on the stream each stage runs on;
+    # with two streams a stage's span includes the time it shares the GPU with
+    # the other plan's stages
+    seg_ms = FrameStep.stage_ms(events)
+
+    # the same step with both plans on one stream, right after the timed region:
+    # each stage alone on the GPU (the per-kernel figures beside the overlapped ones)
+    solo = None
+    if fr.side is not fr.stream:
+        side, fr.side = fr.side, fr.stream
+        n_solo = max(50, min(args.steps, 200))
+        solo_ms, solo_seg, solo_loaded, _ = fr.timed(n_solo)
+        fr.side = side
+        solo = {"steps": n_solo, "ms_per_step": solo_ms / n_solo, "per_launch_ms": solo_seg,
+                "loaded_g": solo_loaded}
 
     # algorithmic bytes per launch
     def ih_bytes(info, n_terms_used):
@@ -384,17 +424,18 @@ def run_swih(args, rank, world, local_rank):
                "gather Gaussian": ["gather_gaussian"],
                "gather Euclidean": ["gather_euclidean"],
                "gather Manhattan": ["gather_manhattan"]}
-    totals = {c: sum(seg_ms.get(k, 0.0) for k in ks) for c, ks in classes.items()}
+    stage_alone = solo["per_launch_ms"] if solo else seg_ms  # which kernel dominates on its own
+    totals = {c: sum(stage_alone.get(k, 0.0) for k in ks) for c, ks in classes.items()}
     dom = max(totals, key=totals.get)
     dom_keys = classes[dom]
     dom_keys = [k for k in dom_keys if k in seg_ms]
     dense_bytes = float(np.mean([algo[k] for k in dom_keys]))
     dom_bytes = dense_bytes
     basis = "dense: every integral-histogram element the kernel's terms use, once, plus the map"
+    maps_b = float(sum(4 * (H - w + 1) * (W - w + 1) for w in WINDOWS))
     if dom == "gather Gaussian" and loaded_g:
         # the gather skips bins and rows absent from its windows: its algorithmic
         # bytes are the row segments it must load (counted by the kernel) + the map
-        maps_b = float(sum(4 * (H - w + 1) * (W - w + 1) for w in WINDOWS))
         dom_bytes = loaded_g / args.steps + maps_b  # one launch per step: the three windows
         basis = ("integral-histogram row segments the sparse gather loads (rows of windows holding "
                  "each bin, counted by the kernel over the timed launches) + the map")
@@ -407,6 +448,18 @@ def run_swih(args, rank, world, local_rank):
     if H != 1024 or B != 32:
         prof = None  # the committed counters are for the benchmark workload only
     traffic = profile_traffic(prof, src) if prof else None
+    roof_solo = None
+    if solo:
+        s_ms = float(np.mean([solo["per_launch_ms"][k] for k in dom_keys]))
+        s_bytes = dom_bytes
+        if dom == "gather Gaussian" and solo["loaded_g"]:
+            s_bytes = solo["loaded_g"] + maps_b
+        roof_solo = {"avg_launch_ms": s_ms, "achieved": s_bytes / (s_ms * 1e-3) / 1e9,
+                     "frac": s_bytes / (s_ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_launch": s_bytes,
+                     "steps": solo["steps"], "ms_per_step": solo["ms_per_step"],
+                     "per_launch_ms": solo["per_launch_ms"],
+                     "note": ("the same step with both plans on one stream, timed right after the timed "
+                              "region: the kernel alone on the GPU")}
 
     # ---- the same step over a timed region of at least 1.5 s (>= 400 steps),
     # with the clocks sampled throughout: the sustained rate beside the K-step line
@@ -450,16 +503,10 @@ def run_swih(args, rank, world, local_rank):
 
     def compute_and_download(i):
         stream.wait_event(ev_in[i])
-        for pl in plans:
-            pl.build_ih(d_imgs[i], stream)
-        for k in kernels:
-            js = job_of[k]
-            for j in js:
-                stream.wait_event(ev_out[i][j])
-            plan_of[k].likelihood_scales(k, [(jobs[j][1], jobs[j][1]) for j in js], [d_tgts[i][j] for j in js],
-                                         [d_maps[i][j] for j in js], stream)
-            for j in js:
-                ev_map[i][j].record(stream)
+        for j in range(len(jobs)):  # set i's maps downloaded two steps ago
+            stream.wait_event(ev_out[i][j])
+        fr.run_maps(d_imgs[i], d_tgts[i], d_maps[i], stream, fr.side,
+                    on_map=lambda j, st: ev_map[i][j].record(st))
         ev_used[i].record(stream)
         with torch.cuda.stream(copy):
             for j in range(len(jobs)):
@@ -526,6 +573,8 @@ def run_swih(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "windows_per_step_per_gpu": wps, "bins": B,
                    "image": f"{H}x{W} u8", "kernels": list(KERNELS), "window_sizes": list(WINDOWS),
                    "parallelism": f"replicas x{world} (independent frames, no collective)",
+                   "streams": ("2 (Gaussian plan | Manhattan+Euclidean plan, forked and joined each step)"
+                               if fr.side is not fr.stream else "1"),
                    "l2": "working set (integral histograms 7.1 GB/step) >> L2; no flush"},
         "e2e": {"value": rate_e2e, "unit": "windows/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
@@ -534,7 +583,7 @@ def run_swih(args, rank, world, local_rank):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
                      "bytes_basis": basis, "dense_bytes_per_launch": dense_bytes,
-                     "avg_launch_ms": dom_ms},
+                     "avg_launch_ms": dom_ms, "solo": roof_solo},
         "per_launch_ms": seg_ms,
         "clocks": clk,
     }
@@ -574,7 +623,9 @@ def run_dense_scene(args, dev):
     bin and every window holds most bins, so the scans store every row and the
     gathers skip almost nothing: the worst case for the method's exact
     skipping of absent bins and rows. Timed like the main line (CUDA events,
-    per launch); the roofline uses the dense bytes of each stage."""
+    the two plans on two streams); the per-stage figures and the roofline come
+    from the same steps run on one stream (each stage alone on the GPU) and use
+    the dense bytes of each stage."""
     import torch
 
     from paper_1705_03524_gb300 import swih as S
@@ -584,12 +635,17 @@ def run_dense_scene(args, dev):
     B = 32
     img = synth.uniform_image(H, W, 8, seed=1)
     stream = torch.cuda.Stream(device=dev)
-    fr = FrameStep(S, dev, img, B, KERNELS, W // 2, H // 2, stream)
+    fr = FrameStep(S, dev, img, B, KERNELS, W // 2, H // 2, stream, streams=args.streams)
     try:
         for _ in range(max(3, args.warmup)):
             fr.step()
         steps = max(args.steps, 50)
-        ms, seg, loaded_g, _ = fr.timed(steps)
+        ms, seg_overlap, loaded_g, _ = fr.timed(steps)
+        seg = seg_overlap
+        if fr.side is not fr.stream:  # per-stage figures with each stage alone on the GPU
+            side, fr.side = fr.side, fr.stream
+            _, seg, loaded_g, _ = fr.timed(steps)
+            fr.side = side
         algo = stage_bytes(fr, H, W, B)
     finally:
         fr.close()
@@ -604,6 +660,7 @@ def run_dense_scene(args, dev):
                      "x windows 21/41/81, full valid maps (no spatial structure: nothing to skip)"),
         "windows_per_step": fr.windows_per_step, "steps": steps, "ms_per_step": ms / steps,
         "windows_per_s": fr.windows_per_step * steps / (ms * 1e-3),
+        "per_launch_ms_overlapped": seg_overlap,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": algo[dom],
                      "bytes_basis": "dense: every integral-histogram element of the stage, once, plus the maps",
@@ -1460,6 +1517,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--size", type=int, default=1024,
                     help="frame side; 1024 is the benchmark workload, smaller sizes are for profiling")
+    ap.add_argument("--streams", type=int, default=2, choices=(1, 2),
+                    help="2: the two plans' builds and gathers on two streams within a step")
     ap.add_argument("--kernels", default="manhattan,euclidean,gaussian",
                     help="subset of kernels (profiling); the benchmark runs all three")
     ap.add_argument("--bins", type=int, default=32,

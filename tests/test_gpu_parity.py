@@ -319,6 +319,51 @@ def test_benchmark_workload_sampled_centres():
             p.close()
 
 
+def test_benchmark_step_two_streams():
+    """The benchmark's step as it is timed: the Gaussian plan on one stream, the
+    Manhattan+Euclidean plan forked onto a second stream and joined back each
+    step, several steps in a row. The nine maps equal those of the same step on
+    one stream bit for bit, and match the oracle at sampled centres."""
+    import bench
+
+    cfg = synth.config2()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    tx, ty = cfg["target_centre"]
+    stream = torch.cuda.Stream(device=DEV)
+    fr = bench.FrameStep(S, DEV, img, B, bench.KERNELS, tx, ty, stream, streams=2)
+    try:
+        assert fr.side is not fr.stream
+        for _ in range(4):
+            fr.step()
+        torch.cuda.synchronize()
+        two = [m.cpu().numpy().copy() for m in fr.maps]
+        for m in fr.maps:
+            m.fill_(-1.0)
+        side, fr.side = fr.side, fr.stream
+        fr.step()
+        fr.side = side
+        torch.cuda.synchronize()
+        for pl in fr.plans:
+            pl.sync_status(stream)
+        one = [m.cpu().numpy() for m in fr.maps]
+        bins = oracle_bins(img, 8, B)
+        rng = np.random.default_rng(13)
+        for j, (kind, w) in enumerate(fr.jobs):
+            assert np.array_equal(two[j], one[j]), (kind, w)
+            K = O.kernel_weights(kind, w, w)
+            q = O.target_hist(bins, B, K, tx, ty)
+            x0, y0, nx, ny = O.valid_centres(H, W, w, w)
+            cx = rng.integers(x0, x0 + nx, 300)
+            cy = rng.integers(y0, y0 + ny, 300)
+            ref = O.likelihood_at(bins, B, K, q, cx, cy)
+            err = np.abs(two[j][cy - y0, cx - x0] - ref).max()
+            assert err <= TOL, (kind, w, err)
+    finally:
+        fr.close()
+
+
 # --------------------------------------------------------------------------- wedding cake
 @pytest.mark.parametrize("rings", [1, 2, 4, 8, 16])
 def test_wedding_cake_parity(rings):
