@@ -472,47 +472,53 @@ def run_swih(args, rank, world, local_rank):
                      "per_launch_ms": sus_seg, "clocks": sus_clk}
 
     # ---- end to end through the C ABI from pinned host buffers. Every step
-    # uploads its frame and targets and downloads its nine maps. The transfers
-    # run on a copy stream: a step's upload overlaps the previous step's
-    # kernels, each map leaves as soon as its gather ends, and two device buffer
-    # sets alternate between steps; events keep every buffer from being
-    # overwritten before it is consumed. The timed region opens before the first
-    # upload and closes after the last download.
+    # uploads its frame and targets and downloads its nine maps. Uploads and
+    # downloads run on two copy streams of their own (so that an upload never
+    # queues behind a download): a step's upload overlaps the previous step's
+    # kernels, and its maps (one contiguous buffer) leave in one copy while the
+    # next step computes; two device buffer sets alternate between steps, and
+    # events keep every buffer from being overwritten before it is consumed.
+    # The timed region opens before the first upload and closes after the last
+    # download.
+    sizes = [m.numel() for m in maps]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+
+    def map_views(flat):
+        return [flat[offs[j]: offs[j + 1]].view(m.shape) for j, m in enumerate(maps)]
+
     h_img = torch.from_numpy(img).pin_memory()
-    h_maps = [torch.empty(m.shape, dtype=torch.float32).pin_memory() for m in maps]
+    h_flat = torch.empty(int(offs[-1]), dtype=torch.float32).pin_memory()
+    h_maps = map_views(h_flat)
     h_targets = targets.cpu().pin_memory()
-    copy = torch.cuda.Stream(device=dev)
+    up = torch.cuda.Stream(device=dev)
+    down = torch.cuda.Stream(device=dev)
     d_imgs = [d_img, torch.empty_like(d_img)]
     d_tgts = [targets, torch.empty_like(targets)]
-    d_maps = [maps, [torch.empty_like(m) for m in maps]]
+    d_flat = [torch.empty(int(offs[-1]), dtype=torch.float32, device=dev) for _ in range(2)]
+    d_maps = [map_views(f) for f in d_flat]
     ev_in = [torch.cuda.Event() for _ in range(2)]      # set i uploaded
-    ev_used = [torch.cuda.Event() for _ in range(2)]    # kernels done reading set i's inputs
-    ev_map = [[torch.cuda.Event() for _ in jobs] for _ in range(2)]  # map j of set i written (its kernel's launch)
-    ev_out = [[torch.cuda.Event() for _ in jobs] for _ in range(2)]  # map j of set i downloaded
+    ev_used = [torch.cuda.Event() for _ in range(2)]    # set i's kernels done (inputs read, maps written)
+    ev_out = [torch.cuda.Event() for _ in range(2)]     # set i's maps downloaded
     for i in range(2):  # nothing pending yet
         ev_used[i].record(stream)
-        for e in ev_out[i]:
-            e.record(stream)
+        ev_out[i].record(stream)
 
     def upload(i):
-        with torch.cuda.stream(copy):
-            copy.wait_event(ev_used[i])
+        with torch.cuda.stream(up):
+            up.wait_event(ev_used[i])
             d_imgs[i].copy_(h_img, non_blocking=True)
             d_tgts[i].copy_(h_targets, non_blocking=True)
-            ev_in[i].record(copy)
+            ev_in[i].record(up)
 
     def compute_and_download(i):
         stream.wait_event(ev_in[i])
-        for j in range(len(jobs)):  # set i's maps downloaded two steps ago
-            stream.wait_event(ev_out[i][j])
-        fr.run_maps(d_imgs[i], d_tgts[i], d_maps[i], stream, fr.side,
-                    on_map=lambda j, st: ev_map[i][j].record(st))
+        stream.wait_event(ev_out[i])  # set i's maps downloaded two steps ago
+        fr.run_maps(d_imgs[i], d_tgts[i], d_maps[i], stream, fr.side)
         ev_used[i].record(stream)
-        with torch.cuda.stream(copy):
-            for j in range(len(jobs)):
-                copy.wait_event(ev_map[i][j])
-                h_maps[j].copy_(d_maps[i][j], non_blocking=True)
-                ev_out[i][j].record(copy)
+        with torch.cuda.stream(down):
+            down.wait_event(ev_used[i])
+            h_flat.copy_(d_flat[i], non_blocking=True)
+            ev_out[i].record(down)
 
     def e2e_run(n):
         upload(0)
@@ -521,7 +527,7 @@ def run_swih(args, rank, world, local_rank):
             compute_and_download(i)
             if n_ + 1 < n:
                 upload(1 - i)
-        stream.wait_stream(copy)
+        stream.wait_stream(down)
 
     e2e_run(max(1, args.warmup))
     torch.cuda.synchronize()
@@ -530,7 +536,8 @@ def run_swih(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    copy.wait_event(e0)
+    up.wait_event(e0)
+    down.wait_event(e0)
     e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
