@@ -1001,6 +1001,122 @@ def large_frame_error(sub, B, job_kw, targets, blocks, bx, by, R, n=512):
 
 
 # ----------------------------------------------------------------------------- exponential kernel
+CHANNEL_BINS = (16, 16, 16)
+
+
+def run_channels(args, dev, steps=50):
+    """Feature channels (Sec. 4: one likelihood map per feature): three
+    features of the benchmark frame (the 1024x1024 u8 scene at 16 bins, a
+    12-bit texture-like u16 channel at 16 bins and a 6-bit u8 channel at 16
+    bins; synth.feature_channels), Manhattan/Euclidean/Gaussian at windows
+    21/41/81. One step = both channel plans' builds (K1 per channel, one K2
+    over all 48 bins; the Manhattan+Euclidean plan on a second stream as in the
+    main step) + 9 gathers, each writing the three channels' maps in one
+    launch. Targets: each channel's window at the object (per-channel
+    normalised, set up untimed). Counted: (centre, window, channel) triples."""
+    import torch
+
+    from paper_1705_03524_gb300 import swih as S
+    from paper_1705_03524_gb300 import synth
+
+    cfg = synth.config2()
+    img = cfg["image"]
+    H, W = img.shape
+    tx, ty = cfg["target_centre"]
+    feats = synth.feature_channels(img, seed=12)
+    bufs, chans = [], []
+    for (a, bd), B in zip(feats, CHANNEL_BINS):
+        u16 = a.dtype == np.uint16
+        bufs.append(torch.from_numpy(a.view(np.int16) if u16 else a).to(dev))
+        chans.append(S.make_channel(W, pixel_type=S.SWIH_PIXEL_U16 if u16 else S.SWIH_PIXEL_U8, bitdepth=bd,
+                                    bins=B))
+    ptrs = [b.data_ptr() for b in bufs]
+    C, Bt = len(chans), sum(CHANNEL_BINS)
+    stream = torch.cuda.Stream(device=dev)
+    side = torch.cuda.Stream(device=dev)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    plans = {"me": S.ChannelPlan(S.make_desc(H, W, bins=1, kernels=("manhattan", "euclidean"), max_win=(81, 81)),
+                                 chans),
+             "g": S.ChannelPlan(S.make_desc(H, W, bins=1, kernels=("gaussian",), max_win=(81, 81)), chans)}
+    jobs = [(k, w) for k in KERNELS for w in WINDOWS]
+    plan_of = {"manhattan": "me", "euclidean": "me", "gaussian": "g"}
+    try:
+        for pl in plans.values():
+            pl.build_ih(ptrs, stream)
+        targets = torch.empty((len(jobs), Bt), device=dev)
+        for j, (k, w) in enumerate(jobs):
+            plans[plan_of[k]].local_hist(k, w, w, tx, ty, 1, 1, targets[j], stream)
+        maps = [torch.empty((C, H - w + 1, W - w + 1), device=dev) for _, w in jobs]
+
+        def step():
+            fork.record(stream)
+            side.wait_event(fork)
+            for name, st in (("me", side), ("g", stream)):
+                plans[name].build_ih(ptrs, st)
+                for j, (k, w) in enumerate(jobs):
+                    if plan_of[k] == name:
+                        plans[name].likelihood_channels(k, w, w, targets[j], maps[j], st)
+            join.record(side)
+            stream.wait_event(join)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        for pl in plans.values():
+            pl.sync_status(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        for pl in plans.values():
+            pl.sync_status(stream)
+        n_win = sum(m.numel() for m in maps)
+        out = {"workload": ("1024x1024 benchmark scene as 3 feature channels (u8 8-bit, u16 12-bit, u8 6-bit; "
+                            "16 bins each), Manhattan/Euclidean/Gaussian x windows 21/41/81, one map per "
+                            "channel"),
+               "channels": C, "bins": list(CHANNEL_BINS), "windows_per_step": n_win, "steps": steps,
+               "ms_per_step": ms, "windows_per_s": n_win / (ms * 1e-3),
+               "launches_per_step": "K1 per channel and one K2 per plan; one gather per (kernel, window)"}
+        if not args.no_cpu_baseline:
+            rng = np.random.default_rng(14)
+            samples = []
+            for j, (k, w) in enumerate(jobs):
+                r = w // 2
+                cx = rng.integers(r, W - r, 128)
+                cy = rng.integers(r, H - r, 128)
+                got = maps[j][:, torch.from_numpy(cy - r).to(dev), torch.from_numpy(cx - r).to(dev)].cpu().numpy()
+                samples.append((k, w, cx, cy, got, targets[j].cpu().numpy().astype(np.float64)))
+            feats_np = [(a, bd) for a, bd in feats]
+            _ORACLE_LATER.append(("channels", lambda: channels_error(feats_np, samples)))
+    finally:
+        for pl in plans.values():
+            pl.close()
+    return out
+
+
+def channels_error(feats, samples):
+    """Largest |GPU - oracle| over 128 sampled centres of every (kernel, window,
+    channel) map, each channel scored over its own bins against its slice of
+    the target the GPU used."""
+    from oracle import swih_oracle as O
+
+    bins = [O.quantize(a, bd, B) for (a, bd), B in zip(feats, CHANNEL_BINS)]
+    worst, n = 0.0, 0
+    for k, w, cx, cy, got, q in samples:
+        K = O.kernel_weights(k, w, w)
+        off = 0
+        for c, B in enumerate(CHANNEL_BINS):
+            ref = O.likelihood_at(bins[c], B, K, q[off:off + B], cx, cy)
+            worst = max(worst, float(np.abs(got[c].astype(np.float64) - ref).max()))
+            n += cx.size
+            off += B
+    return {"max_abs": worst, "tolerance": 1e-5,
+            "sample": f"{n} centres: 128 random valid centres of every (kernel, window, channel) map, FP64 brute force"}
+
+
 def run_exponential(args, dev, lam=0.1, steps=50):
     """The exponential kernel exp(-lambda (|dx| + |dy|)), lambda = 0.1 per pixel,
     on the benchmark frame (1024x1024 u8, B = 32) at windows 21/41/81. One step =
@@ -1602,6 +1718,7 @@ def main():
                          ("batched_regions", run_regions),
                          ("serving", lambda a, d: run_serving(a, d, n_queries=a.serve_queries)),
                          ("large_frame", run_large_frame), ("exponential", run_exponential),
+                         ("channels", run_channels),
                          ("fig6", lambda a, d: run_fig6(a, frames=((1024, 1024),), cpu=False, reps=5))):
             t0 = time.perf_counter()
             line[name] = fn(args, dev)

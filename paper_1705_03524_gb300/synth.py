@@ -171,6 +171,20 @@ def config2(seed: int = 2, size: int = 1024) -> dict:
                 target_centre=sc.centres[0], scene=sc)
 
 
+def feature_channels(image: np.ndarray, seed: int) -> list:
+    """Three feature images of one u8 scene, in the roles of the tracker's
+    intensity, texture and coarse colour features (Sec. 4): the scene itself
+    (u8, 8 bits); a 12-bit texture-like channel mixing the scene with seeded
+    uniform noise (u16); and a 6-bit channel derived from the scene (u8).
+    Returns [(array, bitdepth)]; the array's dtype gives the pixel type."""
+    H, W = image.shape
+    sc = image.astype(np.int64)
+    tex = uniform_image(H, W, 16, seed=seed).astype(np.int64) >> 4  # 12 significant bits
+    tex = ((tex + 16 * sc) % 4096).astype(np.uint16)
+    six = (sc * 3 // 4 % 64).astype(np.uint8)
+    return [(image, 8), (tex, 12), (six, 6)]
+
+
 def config3(seed: int = 3, n_rois: int = 64, size: int = 4096, roi_range: tuple = (96, 768),
             box_range: tuple = (24, 64)) -> dict:
     """Batched search regions: a 4096 x 4096 uint16 frame (fBm background
