@@ -238,9 +238,6 @@ class FrameStep:
         self.stages = ([s for s, pl in (("build_me", self.plan_me), ("build_g", self.plan_g)) if pl]
                        + [f"gather_{k}" for k in kernels])
 
-    def stream_of(self, stage):
-        return self.stream if stage in ("build_g", "gather_gaussian") else self.side
-
     def new_events(self):
         """Begin and end events of every stage of one step."""
         import torch
@@ -248,10 +245,10 @@ class FrameStep:
         return {st: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for st in self.stages}
 
-    def run_maps(self, d_img, targets, maps, s, side, ev=None, on_map=None):
+    def run_maps(self, d_img, targets, maps, s, side, ev=None):
         """Enqueue one step on d_img: builds and gathers of both plans, the
         Manhattan+Euclidean ones on `side` (forked from and joined back to s).
-        on_map(job, stream) runs after each kernel's gather launch."""
+        ev (optional): new_events() of this step."""
         def mark(stage, i, st):
             if ev is not None:
                 ev[stage][i].record(st)
@@ -271,9 +268,6 @@ class FrameStep:
             self.plan_of[k].likelihood_scales(k, [(self.jobs[j][1], self.jobs[j][1]) for j in js],
                                               [targets[j] for j in js], [maps[j] for j in js], st)
             mark(f"gather_{k}", 1, st)
-            if on_map is not None:
-                for j in js:
-                    on_map(j, st)
         if side is not s:
             self.join.record(side)
             s.wait_event(self.join)
