@@ -285,6 +285,17 @@ class FrameStep:
                 out.setdefault(st, []).append(e0.elapsed_time(e1))
         return {k: float(np.mean(v)) for k, v in out.items()}
 
+    @staticmethod
+    def step_ms(events, first="build_g"):
+        """Median, p99 and max of the step periods: from one step's first event
+        on the main stream to the next step's (no extra events: one recorded
+        ahead of the fork changed how the two streams were scheduled)."""
+        t = np.array([a[first][0].elapsed_time(b[first][0]) for a, b in zip(events, events[1:])])
+        if t.size == 0:
+            return None
+        return {"p50": float(np.median(t)), "p99": float(np.percentile(t, 99)), "max": float(t.max()),
+                "periods": int(t.size)}
+
     def timed(self, steps, clocks=None):
         """Time `steps` steps with CUDA events (after a synchronize); returns
         (total ms, per-launch mean ms by stage, integral-histogram bytes the
@@ -442,6 +453,14 @@ def run_swih(args, rank, world, local_rank):
     if H != 1024 or B != 32:
         prof = None  # the committed counters are for the benchmark workload only
     traffic = profile_traffic(prof, src) if prof else None
+    # the gathers (K3) alone: the step's windows over the sum of its gather
+    # launches, each alone on the GPU (the one-stream pass)
+    alone = solo["per_launch_ms"] if solo else seg_ms
+    g_ms = sum(v for k, v in alone.items() if k.startswith("gather_"))
+    gather_only = {"value": fr.windows_per_step / (g_ms * 1e-3) if g_ms else None, "unit": "windows/s",
+                   "ms_per_step": g_ms,
+                   "basis": ("the step's windows over the sum of its gather launches' CUDA-event times, "
+                             "each launch alone on the GPU")}
     roof_solo = None
     if solo:
         s_ms = float(np.mean([solo["per_launch_ms"][k] for k in dom_keys]))
@@ -586,6 +605,8 @@ def run_swih(args, rank, world, local_rank):
                      "bytes_basis": basis, "dense_bytes_per_launch": dense_bytes,
                      "avg_launch_ms": dom_ms, "solo": roof_solo},
         "per_launch_ms": seg_ms,
+        "step_ms": FrameStep.step_ms(events),
+        "gather_only": gather_only,
         "clocks": clk,
     }
     if sustained:
