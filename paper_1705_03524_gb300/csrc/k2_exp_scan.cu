@@ -181,10 +181,13 @@ __global__ void __launch_bounds__(512) exp_scan_kernel(const ExpScanParams p)
     u64 outf[E], outr[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) outf[i] = outr[i] = 0;
+    // the warp-total buffers alternate per scanned row (rows formed by decay
+    // pass no barrier, so alternating per image row could reuse a buffer that
+    // a slower warp has not yet read)
+    int par = 1;
 
     for (int r = r0; r < r1; ++r) {
         const int y = side ? p.H - 1 - r : r;
-        const int par = (r - r0) & 1;
         if constexpr (kDecay) {
             if (r > r0 && r - r0 < 64 && !((rmask >> (r - r0)) & 1ull)) {
 #pragma unroll
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(512) exp_scan_kernel(const ExpScanParams p)
                 continue;
             }
         }
+        par ^= 1;
         const unsigned m = match_bits<E>(p.bins + (int64_t)y * p.bins_pitch, x0, p.W, b);
 #pragma unroll
         for (int i = 0; i < E; ++i) C[i] = mulq(C[i], p.q1) + (((m >> i) & 1u) ? p.one : 0ull);
