@@ -286,10 +286,14 @@ class FrameStep:
         return {k: float(np.mean(v)) for k, v in out.items()}
 
     @staticmethod
-    def step_ms(events, first="build_g"):
+    def step_ms(events):
         """Median, p99 and max of the step periods: from one step's first event
-        on the main stream to the next step's (no extra events: one recorded
-        ahead of the fork changed how the two streams were scheduled)."""
+        on the main stream (the Gaussian build's, else the only plan's) to the
+        next step's (no extra events: one recorded ahead of the fork changed how
+        the two streams were scheduled)."""
+        if not events:
+            return None
+        first = "build_g" if "build_g" in events[0] else next(iter(events[0]))
         t = np.array([a[first][0].elapsed_time(b[first][0]) for a, b in zip(events, events[1:])])
         if t.size == 0:
             return None
