@@ -936,14 +936,15 @@ def run_large_frame(args, dev, budget_gb=100, passes=3):
         loaded = {k: v / passes for k, v in st.load_bytes(reset=True).items() if v}
         stages = st.run_timed(stream)
         st.sync_status(stream)
-        # end to end: frame up from pinned memory, the pass, every map back
-        # (one untimed pass first)
+        # end to end: frame up from pinned memory, the pass with every map's
+        # rows copied back band by band as each band completes (the pass's
+        # own host copies, beside the next band's work); one untimed pass first
+        st.set_host_maps(h_maps)
+
         def e2e_pass():
             with torch.cuda.stream(stream):
                 d_img.copy_(h_img, non_blocking=True)
                 st.run(stream)
-                for hm, m in zip(h_maps, maps):
-                    hm.copy_(m, non_blocking=True)
 
         e2e_pass()
         st.sync_status(stream)

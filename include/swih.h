@@ -491,6 +491,19 @@ swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *j
 /* Enqueue one pass (every band, every job) on the stream. */
 swih_status swih_stream_run(swih_stream_t st, void *stream);
 
+/* Host copies of the maps, made during the pass: h_maps[j] (host memory of
+ * job j's whole valid map, (height - win_h + 1) x (width - win_w + 1) floats,
+ * caller-owned and page-locked: the copies are part of the pass's graph)
+ * receives each band's rows of job j's map as soon as the band's gathers (and
+ * column-tile copies) are done, on a second branch of the pass's graph, while
+ * the next band computes; the pass (swih_stream_run) completes when every
+ * copy has. NULL
+ * h_maps (or a NULL entry) turns the copies off (for that job). Takes effect
+ * at the next swih_stream_run (the pass is captured again); the host buffers
+ * must stay valid while passes that copy into them run. Not used by
+ * swih_stream_run_timed. */
+swih_status swih_stream_set_host_maps(swih_stream_t st, float *const *h_maps);
+
 /* One pass as swih_stream_run, for measurement: the bands' launches are
  * enqueued one by one (not as the graph) with CUDA events between stages, the
  * stream is synchronised, and stage_ms (7 floats) receives milliseconds summed

@@ -46,6 +46,9 @@ struct swih_stream_s {
     char *h_tables = nullptr;  // pinned copies of every band's tables
     std::vector<uint64_t> tab_off;
     cudaStream_t cap = nullptr;
+    std::vector<float *> h_maps;           // per job: host copy of its map (NULL: none)
+    cudaStream_t down = nullptr;           // the graph branch of the host copies
+    cudaEvent_t band_done = nullptr, down_done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -164,17 +167,52 @@ cudaError_t enqueue_copies(const swih_stream_s &S, size_t k, cudaStream_t s)
     return cudaSuccess;
 }
 
+// band k's rows of every job's map into the job's host map (whole rows: one
+// contiguous copy per job), on stream s
+cudaError_t enqueue_downloads(const swih_stream_s &S, int k, cudaStream_t s)
+{
+    const int H = S.desc.height, W = S.desc.width, R = S.R, Hb = S.band_h, nb = S.n_bands;
+    const int lo = k == 0 ? 0 : R + k * Hb;
+    const int hi = k == nb - 1 ? H : R + (k + 1) * Hb;
+    for (size_t j = 0; j < S.jobs.size(); ++j) {
+        float *h = j < S.h_maps.size() ? S.h_maps[j] : nullptr;
+        if (!h) continue;
+        const swih_frame_job &fj = S.jobs[j];
+        const int ry = (fj.win_h - 1) / 2;
+        const int c_lo = std::max(lo, ry), c_hi = std::min(hi, H - ry);
+        if (c_hi <= c_lo) continue;
+        const int64_t nx = W - fj.win_w + 1;
+        const int64_t off = (int64_t)(c_lo - ry) * nx;
+        const cudaError_t e = cudaMemcpyAsync(h + off, fj.d_map + off, (size_t)(c_hi - c_lo) * nx * sizeof(float),
+                                              cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 swih_status capture(swih_stream_s *S)
 {
     cudaError_t e = cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(nullptr, "cudaStreamBeginCapture", e);
     cudaError_t le = cudaSuccess;
+    bool down = false;
+    for (float *h : S->h_maps) down |= h != nullptr;
     for (size_t k = 0; k < S->bands.size() && le == cudaSuccess; ++k) {
         WorkSet &ws = *S->bands[k];
         le = cudaMemcpyAsync(ws.tables_device(), S->h_tables + S->tab_off[k], ws.tables_bytes(),
                              cudaMemcpyHostToDevice, S->cap);
         if (le == cudaSuccess) le = ws.enqueue(S->cap, false);
         if (le == cudaSuccess) le = enqueue_copies(*S, k, S->cap);
+        if (down && le == cudaSuccess && (k + 1) % S->n_tiles == 0) {
+            // the band is complete: its map rows go down beside the next band
+            le = cudaEventRecord(S->band_done, S->cap);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(S->down, S->band_done, 0);
+            if (le == cudaSuccess) le = enqueue_downloads(*S, (int)(k / S->n_tiles), S->down);
+        }
+    }
+    if (down && le == cudaSuccess) {  // the pass ends with its last copy
+        le = cudaEventRecord(S->down_done, S->down);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(S->cap, S->down_done, 0);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(S->cap, &g);
@@ -319,6 +357,9 @@ swih_status swih_stream_plan(const swih_plan_desc *desc, const swih_frame_job *j
     e = cudaMallocHost(reinterpret_cast<void **>(&S->h_tables), std::max<uint64_t>(tab_total, 256));
     if (e == cudaSuccess) e = cudaMemset(S->d_mem, 0, 256);  // status word
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->down, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->band_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->down_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         swih_stream_destroy(S.release());
         return cuda_fail(nullptr, "stream set-up", e);
@@ -338,6 +379,22 @@ swih_status swih_stream_run(swih_stream_t S, void *stream)
     }
     const cudaError_t e = cudaGraphLaunch(S->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(nullptr, "cudaGraphLaunch", e);
+    return SWIH_OK;
+}
+
+swih_status swih_stream_set_host_maps(swih_stream_t S, float *const *h_maps)
+{
+    if (!S) return tfail(SWIH_ERR_INVALID_ARG, "stream plan is NULL");
+    std::vector<float *> v(S->jobs.size(), nullptr);
+    if (h_maps)
+        for (size_t j = 0; j < v.size(); ++j) v[j] = h_maps[j];
+    if (v == S->h_maps) return SWIH_OK;
+    S->h_maps = v;
+    // capture the pass again at the next run
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    S->exec = nullptr;
+    S->graph = nullptr;
     return SWIH_OK;
 }
 
@@ -423,6 +480,9 @@ swih_status swih_stream_destroy(swih_stream_t S)
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
     if (S->cap) cudaStreamDestroy(S->cap);
+    if (S->down) cudaStreamDestroy(S->down);
+    if (S->band_done) cudaEventDestroy(S->band_done);
+    if (S->down_done) cudaEventDestroy(S->down_done);
     cudaError_t e = cudaSuccess;
     if (S->d_mem) e = cudaFree(S->d_mem);
     if (S->h_tables) cudaFreeHost(S->h_tables);

@@ -306,11 +306,13 @@ def _load() -> ctypes.CDLL:
     lib.swih_stream_sync_status.argtypes = [P, P]
     lib.swih_stream_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_uint64)]
+    lib.swih_stream_set_host_maps.argtypes = [P, ctypes.POINTER(ctypes.c_void_p)]
     lib.swih_stream_destroy.argtypes = [P]
     lib.swih_stream_run_timed.argtypes = [P, P, ctypes.POINTER(ctypes.c_float)]
     lib.swih_stream_load_bytes.argtypes = [P, U64P, I]
     for name in ("swih_stream_plan", "swih_stream_run", "swih_stream_sync_status", "swih_stream_get_info",
-                 "swih_stream_destroy", "swih_stream_run_timed", "swih_stream_load_bytes"):
+                 "swih_stream_destroy", "swih_stream_run_timed", "swih_stream_load_bytes",
+                 "swih_stream_set_host_maps"):
         getattr(lib, name).restype = S
     for name in ("swih_server_create", "swih_server_add_frame", "swih_query_out_elems",
                  "swih_server_query_bytes", "swih_server_submit", "swih_server_poll",
@@ -816,12 +818,24 @@ class Stream:
                                     ctypes.byref(h)))
         self.handle = int(h.value)
         self._keep = (image, tuple(keep))
+        self._host = ()
 
     def run(self, stream=None):
         _check(LIB.swih_stream_run(self.handle, _stream(stream)))
 
     def sync_status(self, stream=None):
         _check(LIB.swih_stream_sync_status(self.handle, _stream(stream)))
+
+    def set_host_maps(self, h_maps):
+        """Host copies of the maps made during each pass, band by band (one
+        page-locked host tensor or pointer per job, or None; h_maps None: off)."""
+        if h_maps is None:
+            _check(LIB.swih_stream_set_host_maps(self.handle, None))
+            self._host = ()
+            return
+        arr = (ctypes.c_void_p * len(h_maps))(*[_ptr(m) for m in h_maps])
+        _check(LIB.swih_stream_set_host_maps(self.handle, arr))
+        self._host = tuple(h_maps)  # kept alive while passes copy into them
 
     def run_timed(self, stream=None):
         """One pass launched stage by stage with CUDA events; returns

@@ -100,6 +100,37 @@ def test_budget_sets_the_band_height():
     assert ei.value.status == S.SWIH_ERR_BUDGET
 
 
+@pytest.mark.parametrize("band_height", [37, 0])
+def test_host_maps_copied_band_by_band(band_height):
+    """With host maps set, each pass leaves every map in its page-locked host
+    buffer (copied band by band during the pass) equal to the device map; a
+    second pass into freshly cleared buffers does the same, and turning the
+    copies off leaves the buffers untouched."""
+    img, d = setup_frame(seed=11)
+    bd, B = 12, 16
+    _bins, jobs = make_jobs(img, bd, B, JOBS)
+    full = S.swih_plan_workspace_bytes(desc_for(img, bd, B))
+    desc = desc_for(img, bd, B, hbm_budget_bytes=0 if band_height else full // 4)
+    fj = [S.make_frame_job(j["kernel"], j["w"], j["h"], j["target"], j["map"]) for j in jobs]
+    hosts = [torch.full(j["map"].shape, -2.0).pin_memory() for j in jobs]
+    with S.Stream(desc, fj, d, band_height=band_height) as st:
+        assert st.info()["n_bands"] >= 3
+        st.set_host_maps(hosts)
+        for _ in range(2):
+            for h in hosts:
+                h.fill_(-2.0)
+            st.run()
+            st.sync_status()
+            for h, j in zip(hosts, jobs):
+                assert torch.equal(h, j["map"].cpu()), (j["kernel"], j["w"], j["h"])
+        st.set_host_maps(None)
+        for h in hosts:
+            h.fill_(-2.0)
+        st.run()
+        st.sync_status()
+        assert all((h == -2.0).all() for h in hosts)
+
+
 def test_large_frame_sampled():
     """8192 x 8192 u16 frame, B = 64, Gaussian and Euclidean kernels at windows
     15/25/43/75/127, streamed in bands within a 100 GB budget; sampled centres
