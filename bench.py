@@ -756,9 +756,10 @@ def run_small_frame(args, dev, reps=200):
         g_dev, g_e2e = [], []
         for i in range(reps + 10):
             t0 = time.perf_counter()
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
+            with torch.cuda.stream(stream):  # replay() launches on the current stream
+                e0.record(stream)
+                graph.replay()
+                e1.record(stream)
             stream.synchronize()
             if i >= 10:
                 g_e2e.append((time.perf_counter() - t0) * 1e3)
@@ -767,7 +768,8 @@ def run_small_frame(args, dev, reps=200):
         d_map.fill_(-1.0)
         h_map.fill_(-1.0)
         torch.cuda.synchronize()
-        graph.replay()
+        with torch.cuda.stream(stream):
+            graph.replay()
         stream.synchronize()
         p.sync_status(stream)
         graph_equal = bool(torch.equal(h_map, eager_map))
