@@ -49,6 +49,65 @@ __device__ __forceinline__ void st_release(int *p, int v)
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr)
+{
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for phase 0 of the mbarrier for at most about 2 s; false when it gave up
+__device__ __forceinline__ bool bar_wait0(uint64_t *bar)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, 100000;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar))
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+// The band's n_rows rows of bins (seg bytes each, 16-byte aligned) into shared
+// memory at dst with stride row_bytes: thread 0 issues one bulk copy per row,
+// counted on the mbarrier, and every thread waits (bounded). The result is the
+// same in every thread of the block: false when any thread's wait gave up.
+__device__ __forceinline__ bool band_bins_bulk(uint64_t *bar, uint8_t *dst, int row_bytes, const uint8_t *src,
+                                               int64_t pitch, int n_rows, uint32_t seg)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"((uint32_t)n_rows * seg)
+                     : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int o = 0; o < n_rows; ++o)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(dst + (size_t)o * row_bytes)),
+                "l"(src + (int64_t)o * pitch), "r"(seg), "r"(smem_u32(bar))
+                : "memory");
+    }
+    bool ok = bar_wait0(bar);
+    if (!ok) ok = bar_wait0(bar);  // copies in flight still land in this block's shared memory: wait once more
+    return !__syncthreads_or(!ok);
+}
+
 template <typename T>
 __device__ __forceinline__ T ring_pow(T base, int e)
 {
@@ -228,8 +287,24 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     const uint8_t *bins = r.bins + (int64_t)p.ch_of_bin[b] * p.ch_stride;  // the plane of b's feature channel
     if (ticket == p.stall_tile && band == 0) return;  // injected stall: publish nothing
 
-    // ---- 1. band aggregate of [bin == b] * y^q per column, and which rows hold the bin
+    // ---- 1. band aggregate of [bin == b] * y^q per column, and which rows hold the bin.
+    // When the band's bins are kept in shared memory they arrive there first,
+    // all rows at once, by bulk copies (a row at a time, each a dependent global
+    // load, exposed the memory latency once per row in short tiles).
     if (tid == 0) s_rows = 0ull;
+    const bool bulk = p.sb_rows > 0 && ((reinterpret_cast<uintptr_t>(bins) | (uintptr_t)r.bins_pitch) & 15) == 0;
+    if (bulk) {
+        __shared__ __align__(8) uint64_t s_bar;
+        const uint32_t seg = (uint32_t)((r.W + 15) & ~15);
+        if (!band_bins_bulk(&s_bar, s_band_bins, row_bytes, bins + (int64_t)y_begin * r.bins_pitch, r.bins_pitch,
+                            y_end - y_begin, seg)) {
+            if (tid == 0) {
+                atomicOr(p.status, kStatusTimeout);
+                st_release(r.flags + (int64_t)chain * r.n_bands + band, kFlagError);
+            }
+            return;  // uniform over the block
+        }
+    }
     T agg[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) agg[e] = 0;
@@ -237,8 +312,12 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     if (has_cols) {
         for (int y = y_begin; y < y_end; ++y) {
             uint8_t v[E];
-            load_bins<E>(bins + (int64_t)y * r.bins_pitch, x0, v);
-            if (p.sb_rows > 0) put_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
+            if (bulk) {
+                load_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
+            } else {
+                load_bins<E>(bins + (int64_t)y * r.bins_pitch, x0, v);
+                if (p.sb_rows > 0) put_bins<E>(s_band_bins + (y - y_begin) * row_bytes, x0, v);
+            }
             bool hit[E];
             bool any = false;
 #pragma unroll
