@@ -31,6 +31,7 @@
 // bin image (1 byte per pixel) is read twice per tile and stays in L2.
 #pragma once
 
+#include "bulk_rows.cuh"
 #include "ring128.h"
 #include "swih_internal.h"
 
@@ -47,65 +48,6 @@ __device__ __forceinline__ int ld_acquire(const int *p)
 __device__ __forceinline__ void st_release(int *p, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *ptr)
-{
-    return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// wait for phase 0 of the mbarrier for at most about 2 s; false when it gave up
-__device__ __forceinline__ bool bar_wait0(uint64_t *bar)
-{
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, 100000;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_u32(bar))
-            : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
-    }
-}
-
-// The band's n_rows rows of bins (seg bytes each, 16-byte aligned) into shared
-// memory at dst with stride row_bytes: thread 0 issues one bulk copy per row,
-// counted on the mbarrier, and every thread waits (bounded). The result is the
-// same in every thread of the block: false when any thread's wait gave up.
-__device__ __forceinline__ bool band_bins_bulk(uint64_t *bar, uint8_t *dst, int row_bytes, const uint8_t *src,
-                                               int64_t pitch, int n_rows, uint32_t seg)
-{
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                     "r"((uint32_t)n_rows * seg)
-                     : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int o = 0; o < n_rows; ++o)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(dst + (size_t)o * row_bytes)),
-                "l"(src + (int64_t)o * pitch), "r"(seg), "r"(smem_u32(bar))
-                : "memory");
-    }
-    bool ok = bar_wait0(bar);
-    if (!ok) ok = bar_wait0(bar);  // copies in flight still land in this block's shared memory: wait once more
-    return !__syncthreads_or(!ok);
 }
 
 template <typename T>
@@ -296,8 +238,10 @@ __device__ __forceinline__ void scan_tile(const ScanParams &p, const ScanRoi &r,
     if (bulk) {
         __shared__ __align__(8) uint64_t s_bar;
         const uint32_t seg = (uint32_t)((r.W + 15) & ~15);
-        if (!band_bins_bulk(&s_bar, s_band_bins, row_bytes, bins + (int64_t)y_begin * r.bins_pitch, r.bins_pitch,
-                            y_end - y_begin, seg)) {
+        const uint8_t *band_src = bins + (int64_t)y_begin * r.bins_pitch;
+        const int64_t pitch = r.bins_pitch;
+        if (!rows_bulk(&s_bar, s_band_bins, row_bytes, y_end - y_begin, seg,
+                       [&](int o) { return band_src + (int64_t)o * pitch; })) {
             if (tid == 0) {
                 atomicOr(p.status, kStatusTimeout);
                 st_release(r.flags + (int64_t)chain * r.n_bands + band, kFlagError);
