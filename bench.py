@@ -1630,6 +1630,26 @@ def serving_error(frames, qs, samples):
 _ORACLE_SETUP = {}
 
 
+def cpu_model() -> str:
+    """The host CPU's name (model name, else implementer/part codes), for the
+    CPU baseline's record."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        m = re.search(r"^model name\s*:\s*(.+)$", info, re.M)
+        if m:
+            return m.group(1).strip()
+        imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+        part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+        if imp and part:
+            return f"{platform.machine()} (implementer {imp.group(1)}, part {part.group(1)})"
+    except OSError:
+        pass
+    return platform.machine() or "unknown"
+
+
 def oracle_sample(budget_s: float, seed: int = 7):
     """Time the CPU oracle on random valid centres of the same workload (all nine
     kernel/window maps, round robin) for about budget_s seconds (at least one
@@ -1689,7 +1709,7 @@ def run_reference(args, rank, world):
     wall = time.perf_counter() - t0
     value = float(np.mean(vals))
     cpu = {"value": value, "unit": "windows/s", "cores": res["cores"], "kind": "oracle",
-           "sample": res["sample"]}
+           "sample": res["sample"], "cpu_model": cpu_model()}
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "windows/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1792,6 +1812,7 @@ def main():
         res = oracle_sample(args.cpu_seconds)
         progress(f"cpu baseline: {time.perf_counter() - t0:.1f} s")
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["cpu_model"] = cpu_model()
         if _ORACLE_CHECK:
             try:
                 line["oracle_error"] = oracle_errors(*_ORACLE_CHECK)
