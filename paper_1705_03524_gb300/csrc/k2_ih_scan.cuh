@@ -523,10 +523,16 @@ __global__ void __launch_bounds__(kMaxScanThreads)
     scan_tile<T, E, NP, !SPARSE, SPARSE>(p, r, ticket, band, local - band * n_chains);
 }
 
+// the kernel's dynamic shared memory limit raised to `bytes` when the default
+// 48 KB does not hold them beside the kernel's static shared memory
 template <typename KernelFn>
 cudaError_t allow_smem(KernelFn fn, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes == 0) return cudaSuccess;
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (bytes + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

@@ -266,6 +266,30 @@ def test_injected_stall_reports_timeout_and_recovers():
         check_ih(plan, img, 8, 4)
 
 
+@pytest.mark.parametrize("band_rows", [16, 24, 47, 48, 64])
+def test_band_heights_at_the_shared_memory_limit(band_rows):
+    """Band heights whose band of bins (band_rows x 1024 bytes kept in shared
+    memory) sits on either side of the default 48 KB limit, beside the scan's
+    static shared memory: both plans of the benchmark frame build and equal the
+    default band height's integral histograms through their maps."""
+    cfg = synth.config2()
+    img = cfg["image"]
+    H, W = img.shape
+    B = cfg["B"]
+    d = torch.from_numpy(img).to(DEV)
+    for kernels, kind, w in ((("gaussian",), "gaussian", 81), (("manhattan", "euclidean"), "euclidean", 41)):
+        q = torch.full((B,), 1.0 / B, device=DEV)
+        maps = []
+        for br in (0, band_rows):
+            with S.Plan(S.make_desc(H, W, bins=B, kernels=kernels, max_win=(w, w), band_rows=br)) as p:
+                p.build_ih(d)
+                m = torch.empty((H - w + 1, W - w + 1), device=DEV)
+                p.likelihood(kind, w, w, q, m)
+                p.sync_status()
+                maps.append(m)
+        assert torch.equal(maps[0], maps[1]), (kind, band_rows)
+
+
 # --------------------------------------------------------------------------- full size
 def test_benchmark_workload_sampled_centres():
     """1024 x 1024 synthetic scene, B = 32, the three weighted kernels at windows
