@@ -227,13 +227,20 @@ def test_frames_wider_than_8192_columns_in_column_tiles():
     desc = S.make_desc(H, W, pixel_type=S.SWIH_PIXEL_U16, bitdepth=bd, bins=B,
                        kernels=("manhattan", "euclidean", "gaussian"), max_win=(43, 41))
     fj = [S.make_frame_job(j["kernel"], j["w"], j["h"], j["target"], j["map"]) for j in jobs]
+    hosts = [torch.full(j["map"].shape, -2.0).pin_memory() for j in jobs]
     with S.Stream(desc, fj, d, band_height=150) as st:
         st.run()
         st.sync_status()
         info = st.info()
+        # host maps: each band's rows go down after its last column tile and that
+        # tile's copies into the frame maps
+        st.set_host_maps(hosts)
+        st.run()
+        st.sync_status()
     assert info["n_bands"] == 3
-    for j in jobs:
+    for h, j in zip(hosts, jobs):
         assert (j["map"] >= 0).all(), "a centre was not written"
+        assert torch.equal(h, j["map"].cpu()), (j["kernel"], j["w"])
     # plans over the left and right 8192 columns (frame pitch): every centre of
     # the frame lies in one of them
     for x0 in (0, W - 8192):
