@@ -18,17 +18,21 @@
 // over the bands above it (Merrill & Garland's scheme, carried on W-wide state
 // vectors instead of scalars):
 //   1. sum the band's own rows into a per-column aggregate, publish it
-//      (flag AGGREGATE; band 0 publishes its INCLUSIVE value directly);
+//      (flag AGGREGATE; band 0 publishes its INCLUSIVE value directly); when
+//      the band's bins fit in shared memory they arrive there first, every
+//      row at once, by TMA bulk copies (bulk_rows.cuh);
 //   2. walk back over earlier bands, adding aggregates until an INCLUSIVE
 //      vector is found; every wait is bounded and a wait that gives up marks
 //      the tile ERROR and sets the plan's status word;
 //   3. publish carry + aggregate as INCLUSIVE;
 //   4. sweep the band again, carrying cs_q in registers, and write each row of
 //      every term of the chain with a block-wide scan (thread-serial over E
-//      columns, warp shuffles, then a cross-warp pass through shared memory);
-//      the next row's bins are loaded while the current row is scanned.
+//      columns, warp shuffles, then a cross-warp pass through shared memory),
+//      reading the bins from shared memory (or, for bands too tall to keep
+//      there, loading the next row's bins while the current row is scanned).
 // Output writes are full rows, coalesced, each IH element written once; the
-// bin image (1 byte per pixel) is read twice per tile and stays in L2.
+// bin image (1 byte per pixel) is read once per tile when the band's bins are
+// kept in shared memory, else twice, and stays in L2.
 #pragma once
 
 #include "bulk_rows.cuh"
