@@ -160,3 +160,43 @@ def test_sampled_error_reports_of_the_extra_blocks_find_planted_differences():
     blocks[1][15, 0] += 0.25
     res = bench.large_frame_error(sub, B, job_kw, tg, blocks, 100, 200, R, n=16)
     assert abs(res["per_map"]["euclidean_5"] - 0.25) < 1e-4 and res["per_map"]["gaussian_9"] <= 1e-6, res
+
+
+# --------------------------------------------------------------------------- step timing
+class _Ev:
+    """A stand-in for a CUDA event: elapsed_time is the difference of the
+    recorded times in ms."""
+
+    def __init__(self, t):
+        self.t = t
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+def test_stage_means_and_step_periods():
+    # three steps: the Gaussian build starts each step on the main stream
+    # (at 0, 2.5 and 4.9 ms), every stage has a begin and an end event
+    starts = [0.0, 2.5, 4.9]
+    events = []
+    for i, t0 in enumerate(starts):
+        events.append({"build_me": (_Ev(t0), _Ev(t0 + 0.5 + 0.1 * i)),
+                       "build_g": (_Ev(t0), _Ev(t0 + 0.8)),
+                       "gather_gaussian": (_Ev(t0 + 0.8), _Ev(t0 + 2.3))})
+    ms = bench.FrameStep.stage_ms(events)
+    assert np.isclose(ms["build_me"], 0.6) and np.isclose(ms["build_g"], 0.8)
+    assert np.isclose(ms["gather_gaussian"], 1.5)
+    per = bench.FrameStep.step_ms(events)
+    assert per["periods"] == 2
+    assert np.isclose(per["p50"], 2.45) and np.isclose(per["max"], 2.5)
+    # one stream and no Gaussian plan: the periods start at the first stage
+    me_only = [{"build_me": (_Ev(t), _Ev(t + 0.2))} for t in (0.0, 1.0, 2.2)]
+    per = bench.FrameStep.step_ms(me_only)
+    assert per["periods"] == 2 and np.isclose(per["max"], 1.2)
+    assert bench.FrameStep.step_ms([]) is None
+    assert bench.FrameStep.step_ms(me_only[:1]) is None
+
+
+def test_cpu_model_names_the_host():
+    name = bench.cpu_model()
+    assert isinstance(name, str) and name
