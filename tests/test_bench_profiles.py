@@ -1,4 +1,5 @@
-"""Host logic of bench.py's roofline: which committed ncu counters apply.
+"""Host logic of bench.py: which committed ncu counters apply to the
+roofline, and how the step's CUDA events become stage means and step periods.
 
 bench.py attaches a kernel's DRAM traffic from its summary under profiles/
 only while the kernel's code is the code that was captured. The summary
