@@ -106,29 +106,44 @@ class ClockSampler:
             self.first.wait(timeout)
 
     def stop(self, t0=None, t1=None):
-        """Summary of the samples taken between wall times t0 and t1."""
+        """Summary of the samples taken between wall times t0 and t1. A region
+        shorter than the sampling period may hold none: then the last sample
+        before it and the first after it, which bracket it, are summarised
+        (marked "bracketing")."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        if t1 is not None:  # let a sample after the region arrive (at most 0.5 s)
+            deadline = time.time() + 0.5
+            while time.time() < deadline and not any(ts > t1 for ts, _ in self.lines):
+                time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
+        samples = []
         for ts, ln in self.lines:
-            if t0 is not None and not (t0 <= ts <= t1):
-                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) == 7:
-                rows.append(parts)
+                samples.append((ts, parts))
+        rows = [r for ts, r in samples if t0 is None or t0 <= ts <= t1]
+        bracketing = False
+        if not rows and t0 is not None:
+            before = [r for ts, r in samples if ts < t0][-1:]
+            after = [r for ts, r in samples if ts > t1][:1]
+            rows = before + after
+            bracketing = bool(rows)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         smax = max(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": reasons, "samples": len(rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+               "reasons": reasons, "samples": len(rows)}
+        if bracketing:
+            out["bracketing"] = True  # the samples just before and after the region
+        return out
 
 
 def code_sha256(path: str) -> str:

@@ -201,3 +201,26 @@ def test_stage_means_and_step_periods():
 def test_cpu_model_names_the_host():
     name = bench.cpu_model()
     assert isinstance(name, str) and name
+
+
+def test_clock_summary_of_a_region_shorter_than_the_sampling_period():
+    """Samples inside the region are summarised; a region between two samples
+    gets the samples that bracket it, marked as such."""
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    row = "2070, 2070, 500.0, Not Active, Not Active, Not Active, {}"
+    cs = bench.ClockSampler(0)
+    cs.proc = _Proc()
+    cs.lines = [(1.0, row.format("Not Active")), (1.2, row.format("Active").replace("2070, 2070", "1995, 2070", 1)),
+                (2.0, row.format("Not Active"))]
+    inside = cs.stop(0.9, 1.5)
+    assert inside["samples"] == 2 and "bracketing" not in inside
+    assert inside["reasons"] == ["sw_power_cap"] and inside["sm_mhz"] == (2070 + 1995) / 2
+    short = cs.stop(1.05, 1.1)
+    assert short["bracketing"] and short["samples"] == 2 and short["sm_max_mhz"] == 2070
+    assert cs.stop(5.0, 6.0)["samples"] == 1
