@@ -6,24 +6,30 @@ One step is one pass of the whole hot path over one frame:
     - Gaussian approximant (terms x^k y^l, k, l <= 4; 64-bit ring)
   + window gather / translate / normalise / Bhattacharyya (K3) for every
     valid centre of 3 kernels x 3 windows (21, 41, 81): 8,602,224 windows.
+The two plans share only the frame, so a step runs them on two streams (the
+Gaussian plan on the main one, the other forked from it and joined back).
 The metric is windows per second (whole job). Inputs are resident in HBM
 when the timed region starts; the integral histograms (7.1 GB per step) are
 far larger than L2, so no explicit L2 flush is done between steps.
 
 Also reported: an end-to-end figure through the C ABI from pinned host memory
-(frame and targets up, all nine maps back, every step, on a copy stream that
-overlaps the kernels of neighbouring steps), the roofline of the
-dominant kernel (CUDA events on the launching stream), SM clocks sampled
-during the timed region, and the CPU oracle timed on the host cores on a
-bounded sample of the same workload.
+(frame and targets up, all nine maps back, every step, on copy streams that
+overlap the kernels of neighbouring steps), the gathers alone, the roofline of
+the dominant kernel (CUDA events on the launching stream, in the timed region
+and with the step on one stream), SM clocks sampled during the timed region,
+the step periods, and the CPU oracle timed on the host cores on a bounded
+sample of the same workload.
 
-At N = 1 the line also carries two measurements of the many-region paths:
-"batched_regions" (64 search regions of a 4096x4096 u16 frame, one batch
-replayed as a CUDA graph against one plan per region) and "serving" (a Poisson
-stream of tracking queries at 2000/s against 16 resident frames: the server's
-continuous batching against one plan per query, with p50/p99 latency), and
-"large_frame" (an 8192x8192 u16 frame whose integral histograms exceed device
-memory, streamed in bands).
+At N = 1 the line also carries measurements of other workloads: a 128x128
+frame's latency, the step on an i.i.d. frame (nothing to skip), the
+many-region paths "batched_regions" (64 search regions of a 4096x4096 u16
+frame, one batch replayed as a CUDA graph against one plan per region) and
+"serving" (a Poisson stream of tracking queries at 2000/s against 16 resident
+frames: the server's continuous batching against one plan per query, with
+p50/p99 latency), "large_frame" (an 8192x8192 u16 frame whose integral
+histograms exceed device memory, streamed in bands), the exponential kernel,
+feature channels and the Fig. 6 sweep; each with its error against the
+oracle where it makes maps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swih|reference]
 """
