@@ -694,6 +694,13 @@ def run_dense_scene(args, dev):
             _, seg, loaded_g, _ = fr.timed(steps)
             fr.side = side
         algo = stage_bytes(fr, H, W, B)
+        if not args.no_cpu_baseline:  # the last step's maps, against the oracle after the timed parts
+            torch.cuda.synchronize()
+            d_jobs = list(fr.jobs)
+            d_maps = [m.cpu().numpy() for m in fr.maps]
+            d_tgts = [t.cpu().numpy() for t in fr.targets]
+            _ORACLE_LATER.append(("dense_scene", lambda: oracle_errors(
+                img, B, d_jobs, d_maps, d_tgts, n=256, source="the maps of the block's last step")))
     finally:
         fr.close()
     peak, peak_kind = read_peaks()
@@ -1239,6 +1246,12 @@ def run_exponential(args, dev, lam=0.1, steps=50):
                 prev = ev[2 + i]
         p.sync_status(stream)
         info = p.info()
+        if not args.no_cpu_baseline:  # the last step's maps, against the oracle after the timed parts
+            e_maps = [maps[w].cpu().numpy() for w in WINDOWS]
+            e_q = q.cpu().numpy()
+            _ORACLE_LATER.append(("exponential", lambda: oracle_errors(
+                img, B, [("exponential", w) for w in WINDOWS], e_maps, [e_q] * len(WINDOWS), n=256,
+                source="the maps of the block's last step")))
     build = t_build / steps
     gathers = {w: t / steps for w, t in t_map.items()}
     step_ms = build + sum(gathers.values())
@@ -1574,7 +1587,8 @@ def run_fig6(args, frames=((480, 640), (1024, 1024)), cpu=True, reps=10):
 
 
 # ----------------------------------------------------------------------------- oracle
-def oracle_errors(img, B, jobs, maps, targets, n=2048, seed=11):
+def oracle_errors(img, B, jobs, maps, targets, n=2048, seed=11,
+                  source="the maps copied back at the end of the end-to-end run"):
     """Largest |GPU - oracle| of each likelihood map at n random valid centres.
 
     The FP64 brute-force oracle is evaluated with the target histograms the GPU
@@ -1597,15 +1611,17 @@ def oracle_errors(img, B, jobs, maps, targets, n=2048, seed=11):
             true = O.likelihood_at(bins, B, O.true_gaussian(w, w), np.asarray(targets[j], dtype=np.float64),
                                    cx, cy)
             approx[f"{k}_{w}"] = float(np.abs(got - true).max())
-    return {"max_abs": max(per.values()), "tolerance": 1e-5, "per_map": per,
-            "gaussian_vs_true_gaussian": {
-                "per_map": approx,
-                "note": ("approximation error, not parity: the Gaussian kernel is the degree-2 polynomial "
-                         "stand-in P(dx^2/rx^2) P(dy^2/ry^2) fitted to exp(-d^2/2 sigma^2), sigma = w/4; this "
-                         "is the largest |L_gpu - L| with L the brute-force likelihood under the exact "
-                         "Gaussian weights, same centres and targets")},
-            "sample": (f"{n} random valid centres per map (seed {seed}), FP64 brute-force oracle with the "
-                       "targets the GPU used, against the maps copied back at the end of the end-to-end run")}
+    out = {"max_abs": max(per.values()), "tolerance": 1e-5, "per_map": per,
+           "sample": (f"{n} random valid centres per map (seed {seed}), FP64 brute-force oracle with the "
+                      f"targets the GPU used, against {source}")}
+    if approx:
+        out["gaussian_vs_true_gaussian"] = {
+            "per_map": approx,
+            "note": ("approximation error, not parity: the Gaussian kernel is the degree-2 polynomial "
+                     "stand-in P(dx^2/rx^2) P(dy^2/ry^2) fitted to exp(-d^2/2 sigma^2), sigma = w/4; this "
+                     "is the largest |L_gpu - L| with L the brute-force likelihood under the exact "
+                     "Gaussian weights, same centres and targets")}
+    return out
 
 
 def regions_error(img, B, rois, samples, targets):

@@ -95,6 +95,12 @@ def test_oracle_error_reports_the_true_gaussian_distance():
     g = res["gaussian_vs_true_gaussian"]["per_map"]
     assert set(g) == {"gaussian_21"}
     assert 1e-5 < g["gaussian_21"] < 0.2, g
+    # without a Gaussian map the report carries no approximation entry, and it
+    # names where its maps came from
+    res = bench.oracle_errors(img, B, jobs[1:], maps[1:], np.stack(targets[1:]), n=64, seed=1,
+                              source="the maps of the block's last step")
+    assert "gaussian_vs_true_gaussian" not in res and res["max_abs"] <= 1e-6
+    assert res["sample"].endswith("the maps of the block's last step")
 
 
 def test_sampled_error_reports_of_the_extra_blocks_find_planted_differences():
